@@ -1,0 +1,170 @@
+/*
+ * pcgamg: PCG preconditioned by one aggregation-based AMG V-cycle per
+ * iteration, on one GB300 GPU (sm_103a).
+ *
+ * Method: arxiv 2210.16660, Sec. 3.1 (AMG as a stationary iteration used as
+ * a Krylov preconditioner; Galerkin coarse operators A_{l+1} = P_l^T A_l P_l;
+ * the V-cycle of Eq. (multiplicative composition); coarsening by compatible
+ * weighted matching, Eq. (weights) and Eq. (approximatematch); the tentative
+ * prolongator of Eq. (prolongator); aggregates of size up to 2^n_pass by
+ * multiplying pairwise prolongators) and Sec. 5 (flexible CG, stop on the
+ * Euclidean norm of the relative residual, warm start from the previous
+ * time step). Sec. 4: the preconditioner is built once and applied inside
+ * the Krylov driver through a single call.
+ *
+ * Variant implemented (fixed by the library, not by the paper): l1-Jacobi
+ * smoothing, one pre- and one post-sweep (M = diag(sum_j |a_ij|)); the
+ * tentative prolongator without the smoothing step; a dense float64
+ * direct solve on the coarsest level.
+ *
+ * Conventions for every entry point:
+ *  - All functions return an int status (AMG_OK = 0 or an AMG_ERR_* code);
+ *    none aborts. amg_last_error() returns a message for the calling thread.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). All device work of a call is ordered on that stream.
+ *  - Vectors may be host or device pointers; the library tells them apart
+ *    with cudaPointerGetAttributes. Host vectors are copied in and out
+ *    inside the call (the call then returns after the copy back).
+ *  - The library allocates its own device memory through the allocator set
+ *    by amg_set_allocator (cudaMalloc/cudaFree by default). No call frees
+ *    or writes caller memory other than its documented outputs.
+ *  - All entry points are safe to call from several host threads on
+ *    different handles; one handle must not be used by two calls at once.
+ */
+#ifndef PCGAMG_H
+#define PCGAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status */
+#define AMG_OK 0
+#define AMG_ERR_ARG 1       /* bad sizes, unsorted/unsymmetric CSR, bad handle */
+#define AMG_ERR_OOM 2       /* allocation failed or hbm_budget exceeded */
+#define AMG_ERR_BREAKDOWN 3 /* r.z <= 0 or p.Ap <= 0, or coarsest not SPD */
+#define AMG_ERR_NOCONV 4    /* maxit V-cycles without meeting rtol; x = last iterate */
+#define AMG_ERR_NAN 5       /* NaN or Inf in the iteration */
+#define AMG_ERR_CUDA 6      /* a CUDA runtime call failed */
+#define AMG_ERR_TIMEOUT 7   /* a bounded device-side wait expired */
+#define AMG_ERR_COARSE 8    /* coarsening stalled with more than 4096 rows left */
+
+/* Precision of the V-cycle (Sec. 5 uses flexible CG around the preconditioner). */
+#define AMG_MODE_PCG64 0    /* float64 V-cycle, plain PCG */
+#define AMG_MODE_FCG32 1    /* float32 V-cycle (values, smoother, transfers) inside
+                               float64 FCG(1); the coarsest solve stays float64 */
+
+typedef struct amg_hier *amg_handle;
+
+/* Square sparse matrix in CSR form (the matrix format of Sec. 4).
+ * Requirements: row_ptr[0] = 0, row_ptr nondecreasing, row_ptr[n] = nnz;
+ * column indices in [0, n), strictly increasing within a row; every row has
+ * its diagonal entry and it is > 0; the matrix is exactly symmetric (values
+ * equal bit for bit), as symmetric FE assembly gives. nnz < 2^31.
+ * on_device = 1 when the three arrays are device pointers. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const double *val;
+    int on_device;
+} amg_csr;
+
+/* Hierarchy options (cf. Table 1 of the paper for the paper's own set). */
+typedef struct {
+    int coarse_max;   /* stop coarsening when a level has <= this many rows (200) */
+    int n_pass;       /* pairwise matching passes per level, |G| <= 2^n_pass (2) */
+    int max_levels;   /* at most this many levels, coarsest included (30) */
+    int mode;         /* AMG_MODE_PCG64 or AMG_MODE_FCG32 for pcg_solve (PCG64) */
+    size_t hbm_budget;/* bytes the handle may allocate; 0 = no limit */
+} amg_params;
+
+/* Fill p with the defaults listed above. */
+void amg_default_params(amg_params *p);
+
+/* Device allocator used for every allocation made after the call (process
+ * wide). alloc returns NULL on failure. Passing NULL functions restores
+ * cudaMalloc/cudaFree. */
+typedef void *(*amg_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*amg_free_fn)(void *ptr, void *stream, void *ctx);
+int amg_set_allocator(amg_alloc_fn alloc, amg_free_fn dealloc, void *ctx);
+
+/* Build the AMG hierarchy of A on the current device (Sec. 3.1).
+ * All steps run on the GPU: l1 diagonals, Eq. (weights), the matching
+ * (locally-dominant, equal to the greedy matching under a strict total
+ * order), aggregates and tentative prolongator weights, pairwise Galerkin
+ * products P^T A P, sliced-ELL copies in float64 and float32, and the dense
+ * coarsest inverse. The level sizes are read back once per pass.
+ * A is copied; the caller may free it after the call returns.
+ * Errors: AMG_ERR_ARG (bad CSR), AMG_ERR_OOM, AMG_ERR_BREAKDOWN (coarsest
+ * not SPD), AMG_ERR_COARSE, AMG_ERR_CUDA. *out is NULL on error. */
+int amg_setup(const amg_csr *A, const amg_params *p, void *stream, amg_handle *out);
+
+/* Select the solve mode of a handle (AMG_MODE_PCG64 / AMG_MODE_FCG32). */
+int amg_set_mode(amg_handle h, int mode);
+
+/* Solve A x = b by PCG (mode PCG64) or FCG(1) (mode FCG32) preconditioned by
+ * one V-cycle per iteration (Sec. 3.1, Sec. 5).
+ * b: n values (host or device). x: n values, initial guess on entry (the
+ * warm start of Sec. 5), solution on exit. Stops when the recursive residual
+ * satisfies ||r_k|| / ||b|| <= rtol and the true residual b - A x does too;
+ * if the true one does not, r is replaced by it and the recurrence restarts.
+ * iters (may be NULL): V-cycles applied. res_hist (may be NULL, host or
+ * device, maxit+1 values): ||r_k|| / ||b|| for k = 0..iters.
+ * ||b|| = 0 returns x = 0, iters = 0. Returns AMG_ERR_NOCONV after maxit
+ * iterations (x holds the last iterate), AMG_ERR_BREAKDOWN, AMG_ERR_NAN. */
+int pcg_solve(amg_handle h, const double *b, double *x, double rtol, int maxit,
+              int *iters, double *res_hist, void *stream);
+
+/* True relative residual ||b - A x|| / ||b|| at the end of the last solve on h. */
+double amg_last_true_residual(amg_handle h);
+
+/* Hierarchy description: number of levels and, when the arrays are not NULL
+ * (host, length >= levels), rows and stored entries per level. */
+int amg_info(amg_handle h, int *levels, int64_t *n_l, int64_t *nnz_l);
+
+/* Aggregate map of one matching pass (host output, length = rows entering
+ * the pass): agg[i] = coarse index or -1 for a row left out of the coarse
+ * space. pass = -1 gives the composed map of the level. *n_out receives the
+ * rows entering the pass (call with agg = NULL to size the buffer), *nc_out
+ * the coarse rows it produces. */
+int amg_level_agg(amg_handle h, int level, int pass, int32_t *agg, int64_t *n_out,
+                  int64_t *nc_out);
+
+/* Copy level l's matrix in CSR form to host buffers (row_ptr n+1, col/val nnz). */
+int amg_level_csr(amg_handle h, int level, int32_t *row_ptr, int32_t *col, double *val);
+
+/* Setup time split, milliseconds (host buffer of 4): total, matching,
+ * Galerkin products, everything else. */
+int amg_setup_times(amg_handle h, double *ms);
+
+/* Kernel timing of later solves on h (enable = 1) or off (0). When on, each
+ * solve records CUDA events on its stream around the level-0 kernels and
+ * around the coarse-level part of the V-cycle. Adds no work to the kernels. */
+int amg_profile(amg_handle h, int enable);
+
+/* Accumulated device time (ms) and launch count per kernel kind since the
+ * last read, then reset. kinds: 0 level-0 pre-smooth/residual, 1 level-0
+ * prolong/post-smooth (+ r.z), 2 q = A p, 3 x/r update, 4 true residual,
+ * 5 levels >= 1 incl. restriction and coarsest solve (one span per V-cycle).
+ * ms and counts are host arrays of length nkinds (<= 6). */
+int amg_profile_read(amg_handle h, double *ms, int64_t *counts, int nkinds);
+
+/* Kernels launched by solves on h since setup (every launch, including the
+ * ones that find the solve finished and return at once). */
+int64_t amg_launch_count(amg_handle h);
+
+/* Release every device allocation of the handle (NULL is ignored). */
+void amg_destroy(amg_handle h);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCGAMG_H */

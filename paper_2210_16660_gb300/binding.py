@@ -1,0 +1,284 @@
+"""Python binding of libpcgamg: argument marshalling only.
+
+Every step of setup and solve runs in the CUDA library through its C ABI
+(``include/pcgamg.h``); this module converts numpy arrays / torch tensors to
+pointers, passes torch's current CUDA stream, and can route the library's
+device allocations through torch's caching allocator. If the library cannot
+be loaded the import of this module raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_NAN, ERR_CUDA, ERR_TIMEOUT, ERR_COARSE = range(9)
+MODE_PCG64, MODE_FCG32 = 0, 1
+_MODES = {"pcg64": MODE_PCG64, "fcg32": MODE_FCG32}
+
+# Every symbol the header declares (checked by the CPU tests).
+EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode", "pcg_solve",
+           "amg_last_true_residual", "amg_info", "amg_level_agg", "amg_level_csr", "amg_setup_times",
+           "amg_destroy", "amg_last_error", "amg_profile", "amg_profile_read", "amg_launch_count")
+
+
+class AmgCsr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("on_device", C.c_int)]
+
+
+class AmgParams(C.Structure):
+    _fields_ = [("coarse_max", C.c_int), ("n_pass", C.c_int), ("max_levels", C.c_int), ("mode", C.c_int),
+                ("hbm_budget", C.c_size_t)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libpcgamg.so (building it with nvcc when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpcgamg not built: {path}")
+    lib = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    lib.amg_default_params.argtypes = [C.POINTER(AmgParams)]
+    lib.amg_default_params.restype = None
+    lib.amg_set_allocator.argtypes = [P, P, P]
+    lib.amg_set_allocator.restype = I
+    lib.amg_setup.argtypes = [C.POINTER(AmgCsr), C.POINTER(AmgParams), P, C.POINTER(P)]
+    lib.amg_setup.restype = I
+    lib.amg_set_mode.argtypes = [P, I]
+    lib.amg_set_mode.restype = I
+    lib.pcg_solve.argtypes = [P, P, P, D, I, C.POINTER(I), P, P]
+    lib.pcg_solve.restype = I
+    lib.amg_last_true_residual.argtypes = [P]
+    lib.amg_last_true_residual.restype = D
+    lib.amg_info.argtypes = [P, C.POINTER(I), P, P]
+    lib.amg_info.restype = I
+    lib.amg_level_agg.argtypes = [P, I, I, P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.amg_level_agg.restype = I
+    lib.amg_level_csr.argtypes = [P, I, P, P, P]
+    lib.amg_level_csr.restype = I
+    lib.amg_setup_times.argtypes = [P, P]
+    lib.amg_setup_times.restype = I
+    lib.amg_profile.argtypes = [P, I]
+    lib.amg_profile.restype = I
+    lib.amg_profile_read.argtypes = [P, P, P, I]
+    lib.amg_profile_read.restype = I
+    lib.amg_launch_count.argtypes = [P]
+    lib.amg_launch_count.restype = C.c_int64
+    lib.amg_destroy.argtypes = [P]
+    lib.amg_destroy.restype = None
+    lib.amg_last_error.argtypes = []
+    lib.amg_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class AmgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def last_error() -> str:
+    return load().amg_last_error().decode()
+
+
+# ------------------------------------------------------------ torch glue
+_torch_alloc_refs = None
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route the library's device allocations through torch's caching allocator."""
+    global _torch_alloc_refs
+    lib = load()
+    if not enable:
+        lib.amg_set_allocator(None, None, None)
+        _torch_alloc_refs = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            dev = torch.cuda.current_device()
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    refs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    st = lib.amg_set_allocator(C.cast(refs[0], C.c_void_p), C.cast(refs[1], C.c_void_p), None)
+    if st:
+        raise AmgError(st, last_error())
+    _torch_alloc_refs = refs
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream or None
+        except Exception:
+            return None
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _ptr(a, dtype):
+    """Pointer of a numpy array or torch tensor (contiguous, given dtype)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected contiguous {dtype} array")
+        return a.ctypes.data, False
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise TypeError("expected a contiguous tensor")
+        return a.data_ptr(), a.is_cuda
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+@dataclasses.dataclass
+class SolveResult:
+    status: int
+    iters: int
+    hist: np.ndarray
+    true_rel: float
+    message: str
+
+
+class AMG:
+    """A resident AMG hierarchy (``amg_setup``) and its solves (``pcg_solve``)."""
+
+    def __init__(self, row_ptr, col, val, n: int | None = None, coarse_max: int = 200, n_pass: int = 2,
+                 max_levels: int = 30, mode: str = "pcg64", hbm_budget: int = 0, stream=None):
+        lib = load()
+        rp, rp_dev = _ptr(row_ptr, np.int32)
+        ci, ci_dev = _ptr(col, np.int32)
+        v, v_dev = _ptr(val, np.float64)
+        if not (rp_dev == ci_dev == v_dev):
+            raise TypeError("CSR arrays must all be host or all device")
+        nrows = (len(row_ptr) - 1) if n is None else n
+        nnz = len(col)
+        csr = AmgCsr(nrows, nnz, rp, ci, v, int(rp_dev))
+        prm = AmgParams()
+        lib.amg_default_params(C.byref(prm))
+        prm.coarse_max, prm.n_pass, prm.max_levels = coarse_max, n_pass, max_levels
+        prm.mode, prm.hbm_budget = _MODES[mode], hbm_budget
+        h = C.c_void_p()
+        st = lib.amg_setup(C.byref(csr), C.byref(prm), _stream_ptr(stream), C.byref(h))
+        if st:
+            raise AmgError(st, last_error())
+        self._h = h
+        self.n = nrows
+        self.mode = mode
+
+    @classmethod
+    def from_csr(cls, A, **kw):
+        return cls(A.row_ptr, A.col, A.val, n=A.n, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().amg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_mode(self, mode: str):
+        st = load().amg_set_mode(self._h, _MODES[mode])
+        if st:
+            raise AmgError(st, last_error())
+        self.mode = mode
+
+    def solve(self, b, x, rtol: float = 1e-8, maxit: int = 1000, stream=None, hist: bool = True,
+              check: bool = False) -> SolveResult:
+        """``pcg_solve``: x (in: initial guess, out: solution) is updated in place."""
+        lib = load()
+        bp, _ = _ptr(b, np.float64)
+        xp, _ = _ptr(x, np.float64)
+        h = np.zeros(maxit + 1) if hist else None
+        it = C.c_int(0)
+        st = lib.pcg_solve(self._h, bp, xp, rtol, maxit, C.byref(it),
+                           h.ctypes.data if hist else None, _stream_ptr(stream))
+        msg = last_error() if st else ""
+        if check and st:
+            raise AmgError(st, msg)
+        return SolveResult(st, it.value, h[: it.value + 1] if hist else None,
+                           lib.amg_last_true_residual(self._h), msg)
+
+    def info(self):
+        lib = load()
+        L = C.c_int(0)
+        lib.amg_info(self._h, C.byref(L), None, None)
+        n = np.zeros(L.value, np.int64)
+        z = np.zeros(L.value, np.int64)
+        lib.amg_info(self._h, C.byref(L), n.ctypes.data, z.ctypes.data)
+        return list(zip(n.tolist(), z.tolist()))
+
+    def level_agg(self, level: int, ps: int = -1):
+        lib = load()
+        n, nc = C.c_int64(), C.c_int64()
+        st = lib.amg_level_agg(self._h, level, ps, None, C.byref(n), C.byref(nc))
+        if st:
+            raise AmgError(st, last_error())
+        a = np.empty(n.value, np.int32)
+        st = lib.amg_level_agg(self._h, level, ps, a.ctypes.data, C.byref(n), C.byref(nc))
+        if st:
+            raise AmgError(st, last_error())
+        return a, nc.value
+
+    def level_csr(self, level: int):
+        n, z = self.info()[level]
+        rp = np.empty(n + 1, np.int32)
+        ci = np.empty(z, np.int32)
+        v = np.empty(z)
+        st = load().amg_level_csr(self._h, level, rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+        if st:
+            raise AmgError(st, last_error())
+        return rp, ci, v
+
+    KINDS = ("down0", "up0", "spmv", "update", "residual", "coarse_levels")
+
+    def profile(self, enable: bool = True):
+        st = load().amg_profile(self._h, int(enable))
+        if st:
+            raise AmgError(st, last_error())
+
+    def profile_read(self) -> dict:
+        ms = np.zeros(6)
+        cnt = np.zeros(6, np.int64)
+        load().amg_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, 6)
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KINDS)}
+
+    def launch_count(self) -> int:
+        return int(load().amg_launch_count(self._h))
+
+    def setup_times(self):
+        ms = np.zeros(4)
+        load().amg_setup_times(self._h, ms.ctypes.data)
+        return {"total_ms": ms[0], "matching_ms": ms[1], "galerkin_ms": ms[2], "other_ms": ms[3]}

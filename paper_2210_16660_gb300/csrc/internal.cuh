@@ -1,0 +1,161 @@
+// Internal declarations shared by the CUDA sources of libpcgamg.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "pcgamg.h"
+
+namespace pcgamg {
+
+constexpr int kSlice = 32;        // sliced-ELL slice height (one warp)
+constexpr int kBlock = 256;       // threads per block of the streaming kernels
+constexpr int kDenseMax = 4096;   // largest coarsest level solved densely
+constexpr int kMaxPass = 8;
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define PCG_CK(call)                                                        \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess)                                              \
+            return ::pcgamg::cuda_fail(e_, #call, __FILE__, __LINE__);      \
+    } while (0)
+#define PCG_TRY(x)              \
+    do {                        \
+        int s_ = (x);           \
+        if (s_) return s_;      \
+    } while (0)
+#define PCG_LAUNCH_CK() PCG_CK(cudaGetLastError())
+
+// -------------------------------------------------------------- allocator
+// Device allocations of one handle: every pointer is tracked with its size
+// so the handle can free everything and enforce its byte budget.
+struct Mem {
+    cudaStream_t stream = nullptr;
+    size_t bytes = 0, peak = 0, budget = 0;
+    std::unordered_map<void *, size_t> live;
+    int alloc_bytes(void **p, size_t bytes);
+    void release(void *p);
+    void release_all();
+};
+
+template <class T>
+inline int alloc(Mem &m, T **p, size_t count) {
+    return m.alloc_bytes(reinterpret_cast<void **>(p), (count > 0 ? count : 1) * sizeof(T));
+}
+template <class T>
+inline void release(Mem &m, T *&p) {
+    if (p) m.release(p);
+    p = nullptr;
+}
+
+// ------------------------------------------------------------ data layout
+struct DevCSR {
+    int n = 0;
+    int64_t nnz = 0;
+    int32_t *rp = nullptr, *ci = nullptr;
+    double *v = nullptr;
+};
+
+// Sliced ELL with slice height 32: entry k of row 32*s + lane lives at
+// sptr[s] + 32*k + lane; rows shorter than the slice width are padded with
+// their own index and a zero value. One warp streams one slice.
+struct Sell {
+    int n = 0, nslices = 0;
+    int64_t nnz_pad = 0;
+    int32_t *sptr = nullptr;   // nslices + 1 element offsets
+    int32_t *col = nullptr;
+    double *v64 = nullptr;
+    float *v32 = nullptr;
+};
+
+struct Level {
+    DevCSR A;
+    Sell S;
+    double *dinv = nullptr;   // 1 / sum_j |a_ij|
+    float *dinv32 = nullptr;
+    double *w = nullptr;      // the vector w of this level
+    // transfer to level l+1 (unused on the coarsest level)
+    int nc = 0;
+    int32_t *agg = nullptr;   // composed aggregate map, -1 = left out
+    double *p = nullptr;      // composed tentative-prolongator weight
+    float *p32 = nullptr;
+    int32_t *rptr = nullptr;  // members of each coarse row: rptr[nc+1], ridx[...]
+    int32_t *ridx = nullptr;
+    std::vector<int32_t *> pass_agg;
+    std::vector<int> pass_n;  // rows entering pass k; pass_n[npass] = nc
+    // V-cycle work vectors: right-hand side, solution, restricted residual
+    double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr;
+    float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr;
+};
+
+// Device-resident Krylov state; every scalar of the iteration lives here so
+// that an iteration needs no host round trip.
+struct Ctl {
+    double bnorm;        // ||b||
+    double rho, rho_old; // r.z
+    double pq, pq_old;   // p.Ap
+    double zq;           // z . q_old (FCG)
+    double alpha, beta;
+    double rel;          // ||r|| / ||b|| of the last update
+    double true_rel;     // ||b - A x|| / ||b|| of the last check
+    double rtol;
+    int iter;            // V-cycles applied
+    int maxit;
+    int mode;
+    int restart;         // next direction is p = z
+    int check;           // recursive residual met rtol: form the true one
+    int done;            // 1 converged, 2 error
+    int status;          // AMG_* code once done
+    int pad;
+    unsigned int counter[8];  // last-block-done counters of the reducing kernels
+};
+
+}  // namespace pcgamg
+
+struct amg_hier {
+    int device = 0;
+    int mode = AMG_MODE_PCG64;
+    amg_params prm{};
+    pcgamg::Mem mem;
+    std::vector<pcgamg::Level> lev;
+    int nL = 0;
+    double *Ainv = nullptr;   // inverse of the coarsest matrix, row-major
+    double *bL = nullptr;     // coarsest right-hand side in float64
+    // Krylov workspace (level-0 length)
+    double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr;
+    double *pv[2] = {nullptr, nullptr};
+    double *partials = nullptr;  // per-block partial sums (several slots)
+    double *hist = nullptr;      // device history, maxit_cap + 1
+    int hist_cap = 0;
+    pcgamg::Ctl *ctl = nullptr;
+    pcgamg::Ctl *ctl_host = nullptr;  // pinned mirror
+    int nblk = 0;                // blocks of the level-0 reducing kernels
+    double last_true_rel = 0.0;
+    double setup_ms[4] = {0, 0, 0, 0};
+    // kernel timing (amg_profile)
+    static constexpr int kKinds = 6;
+    int profile = 0;
+    std::vector<cudaEvent_t> ev;      // pool: pairs per kind per iteration of a chunk
+    int ev_used = 0;
+    int ev_kind[256] = {0};
+    double prof_ms[kKinds] = {0};
+    int64_t prof_n[kKinds] = {0};
+    int64_t launches = 0;
+};
+
+namespace pcgamg {
+int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_t s);
+int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, int *iters,
+               double *res_hist, cudaStream_t s);
+int alloc_solve_workspace(amg_hier *h);
+int set_profile(amg_hier *h, int enable);
+void free_profile(amg_hier *h);
+}  // namespace pcgamg

@@ -1,0 +1,835 @@
+// Device-side construction of the AMG hierarchy (arxiv 2210.16660, Sec. 3.1).
+//
+// Per level: n_pass pairwise passes of {edge weights of Eq. (weights) ->
+// matching (Eq. approximatematch) -> pair/singleton aggregates and the
+// tentative prolongator of Eq. (prolongator) -> Galerkin product P^T A P};
+// the composed map and weight of the passes define the level's transfer.
+// Then l1 diagonals, sliced-ELL copies in float64/float32, and the dense
+// inverse of the coarsest matrix.
+//
+// Floating-point steps whose results decide integers (the edge weights that
+// order the matching) and the values feeding them (Galerkin products,
+// prolongator weights) use explicitly rounded operations (__dmul_rn etc.),
+// never a fused multiply-add, in the order stated at each kernel, so the
+// aggregates are reproducible bit for bit by any IEEE implementation that
+// follows the same order.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+
+#include "internal.cuh"
+
+namespace pcgamg {
+
+namespace {
+
+inline int grid_for(int64_t n, int block = kBlock) {
+    int64_t g = (n + block - 1) / block;
+    return (int)(g > 0 ? g : 1);
+}
+
+// ------------------------------------------------------------ prefix sums
+// Exclusive scan of n values into out[0..n], out[n] = total.
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename Tin, typename T>
+__global__ void k_scan_tiles(const Tin *__restrict__ in, T *__restrict__ out, T *__restrict__ tsum,
+                             int64_t n) {
+    __shared__ T sh[kScanThreads];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T v[kScanItems];
+    T loc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + k;
+        v[k] = i < n ? (T)in[i] : (T)0;
+        loc += v[k];
+    }
+    sh[threadIdx.x] = loc;
+    __syncthreads();
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        T a = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : (T)0;
+        __syncthreads();
+        sh[threadIdx.x] += a;
+        __syncthreads();
+    }
+    T ex = sh[threadIdx.x] - loc;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t i = base + k;
+        if (i < n) out[i] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == kScanThreads - 1) tsum[blockIdx.x] = sh[kScanThreads - 1];
+}
+
+template <typename T>
+__global__ void k_scan_tile_sums(T *tsum, int64_t nt, T *total) {
+    __shared__ T sh[1024];
+    __shared__ T carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t c = 0; c < nt; c += 1024) {
+        int64_t i = c + threadIdx.x;
+        T v = i < nt ? tsum[i] : (T)0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            T a = threadIdx.x >= (unsigned)off ? sh[threadIdx.x - off] : (T)0;
+            __syncthreads();
+            sh[threadIdx.x] += a;
+            __syncthreads();
+        }
+        if (i < nt) tsum[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += sh[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+template <typename T>
+__global__ void k_scan_add(T *__restrict__ out, const T *__restrict__ tsum, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tsum[i / kScanTile];
+}
+
+// out must hold n + 1 values. *total_host receives out[n] (synchronises).
+template <typename Tin, typename T>
+int scan_exclusive(Mem &M, const Tin *in, T *out, int64_t n, T *total_host, cudaStream_t s) {
+    int64_t nt = (n + kScanTile - 1) / kScanTile;
+    if (nt < 1) nt = 1;
+    T *tsum = nullptr;
+    PCG_TRY(alloc(M, &tsum, (size_t)nt));
+    k_scan_tiles<Tin, T><<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, tsum, n);
+    k_scan_tile_sums<T><<<1, 1024, 0, s>>>(tsum, nt, out + n);
+    if (n > 0) k_scan_add<T><<<grid_for(n), kBlock, 0, s>>>(out, tsum, n);
+    PCG_LAUNCH_CK();
+    if (total_host) {
+        PCG_CK(cudaMemcpyAsync(total_host, out + n, sizeof(T), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaStreamSynchronize(s));
+    }
+    release(M, tsum);
+    return AMG_OK;
+}
+
+// ------------------------------------------------------------ validation
+// flag bits: 1 column out of range or unsorted, 2 diagonal missing or <= 0,
+// 4 row pointer decreasing or wrong bounds, 8 not exactly symmetric.
+__global__ void k_check_csr(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, int64_t nnz, int *flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t s = rp[i], e = rp[i + 1];
+    if (e < s || s < 0 || (int64_t)e > nnz || (i == 0 && s != 0) || (i == n - 1 && (int64_t)e != nnz)) {
+        atomicOr(flag, 4);
+        return;
+    }
+    int has = 0;
+    for (int32_t k = s; k < e; k++) {
+        int32_t j = ci[k];
+        if (j < 0 || j >= n || (k > s && j <= ci[k - 1])) atomicOr(flag, 1);
+        if (j == i) has = v[k] > 0.0 ? 1 : -1;
+    }
+    if (has != 1) atomicOr(flag, 2);
+}
+
+__global__ void k_check_sym(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, int *flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+        int32_t j = ci[k];
+        if (j <= i) continue;
+        int32_t lo = rp[j], hi = rp[j + 1] - 1, hit = -1;
+        while (lo <= hi) {
+            int32_t mid = (lo + hi) >> 1;
+            int32_t c = ci[mid];
+            if (c == i) { hit = mid; break; }
+            if (c < i) lo = mid + 1; else hi = mid - 1;
+        }
+        if (hit < 0 || __double_as_longlong(v[hit]) != __double_as_longlong(v[k])) {
+            atomicOr(flag, 8);
+            return;
+        }
+    }
+}
+
+// ------------------------------------------------------------ small fills
+template <typename T>
+__global__ void k_fill(T *a, int64_t n, T val) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = val;
+}
+
+__global__ void k_iota(int32_t *a, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = i;
+}
+
+__global__ void k_diag(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                       const double *__restrict__ v, double *__restrict__ dg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; k++)
+        if (ci[k] == i) { d = v[k]; break; }
+    dg[i] = d;
+}
+
+// ------------------------------------------------------------ matching
+// Eq. (weights) for edge {a, b}, a < b, evaluated as
+// 1 - ((2 a_ab) w_a) w_b / ((a_aa w_a) w_a + (a_bb w_b) w_b), every step rounded.
+__device__ __forceinline__ double edge_weight(double aab, double aaa, double abb, double wa, double wb) {
+    double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, aab), wa), wb);
+    double den = __dadd_rn(__dmul_rn(__dmul_rn(aaa, wa), wa), __dmul_rn(__dmul_rn(abb, wb), wb));
+    return __dsub_rn(1.0, __ddiv_rn(num, den));
+}
+
+// Strict total order on candidate edges: larger weight first, then smaller
+// (min, max) endpoint pair.
+__device__ __forceinline__ bool edge_before(double c1, int a1, int b1, double c2, int a2, int b2) {
+    if (c1 != c2) return c1 > c2;
+    if (a1 != a2) return a1 < a2;
+    return b1 < b2;
+}
+
+// One round of the locally-dominant matching, part 1: every free vertex
+// points at its first candidate edge (c > 1) to another free vertex.
+__global__ void k_match_cand(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const double *__restrict__ v, const double *__restrict__ dg,
+                             const double *__restrict__ w, const int32_t *__restrict__ mate,
+                             int32_t *__restrict__ cand, int *any) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (mate[i] >= 0) { cand[i] = -1; return; }
+    double bc = 0.0;
+    int bj = -1, ba = 0, bb = 0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+        int j = ci[k];
+        if (j == i || mate[j] >= 0) continue;
+        int a = min(i, j), b = max(i, j);
+        double c = edge_weight(v[k], dg[a], dg[b], w[a], w[b]);
+        if (!(c > 1.0)) continue;
+        if (bj < 0 || edge_before(c, a, b, bc, ba, bb)) { bc = c; bj = j; ba = a; bb = b; }
+    }
+    cand[i] = bj;
+    if (bj >= 0) *any = 1;
+}
+
+// Part 2: mutual pointers are locally dominant edges; take them.
+__global__ void k_match_commit(int n, const int32_t *__restrict__ cand, int32_t *__restrict__ mate) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (mate[i] >= 0) return;
+    int j = cand[i];
+    if (j >= 0 && cand[j] == i) mate[i] = j;
+}
+
+// ------------------------------------------------------------ aggregates
+// lead[i] = 1 when i opens an aggregate: a singleton that has a nonzero
+// off-diagonal entry, or the smaller end of a matched pair. Unmatched rows
+// without nonzero couplings are left out of the coarse space.
+__global__ void k_leaders(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ v, const int32_t *__restrict__ mate,
+                          int32_t *__restrict__ lead) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int m = mate[i];
+    if (m >= 0) { lead[i] = i < m ? 1 : 0; return; }
+    int iso = 1;
+    for (int32_t k = rp[i]; k < rp[i + 1]; k++)
+        if (ci[k] != i && v[k] != 0.0) { iso = 0; break; }
+    lead[i] = iso ? 0 : 1;
+}
+
+// Eq. (prolongator): pair weights w_e = (w_i, w_j) / ||(w_i, w_j)||, singleton
+// weight w_s / |w_s|; coarse w_c = ||w restricted to the aggregate||.
+__global__ void k_assign(int n, const int32_t *__restrict__ mate, const int32_t *__restrict__ lead,
+                         const int32_t *__restrict__ idx, const double *__restrict__ w,
+                         int32_t *__restrict__ agg, double *__restrict__ p, double *__restrict__ wc,
+                         int32_t *__restrict__ mem0, int32_t *__restrict__ mem1) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int j = mate[i];
+    if (!lead[i]) {
+        if (j < 0) { agg[i] = -1; p[i] = 0.0; }
+        return;
+    }
+    int I = idx[i];
+    double wi = w[i];
+    if (j >= 0) {
+        double wj = w[j];
+        double nrm = __dsqrt_rn(__dadd_rn(__dmul_rn(wi, wi), __dmul_rn(wj, wj)));
+        agg[i] = I; agg[j] = I;
+        p[i] = __ddiv_rn(wi, nrm);
+        p[j] = __ddiv_rn(wj, nrm);
+        wc[I] = nrm;
+        mem0[I] = i; mem1[I] = j;
+    } else {
+        double a = fabs(wi);
+        agg[i] = I;
+        p[i] = __ddiv_rn(wi, a);
+        wc[I] = a;
+        mem0[I] = i; mem1[I] = -1;
+    }
+}
+
+// ------------------------------------------------------------ Galerkin product
+__global__ void k_rap_count(int nc, const int32_t *__restrict__ mem0, const int32_t *__restrict__ mem1,
+                            const int32_t *__restrict__ rp, int32_t *__restrict__ cnt) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int i0 = mem0[I], i1 = mem1[I];
+    int c = rp[i0 + 1] - rp[i0];
+    if (i1 >= 0) c += rp[i1 + 1] - rp[i1];
+    cnt[I] = c;
+}
+
+// Coarse row I of P^T A P for a pairwise aggregation: every stored a_ij with
+// i in G_I and agg(j) >= 0 contributes t = a_ij * (p_i * p_j) to entry
+// (I, agg(j)); contributions to one entry are added in increasing order of
+// (min(i,j), max(i,j)). Terms are kept sorted by (J, min, max) in the row's
+// scratch segment (insertion sort, stable), then runs are summed in place.
+__global__ void k_rap_terms(int nc, const int32_t *__restrict__ mem0, const int32_t *__restrict__ mem1,
+                            const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, const int32_t *__restrict__ agg,
+                            const double *__restrict__ p, const int32_t *__restrict__ off,
+                            int32_t *__restrict__ tJ, unsigned long long *__restrict__ tK,
+                            double *__restrict__ tT, int32_t *__restrict__ ucnt) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int32_t base = off[I];
+    int m = 0;
+    int mem[2] = {mem0[I], mem1[I]};
+    for (int q = 0; q < 2; q++) {
+        int i = mem[q];
+        if (i < 0) break;
+        double pi = p[i];
+        for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+            int j = ci[k];
+            int J = agg[j];
+            if (J < 0) continue;
+            unsigned long long key = ((unsigned long long)(unsigned)min(i, j) << 32) |
+                                     (unsigned long long)(unsigned)max(i, j);
+            double t = __dmul_rn(v[k], __dmul_rn(pi, p[j]));
+            int32_t pos = base + m;
+            while (pos > base && (tJ[pos - 1] > J || (tJ[pos - 1] == J && tK[pos - 1] > key))) {
+                tJ[pos] = tJ[pos - 1];
+                tK[pos] = tK[pos - 1];
+                tT[pos] = tT[pos - 1];
+                pos--;
+            }
+            tJ[pos] = J; tK[pos] = key; tT[pos] = t;
+            m++;
+        }
+    }
+    int u = 0;
+    for (int q = 0; q < m; q++) {
+        int32_t J = tJ[base + q];
+        double t = tT[base + q];
+        if (u == 0 || J != tJ[base + u - 1]) {
+            tJ[base + u] = J;
+            tT[base + u] = t;
+            u++;
+        } else {
+            tT[base + u - 1] = __dadd_rn(tT[base + u - 1], t);
+        }
+    }
+    ucnt[I] = u;
+}
+
+__global__ void k_rap_copy(int nc, const int32_t *__restrict__ off, const int32_t *__restrict__ rpc,
+                           const int32_t *__restrict__ tJ, const double *__restrict__ tT,
+                           int32_t *__restrict__ cic, double *__restrict__ vc) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int32_t o = off[I], s = rpc[I], e = rpc[I + 1];
+    for (int32_t q = 0; q < e - s; q++) {
+        cic[s + q] = tJ[o + q];
+        vc[s + q] = tT[o + q];
+    }
+}
+
+// Product of the pass maps and weights, in pass order.
+__global__ void k_compose(int n, int32_t *__restrict__ cagg, double *__restrict__ cp,
+                          const int32_t *__restrict__ agg, const double *__restrict__ p) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = cagg[i];
+    double c = cp[i];
+    if (a >= 0) {
+        c = __dmul_rn(c, p[a]);
+        a = agg[a];
+    }
+    if (a < 0) c = 0.0;
+    cagg[i] = a;
+    cp[i] = c;
+}
+
+// ------------------------------------------------------------ level data
+// l1 smoother diagonal d_i = sum_j |a_ij| (row order), stored inverted.
+__global__ void k_l1diag(int n, const int32_t *__restrict__ rp, const double *__restrict__ v,
+                         double *__restrict__ dinv, float *__restrict__ dinv32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; k++) s = __dadd_rn(s, fabs(v[k]));
+    double d = __ddiv_rn(1.0, s);
+    dinv[i] = d;
+    dinv32[i] = __double2float_rn(d);
+}
+
+__global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __double2float_rn(a[i]);
+}
+
+__global__ void k_sell_width(int n, int nsl, const int32_t *__restrict__ rp, int32_t *__restrict__ sw) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsl) return;
+    int r0 = s * kSlice, r1 = min(r0 + kSlice, n);
+    int mx = 0;
+    for (int r = r0; r < r1; r++) mx = max(mx, rp[r + 1] - rp[r]);
+    sw[s] = mx * kSlice;
+}
+
+__global__ void k_sell_fill(int n, int nsl, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, const int32_t *__restrict__ sptr,
+                            int32_t *__restrict__ col, double *__restrict__ v64, float *__restrict__ v32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nsl * kSlice) return;
+    int s = i / kSlice, lane = i % kSlice;
+    int32_t base = sptr[s];
+    int w = (sptr[s + 1] - base) / kSlice;
+    int len = i < n ? rp[i + 1] - rp[i] : 0;
+    int32_t r0 = i < n ? rp[i] : 0;
+    int pad = i < n ? i : 0;
+    for (int k = 0; k < w; k++) {
+        int32_t e = base + k * kSlice + lane;
+        if (k < len) {
+            double a = v[r0 + k];
+            col[e] = ci[r0 + k];
+            v64[e] = a;
+            v32[e] = __double2float_rn(a);
+        } else {
+            col[e] = pad;
+            v64[e] = 0.0;
+            v32[e] = 0.0f;
+        }
+    }
+}
+
+__global__ void k_count_members(int n, const int32_t *__restrict__ agg, int32_t *__restrict__ cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (agg[i] >= 0) atomicAdd(&cnt[agg[i]], 1);
+}
+
+__global__ void k_fill_members(int n, const int32_t *__restrict__ agg, const int32_t *__restrict__ rptr,
+                               int32_t *__restrict__ cur, int32_t *__restrict__ ridx) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = agg[i];
+    if (a < 0) return;
+    int pos = atomicAdd(&cur[a], 1);
+    ridx[rptr[a] + pos] = i;
+}
+
+__global__ void k_sort_members(int nc, const int32_t *__restrict__ rptr, int32_t *__restrict__ ridx) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int32_t s = rptr[I], e = rptr[I + 1];
+    for (int32_t a = s + 1; a < e; a++) {
+        int32_t x = ridx[a];
+        int32_t b = a;
+        while (b > s && ridx[b - 1] > x) { ridx[b] = ridx[b - 1]; b--; }
+        ridx[b] = x;
+    }
+}
+
+// ------------------------------------------------------------ coarsest level
+__global__ void k_dense(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                        const double *__restrict__ v, double *__restrict__ ad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t k = rp[i]; k < rp[i + 1]; k++) ad[(int64_t)i * n + ci[k]] = v[k];
+}
+
+// In-place Cholesky (lower triangle, row-major) by one block; flag = 1 when
+// a pivot is not positive.
+__global__ void k_chol(int n, double *a, int *flag) {
+    __shared__ double red[1024];
+    __shared__ double piv;
+    for (int j = 0; j < n; j++) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < j; k += blockDim.x) s += a[(int64_t)j * n + k] * a[(int64_t)j * n + k];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < (unsigned)o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            double d = a[(int64_t)j * n + j] - red[0];
+            if (!(d > 0.0)) { *flag = 1; d = 1.0; }
+            piv = sqrt(d);
+            a[(int64_t)j * n + j] = piv;
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            double t = a[(int64_t)i * n + j];
+            for (int k = 0; k < j; k++) t -= a[(int64_t)i * n + k] * a[(int64_t)j * n + k];
+            a[(int64_t)i * n + j] = t / piv;
+        }
+        __syncthreads();
+    }
+}
+
+// Column c of A^{-1} = L^{-T} L^{-1} e_c by one block per column.
+__global__ void k_chol_inverse(int n, const double *__restrict__ L, double *__restrict__ ainv) {
+    extern __shared__ double y[];
+    int c = blockIdx.x;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) y[k] = k == c ? 1.0 : 0.0;
+    __syncthreads();
+    for (int i = 0; i < n; i++) {           // L y = e_c
+        double yi = y[i] / L[(int64_t)i * n + i];
+        __syncthreads();
+        if (threadIdx.x == 0) y[i] = yi;
+        for (int k = i + 1 + threadIdx.x; k < n; k += blockDim.x) y[k] -= L[(int64_t)k * n + i] * yi;
+        __syncthreads();
+    }
+    for (int i = n - 1; i >= 0; i--) {      // L^T x = y
+        double xi = y[i] / L[(int64_t)i * n + i];
+        __syncthreads();
+        if (threadIdx.x == 0) y[i] = xi;
+        for (int k = threadIdx.x; k < i; k += blockDim.x) y[k] -= L[(int64_t)i * n + k] * xi;
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < n; k += blockDim.x) ainv[(int64_t)k * n + c] = y[k];
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int read_flag(int *dflag, cudaStream_t s, int *out) {
+    PCG_CK(cudaMemcpyAsync(out, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PCG_CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+void free_csr(Mem &M, DevCSR &a) {
+    release(M, a.rp);
+    release(M, a.ci);
+    release(M, a.v);
+}
+
+// One pairwise pass on cur (weights w): fills agg/p of the pass, the coarse
+// matrix nxt and its w. Returns AMG_OK or an error.
+int pairwise_pass(amg_hier *h, const DevCSR &cur, const double *w, int32_t **agg_out, double **p_out,
+                  DevCSR *nxt, double **wc_out, double *t_match, double *t_rap, cudaStream_t s) {
+    Mem &M = h->mem;
+    int m = cur.n;
+    double *dg = nullptr, *p = nullptr, *wc = nullptr;
+    int32_t *mate = nullptr, *cand = nullptr, *lead = nullptr, *idx = nullptr, *agg = nullptr;
+    int32_t *mem0 = nullptr, *mem1 = nullptr;
+    int *dflag = nullptr;
+    PCG_TRY(alloc(M, &dg, m));
+    PCG_TRY(alloc(M, &mate, m));
+    PCG_TRY(alloc(M, &cand, m));
+    PCG_TRY(alloc(M, &dflag, 1));
+    double t0 = now_ms();
+    k_diag<<<grid_for(m), kBlock, 0, s>>>(m, cur.rp, cur.ci, cur.v, dg);
+    k_fill<int32_t><<<grid_for(m), kBlock, 0, s>>>(mate, m, -1);
+    PCG_LAUNCH_CK();
+    for (int round = 0;; round++) {
+        PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+        k_match_cand<<<grid_for(m), kBlock, 0, s>>>(m, cur.rp, cur.ci, cur.v, dg, w, mate, cand, dflag);
+        k_match_commit<<<grid_for(m), kBlock, 0, s>>>(m, cand, mate);
+        PCG_LAUNCH_CK();
+        int any = 0;
+        PCG_TRY(read_flag(dflag, s, &any));
+        if (!any) break;
+        if (round >= 20000) {
+            set_error("matching did not finish in 20000 rounds");
+            return AMG_ERR_CUDA;
+        }
+    }
+    release(M, cand);
+    release(M, dg);
+    *t_match += now_ms() - t0;
+    t0 = now_ms();
+    PCG_TRY(alloc(M, &lead, m));
+    PCG_TRY(alloc(M, &idx, (size_t)m + 1));
+    k_leaders<<<grid_for(m), kBlock, 0, s>>>(m, cur.rp, cur.ci, cur.v, mate, lead);
+    PCG_LAUNCH_CK();
+    int32_t nc = 0;
+    PCG_TRY(scan_exclusive(M, lead, idx, m, &nc, s));
+    PCG_TRY(alloc(M, &agg, m));
+    PCG_TRY(alloc(M, &p, m));
+    PCG_TRY(alloc(M, &wc, nc));
+    PCG_TRY(alloc(M, &mem0, nc));
+    PCG_TRY(alloc(M, &mem1, nc));
+    k_assign<<<grid_for(m), kBlock, 0, s>>>(m, mate, lead, idx, w, agg, p, wc, mem0, mem1);
+    PCG_LAUNCH_CK();
+    release(M, lead);
+    release(M, idx);
+    release(M, mate);
+
+    // Galerkin product
+    int32_t *cnt = nullptr, *off = nullptr, *ucnt = nullptr, *tJ = nullptr;
+    unsigned long long *tK = nullptr;
+    double *tT = nullptr;
+    PCG_TRY(alloc(M, &cnt, nc));
+    PCG_TRY(alloc(M, &off, (size_t)nc + 1));
+    k_rap_count<<<grid_for(nc), kBlock, 0, s>>>(nc, mem0, mem1, cur.rp, cnt);
+    PCG_LAUNCH_CK();
+    int32_t nterm = 0;
+    PCG_TRY(scan_exclusive(M, cnt, off, nc, &nterm, s));
+    release(M, cnt);
+    PCG_TRY(alloc(M, &tJ, nterm));
+    PCG_TRY(alloc(M, &tK, nterm));
+    PCG_TRY(alloc(M, &tT, nterm));
+    PCG_TRY(alloc(M, &ucnt, nc));
+    k_rap_terms<<<grid_for(nc, 128), 128, 0, s>>>(nc, mem0, mem1, cur.rp, cur.ci, cur.v, agg, p, off, tJ,
+                                                   tK, tT, ucnt);
+    PCG_LAUNCH_CK();
+    DevCSR c;
+    c.n = nc;
+    PCG_TRY(alloc(M, &c.rp, (size_t)nc + 1));
+    int32_t nzc = 0;
+    PCG_TRY(scan_exclusive(M, ucnt, c.rp, nc, &nzc, s));
+    c.nnz = nzc;
+    PCG_TRY(alloc(M, &c.ci, nzc));
+    PCG_TRY(alloc(M, &c.v, nzc));
+    k_rap_copy<<<grid_for(nc), kBlock, 0, s>>>(nc, off, c.rp, tJ, tT, c.ci, c.v);
+    PCG_LAUNCH_CK();
+    PCG_CK(cudaStreamSynchronize(s));
+    release(M, tJ);
+    release(M, tK);
+    release(M, tT);
+    release(M, ucnt);
+    release(M, off);
+    release(M, mem0);
+    release(M, mem1);
+    release(M, dflag);
+    *t_rap += now_ms() - t0;
+    *agg_out = agg;
+    *p_out = p;
+    *nxt = c;
+    *wc_out = wc;
+    return AMG_OK;
+}
+
+int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
+    Mem &M = h->mem;
+    int n = lv.A.n;
+    PCG_TRY(alloc(M, &lv.dinv, n));
+    PCG_TRY(alloc(M, &lv.dinv32, n));
+    k_l1diag<<<grid_for(n), kBlock, 0, s>>>(n, lv.A.rp, lv.A.v, lv.dinv, lv.dinv32);
+    PCG_LAUNCH_CK();
+    // sliced ELL
+    Sell &S = lv.S;
+    S.n = n;
+    S.nslices = (n + kSlice - 1) / kSlice;
+    int32_t *sw = nullptr;
+    PCG_TRY(alloc(M, &sw, S.nslices));
+    PCG_TRY(alloc(M, &S.sptr, (size_t)S.nslices + 1));
+    k_sell_width<<<grid_for(S.nslices), kBlock, 0, s>>>(n, S.nslices, lv.A.rp, sw);
+    PCG_LAUNCH_CK();
+    int32_t tot = 0;
+    PCG_TRY(scan_exclusive(M, sw, S.sptr, S.nslices, &tot, s));
+    release(M, sw);
+    S.nnz_pad = tot;
+    PCG_TRY(alloc(M, &S.col, tot));
+    PCG_TRY(alloc(M, &S.v64, tot));
+    PCG_TRY(alloc(M, &S.v32, tot));
+    k_sell_fill<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(n, S.nslices, lv.A.rp, lv.A.ci,
+                                                                         lv.A.v, S.sptr, S.col, S.v64, S.v32);
+    PCG_LAUNCH_CK();
+    // work vectors
+    PCG_TRY(alloc(M, &lv.b64, n));
+    PCG_TRY(alloc(M, &lv.x64, n));
+    PCG_TRY(alloc(M, &lv.t64, n));
+    PCG_TRY(alloc(M, &lv.b32, n));
+    PCG_TRY(alloc(M, &lv.x32, n));
+    PCG_TRY(alloc(M, &lv.t32, n));
+    if (!coarsest) {
+        PCG_TRY(alloc(M, &lv.p32, n));
+        k_to_f32<<<grid_for(n), kBlock, 0, s>>>(lv.p, lv.p32, n);
+        // members of each coarse row, increasing fine index
+        int32_t *cnt = nullptr, *cur = nullptr;
+        PCG_TRY(alloc(M, &cnt, lv.nc));
+        PCG_TRY(alloc(M, &cur, lv.nc));
+        PCG_TRY(alloc(M, &lv.rptr, (size_t)lv.nc + 1));
+        PCG_CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * lv.nc, s));
+        PCG_CK(cudaMemsetAsync(cur, 0, sizeof(int32_t) * lv.nc, s));
+        k_count_members<<<grid_for(n), kBlock, 0, s>>>(n, lv.agg, cnt);
+        PCG_LAUNCH_CK();
+        int32_t nm = 0;
+        PCG_TRY(scan_exclusive(M, cnt, lv.rptr, lv.nc, &nm, s));
+        PCG_TRY(alloc(M, &lv.ridx, nm));
+        k_fill_members<<<grid_for(n), kBlock, 0, s>>>(n, lv.agg, lv.rptr, cur, lv.ridx);
+        k_sort_members<<<grid_for(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx);
+        PCG_LAUNCH_CK();
+        PCG_CK(cudaStreamSynchronize(s));
+        release(M, cnt);
+        release(M, cur);
+    }
+    return AMG_OK;
+}
+
+}  // namespace
+
+int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_t s) {
+    double t_begin = now_ms(), t_match = 0, t_rap = 0;
+    Mem &M = h->mem;
+    M.stream = s;
+    M.budget = prm->hbm_budget;
+    h->prm = *prm;
+    h->mode = prm->mode;
+    if (!A || A->n <= 0 || A->n >= (int64_t)1 << 31 || A->nnz < A->n || A->nnz >= (int64_t)1 << 31 ||
+        !A->row_ptr || !A->col || !A->val) {
+        set_error("amg_setup: bad CSR sizes or NULL arrays");
+        return AMG_ERR_ARG;
+    }
+    if (prm->n_pass < 1 || prm->n_pass > kMaxPass || prm->coarse_max < 1 || prm->max_levels < 1 ||
+        (prm->mode != AMG_MODE_PCG64 && prm->mode != AMG_MODE_FCG32)) {
+        set_error("amg_setup: bad parameters");
+        return AMG_ERR_ARG;
+    }
+    int n = (int)A->n;
+    int64_t nnz = A->nnz;
+    h->lev.reserve((size_t)prm->max_levels + 1);
+    h->lev.emplace_back();
+    Level &l0 = h->lev[0];
+    l0.A.n = n;
+    l0.A.nnz = nnz;
+    PCG_TRY(alloc(M, &l0.A.rp, (size_t)n + 1));
+    PCG_TRY(alloc(M, &l0.A.ci, nnz));
+    PCG_TRY(alloc(M, &l0.A.v, nnz));
+    cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    PCG_CK(cudaMemcpyAsync(l0.A.rp, A->row_ptr, sizeof(int32_t) * ((size_t)n + 1), kind, s));
+    PCG_CK(cudaMemcpyAsync(l0.A.ci, A->col, sizeof(int32_t) * nnz, kind, s));
+    PCG_CK(cudaMemcpyAsync(l0.A.v, A->val, sizeof(double) * nnz, kind, s));
+    int *dflag = nullptr;
+    PCG_TRY(alloc(M, &dflag, 1));
+    PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+    k_check_csr<<<grid_for(n), kBlock, 0, s>>>(n, l0.A.rp, l0.A.ci, l0.A.v, nnz, dflag);
+    PCG_LAUNCH_CK();
+    int flag = 0;
+    PCG_TRY(read_flag(dflag, s, &flag));
+    if (flag == 0) {
+        k_check_sym<<<grid_for(n), kBlock, 0, s>>>(n, l0.A.rp, l0.A.ci, l0.A.v, dflag);
+        PCG_LAUNCH_CK();
+        PCG_TRY(read_flag(dflag, s, &flag));
+    }
+    release(M, dflag);
+    if (flag) {
+        set_error("amg_setup: invalid CSR (flags 0x%x: 1 column order/range, 2 diagonal, 4 row "
+                  "pointers, 8 not exactly symmetric)", flag);
+        return AMG_ERR_ARG;
+    }
+    PCG_TRY(alloc(M, &l0.w, n));
+    k_fill<double><<<grid_for(n), kBlock, 0, s>>>(l0.w, n, 1.0);
+    PCG_LAUNCH_CK();
+
+    for (int l = 0;; l++) {
+        Level &lv = h->lev[l];
+        int nl = lv.A.n;
+        if (nl <= prm->coarse_max || l == prm->max_levels - 1) break;
+        DevCSR cur = lv.A;
+        double *curw = lv.w;
+        bool own = false;
+        int32_t *cagg = nullptr;
+        double *cp = nullptr;
+        PCG_TRY(alloc(M, &cagg, nl));
+        PCG_TRY(alloc(M, &cp, nl));
+        k_iota<<<grid_for(nl), kBlock, 0, s>>>(cagg, nl);
+        k_fill<double><<<grid_for(nl), kBlock, 0, s>>>(cp, nl, 1.0);
+        PCG_LAUNCH_CK();
+        lv.pass_n.push_back(nl);
+        for (int ps = 0; ps < prm->n_pass; ps++) {
+            int32_t *agg = nullptr;
+            double *p = nullptr, *wc = nullptr;
+            DevCSR nxt;
+            PCG_TRY(pairwise_pass(h, cur, curw, &agg, &p, &nxt, &wc, &t_match, &t_rap, s));
+            k_compose<<<grid_for(nl), kBlock, 0, s>>>(nl, cagg, cp, agg, p);
+            PCG_LAUNCH_CK();
+            PCG_CK(cudaStreamSynchronize(s));
+            release(M, p);
+            lv.pass_agg.push_back(agg);
+            lv.pass_n.push_back(nxt.n);
+            if (own) {
+                free_csr(M, cur);
+                release(M, curw);
+            }
+            cur = nxt;
+            curw = wc;
+            own = true;
+        }
+        int nc = cur.n;
+        if (nc == 0 || (double)nc > 0.9 * (double)nl) {
+            free_csr(M, cur);
+            release(M, curw);
+            release(M, cagg);
+            release(M, cp);
+            for (auto *a : lv.pass_agg) M.release(a);
+            lv.pass_agg.clear();
+            lv.pass_n.clear();
+            break;
+        }
+        lv.agg = cagg;
+        lv.p = cp;
+        lv.nc = nc;
+        h->lev.emplace_back();
+        Level &nx = h->lev[l + 1];
+        nx.A = cur;
+        nx.w = curw;
+    }
+    int L = (int)h->lev.size() - 1;
+    for (int l = 0; l <= L; l++) PCG_TRY(finish_level(h, h->lev[l], l == L, s));
+
+    // dense inverse of the coarsest matrix
+    Level &lc = h->lev[L];
+    int nL = lc.A.n;
+    if (nL > kDenseMax) {
+        set_error("amg_setup: coarsening stalled at %d rows (dense limit %d)", nL, kDenseMax);
+        return AMG_ERR_COARSE;
+    }
+    h->nL = nL;
+    double *ad = nullptr;
+    PCG_TRY(alloc(M, &ad, (size_t)nL * nL));
+    PCG_TRY(alloc(M, &h->Ainv, (size_t)nL * nL));
+    PCG_TRY(alloc(M, &h->bL, nL));
+    PCG_TRY(alloc(M, &dflag, 1));
+    PCG_CK(cudaMemsetAsync(ad, 0, sizeof(double) * (size_t)nL * nL, s));
+    PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+    k_dense<<<grid_for(nL), kBlock, 0, s>>>(nL, lc.A.rp, lc.A.ci, lc.A.v, ad);
+    k_chol<<<1, 256, 0, s>>>(nL, ad, dflag);
+    PCG_LAUNCH_CK();
+    PCG_TRY(read_flag(dflag, s, &flag));
+    release(M, dflag);
+    if (flag) {
+        release(M, ad);
+        set_error("amg_setup: coarsest matrix is not SPD (Cholesky pivot <= 0)");
+        return AMG_ERR_BREAKDOWN;
+    }
+    k_chol_inverse<<<nL, 256, sizeof(double) * nL, s>>>(nL, ad, h->Ainv);
+    PCG_LAUNCH_CK();
+    PCG_CK(cudaStreamSynchronize(s));
+    release(M, ad);
+    PCG_TRY(alloc_solve_workspace(h));
+    PCG_CK(cudaStreamSynchronize(s));
+    h->setup_ms[0] = now_ms() - t_begin;
+    h->setup_ms[1] = t_match;
+    h->setup_ms[2] = t_rap;
+    h->setup_ms[3] = h->setup_ms[0] - t_match - t_rap;
+    return AMG_OK;
+}
+
+}  // namespace pcgamg

@@ -1,0 +1,624 @@
+// Solve phase: PCG / FCG(1) preconditioned by one V-cycle per iteration
+// (arxiv 2210.16660, Sec. 3.1 Eq. (multiplicative composition) with nu = 1
+// and M = D_l1; Sec. 5 flexible CG with a relative-residual stop).
+//
+// Every kernel streams a sliced-ELL matrix (one warp per 32-row slice,
+// coalesced value/column loads) and fuses the vector work around it:
+//   down  : x = D^-1 b on the fly, t = p .* (b - A x)        (pre-smooth, residual)
+//   restr : b_{l+1}[I] = sum_{i in G_I} t_i, members in index order
+//   coarse: x_L = A_L^{-1} b_L (dense float64 inverse)
+//   up    : x = D^-1 b + P x_{l+1} on the fly, z = x + D^-1 (b - A x)
+//           (prolongation + post-smooth; on level 0 also r.z and z.q_old)
+//   spmv  : p = z + beta p_old on the fly, q = A p, p.q
+//   update: x += alpha p, r -= alpha q, ||r||^2
+//   check : r = b - A x and ||r||^2 when the recursive residual met rtol
+// Reductions are two-stage and deterministic: each block writes a partial,
+// the last block to finish (atomic ticket) sums the partials in index order
+// and updates the scalars of the iteration in device memory (struct Ctl), so
+// a whole iteration runs without a host round trip.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace pcgamg {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// Block-wide sum of two doubles (blockDim.x == kBlock); result in thread 0.
+__device__ __forceinline__ void block_sum2(double &a, double &b) {
+    __shared__ double sa[kBlock / 32], sb[kBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = lane < kBlock / 32 ? sa[lane] : 0.0;
+        b = lane < kBlock / 32 ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+// Writes this block's partials; returns true in every thread of the last
+// block to finish, after which partials[0..gridDim) are complete.
+__device__ __forceinline__ bool publish_partials(double a, double b, double *partials, unsigned *counter) {
+    __shared__ bool last;
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = a;
+        partials[gridDim.x + blockIdx.x] = b;
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return last;
+}
+
+// Sum of the partials in a fixed order (run by the whole last block).
+__device__ __forceinline__ void final_sum2(const double *partials, double &a, double &b) {
+    __threadfence();
+    a = 0.0;
+    b = 0.0;
+    int nb = gridDim.x;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        a += __ldcg(partials + k);
+        b += __ldcg(partials + nb + k);
+    }
+    block_sum2(a, b);
+}
+
+__device__ __forceinline__ void fail(Ctl *c, int status) {
+    c->done = 2;
+    c->status = status;
+}
+
+// ------------------------------------------------------------ level kernels
+// Pre-smooth from zero, residual and weighted restriction input:
+// t_i = p_i (b_i - sum_j a_ij dinv_j b_j).
+template <typename T, typename TIO>
+__global__ void __launch_bounds__(kBlock) k_down(int n, const int32_t *__restrict__ sptr,
+                                                 const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                 const TIO *__restrict__ b, const T *__restrict__ dinv,
+                                                 const T *__restrict__ p, T *__restrict__ t,
+                                                 const Ctl *__restrict__ ctl) {
+    if (ctl->done) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int s = i >> 5, lane = i & 31;
+        int32_t base = ldg(sptr + s);
+        int w = (ldg(sptr + s + 1) - base) >> 5;
+        const int32_t *c = col + base + lane;
+        const T *a = val + base + lane;
+        T acc = 0;
+        for (int k = 0; k < w; k++) {
+            int j = ldg(c + 32 * k);
+            T xj = ldg(dinv + j) * (T)ldg(b + j);
+            acc += ldg(a + 32 * k) * xj;
+        }
+        T r = (T)b[i] - acc;
+        t[i] = ldg(p + i) * r;
+    }
+}
+
+// b_c[I] = sum of t over the members of aggregate I, in increasing index order.
+template <typename T, typename TO>
+__global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t *__restrict__ rptr,
+                                                     const int32_t *__restrict__ ridx,
+                                                     const T *__restrict__ t, TO *__restrict__ bc,
+                                                     const Ctl *__restrict__ ctl) {
+    if (ctl->done) return;
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    T s = 0;
+    for (int32_t k = ldg(rptr + I); k < ldg(rptr + I + 1); k++) s += ldg(t + ldg(ridx + k));
+    bc[I] = (TO)s;
+}
+
+// x_L = A_L^{-1} b_L, one warp per row; TO = float rounds the float64 result.
+template <typename TO>
+__global__ void __launch_bounds__(kBlock) k_coarse(int nL, const double *__restrict__ ainv,
+                                                   const double *__restrict__ bL, TO *__restrict__ xL,
+                                                   const Ctl *__restrict__ ctl) {
+    if (ctl->done) return;
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= nL) return;
+    const double *a = ainv + (int64_t)row * nL;
+    double s = 0.0;
+    for (int j = lane; j < nL; j += 32) s += ldg(a + j) * ldg(bL + j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) xL[row] = (TO)s;
+}
+
+// Prolongation + post-smooth: x_j = dinv_j b_j + p_j xc[agg_j] (formed on
+// the fly for every column j), z_i = x_i + dinv_i (b_i - sum_j a_ij x_j).
+// On level 0 (DOT) also r.z (b = r) and, for FCG, z.q_old; the last block
+// turns them into rho and beta.
+template <typename T, typename TIO, bool DOT, bool FCG>
+__global__ void __launch_bounds__(kBlock) k_up(int n, const int32_t *__restrict__ sptr,
+                                               const int32_t *__restrict__ col, const T *__restrict__ val,
+                                               const TIO *__restrict__ b, const T *__restrict__ dinv,
+                                               const T *__restrict__ p, const int32_t *__restrict__ agg,
+                                               const T *__restrict__ xc, TIO *__restrict__ z,
+                                               const double *__restrict__ qold, double *partials,
+                                               Ctl *ctl) {
+    if (ctl->done) return;
+    double rz = 0.0, zq = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int s = i >> 5, lane = i & 31;
+        int32_t base = ldg(sptr + s);
+        int w = (ldg(sptr + s + 1) - base) >> 5;
+        const int32_t *c = col + base + lane;
+        const T *a = val + base + lane;
+        T acc = 0;
+        for (int k = 0; k < w; k++) {
+            int j = ldg(c + 32 * k);
+            T xj = ldg(dinv + j) * (T)ldg(b + j);
+            int aj = ldg(agg + j);
+            if (aj >= 0) xj += ldg(p + j) * ldg(xc + aj);
+            acc += ldg(a + 32 * k) * xj;
+        }
+        T bi = (T)b[i];
+        T di = ldg(dinv + i);
+        T xi = di * bi;
+        int ai = ldg(agg + i);
+        if (ai >= 0) xi += ldg(p + i) * ldg(xc + ai);
+        T zi = xi + di * (bi - acc);
+        TIO zo = (TIO)zi;
+        z[i] = zo;
+        if (DOT) {
+            rz += (double)b[i] * (double)zo;
+            if (FCG) zq += (double)zo * ldg(qold + i);
+        }
+    }
+    if (DOT) {
+        if (publish_partials(rz, zq, partials, &ctl->counter[0])) {
+            double a, bb;
+            final_sum2(partials, a, bb);
+            if (threadIdx.x == 0) {
+                ctl->counter[0] = 0;
+                if (!isfinite(a) || !isfinite(bb)) { fail(ctl, AMG_ERR_NAN); return; }
+                if (!(a > 0.0)) { fail(ctl, AMG_ERR_BREAKDOWN); return; }
+                ctl->rho = a;
+                ctl->zq = bb;
+                double beta = 0.0;
+                if (!ctl->restart) beta = ctl->mode == AMG_MODE_FCG32 ? -bb / ctl->pq_old : a / ctl->rho_old;
+                ctl->beta = beta;
+            }
+        }
+    }
+}
+
+// Single-level hierarchy: z = A^{-1} r (optionally through float32 as the
+// float32 V-cycle would round it), then r.z / z.q_old as in k_up.
+template <bool F32, bool FCG>
+__global__ void __launch_bounds__(kBlock) k_coarse_only(int n, const double *__restrict__ ainv,
+                                                        const double *__restrict__ r, double *__restrict__ z,
+                                                        const double *__restrict__ qold, double *partials,
+                                                        Ctl *ctl) {
+    if (ctl->done) return;
+    double rz = 0.0, zq = 0.0;
+    int lane = threadIdx.x & 31;
+    int wpb = blockDim.x >> 5;
+    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < n; row += gridDim.x * wpb) {
+        const double *a = ainv + (int64_t)row * n;
+        double s = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            double rj = ldg(r + j);
+            if (F32) rj = (double)(float)rj;
+            s += ldg(a + j) * rj;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            double zo = F32 ? (double)(float)s : s;
+            z[row] = zo;
+            rz += r[row] * zo;
+            if (FCG) zq += zo * qold[row];
+        }
+    }
+    if (publish_partials(rz, zq, partials, &ctl->counter[0])) {
+        double a, bb;
+        final_sum2(partials, a, bb);
+        if (threadIdx.x == 0) {
+            ctl->counter[0] = 0;
+            if (!isfinite(a) || !isfinite(bb)) { fail(ctl, AMG_ERR_NAN); return; }
+            if (!(a > 0.0)) { fail(ctl, AMG_ERR_BREAKDOWN); return; }
+            ctl->rho = a;
+            ctl->zq = bb;
+            double beta = 0.0;
+            if (!ctl->restart) beta = ctl->mode == AMG_MODE_FCG32 ? -bb / ctl->pq_old : a / ctl->rho_old;
+            ctl->beta = beta;
+        }
+    }
+}
+
+// ------------------------------------------------------------ Krylov kernels
+// p = z + beta p_old (formed on the fly for every column), q = A p, p.q.
+__global__ void __launch_bounds__(kBlock) k_spmv_p(int n, const int32_t *__restrict__ sptr,
+                                                   const int32_t *__restrict__ col,
+                                                   const double *__restrict__ val, const double *__restrict__ z,
+                                                   const double *__restrict__ pold, double *__restrict__ pnew,
+                                                   double *__restrict__ q, double *partials, Ctl *ctl) {
+    if (ctl->done) return;
+    double beta = ctl->beta;
+    double pq = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int s = i >> 5, lane = i & 31;
+        int32_t base = ldg(sptr + s);
+        int w = (ldg(sptr + s + 1) - base) >> 5;
+        const int32_t *c = col + base + lane;
+        const double *a = val + base + lane;
+        double acc = 0.0;
+        for (int k = 0; k < w; k++) {
+            int j = ldg(c + 32 * k);
+            double pj = ldg(z + j) + beta * ldg(pold + j);
+            acc += ldg(a + 32 * k) * pj;
+        }
+        double pi = ldg(z + i) + beta * ldg(pold + i);
+        pnew[i] = pi;
+        q[i] = acc;
+        pq += pi * acc;
+    }
+    if (publish_partials(pq, 0.0, partials, &ctl->counter[1])) {
+        double a, unused;
+        final_sum2(partials, a, unused);
+        if (threadIdx.x == 0) {
+            ctl->counter[1] = 0;
+            if (!isfinite(a)) { fail(ctl, AMG_ERR_NAN); return; }
+            if (!(a > 0.0)) { fail(ctl, AMG_ERR_BREAKDOWN); return; }
+            ctl->pq = a;
+            ctl->alpha = ctl->rho / a;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q, ||r||^2; the last block records the relative
+// residual, advances the iteration and decides whether to check the true one.
+__global__ void __launch_bounds__(kBlock) k_update(int n, const double *__restrict__ p,
+                                                   const double *__restrict__ q, double *__restrict__ x,
+                                                   double *__restrict__ r, double *partials, Ctl *ctl,
+                                                   double *hist) {
+    if (ctl->done) return;
+    double alpha = ctl->alpha;
+    double rr = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = x[i] + alpha * p[i];
+        double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        rr += ri * ri;
+    }
+    if (publish_partials(rr, 0.0, partials, &ctl->counter[2])) {
+        double a, unused;
+        final_sum2(partials, a, unused);
+        if (threadIdx.x == 0) {
+            ctl->counter[2] = 0;
+            int it = ctl->iter + 1;
+            ctl->iter = it;
+            double rel = sqrt(a) / ctl->bnorm;
+            ctl->rel = rel;
+            hist[it] = rel;
+            ctl->rho_old = ctl->rho;
+            ctl->pq_old = ctl->pq;
+            ctl->restart = 0;
+            if (!isfinite(rel)) { fail(ctl, AMG_ERR_NAN); return; }
+            if (rel <= ctl->rtol) ctl->check = 1;
+            else if (it >= ctl->maxit) fail(ctl, AMG_ERR_NOCONV);
+        }
+    }
+}
+
+// r = b - A x and ||r||^2, ||b||^2. INIT: first residual of the solve.
+// Otherwise runs only when the recursive residual met rtol.
+template <bool INIT>
+__global__ void __launch_bounds__(kBlock) k_residual(int n, const int32_t *__restrict__ sptr,
+                                                     const int32_t *__restrict__ col,
+                                                     const double *__restrict__ val, const double *__restrict__ b,
+                                                     const double *__restrict__ x, double *__restrict__ r,
+                                                     double *partials, Ctl *ctl, double *hist) {
+    if (ctl->done) return;
+    if (!INIT && !ctl->check) return;
+    double rr = 0.0, bb = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int s = i >> 5, lane = i & 31;
+        int32_t base = ldg(sptr + s);
+        int w = (ldg(sptr + s + 1) - base) >> 5;
+        const int32_t *c = col + base + lane;
+        const double *a = val + base + lane;
+        double acc = 0.0;
+        for (int k = 0; k < w; k++) acc += ldg(a + 32 * k) * ldg(x + ldg(c + 32 * k));
+        double bi = b[i];
+        double ri = bi - acc;
+        r[i] = ri;
+        rr += ri * ri;
+        if (INIT) bb += bi * bi;
+    }
+    if (publish_partials(rr, bb, partials, &ctl->counter[3])) {
+        double a, bsq;
+        final_sum2(partials, a, bsq);
+        if (threadIdx.x == 0) {
+            ctl->counter[3] = 0;
+            if (INIT) {
+                double bn = sqrt(bsq);
+                ctl->bnorm = bn;
+                if (!isfinite(bn) || !isfinite(a)) { fail(ctl, AMG_ERR_NAN); return; }
+                if (bn == 0.0) { ctl->done = 1; ctl->status = AMG_OK; ctl->true_rel = 0.0; hist[0] = 0.0; return; }
+                double rel = sqrt(a) / bn;
+                ctl->rel = rel;
+                ctl->true_rel = rel;
+                hist[0] = rel;
+                if (rel <= ctl->rtol) { ctl->done = 1; ctl->status = AMG_OK; }
+                else if (ctl->maxit <= 0) fail(ctl, AMG_ERR_NOCONV);
+            } else {
+                double rel = sqrt(a) / ctl->bnorm;
+                ctl->true_rel = rel;
+                ctl->check = 0;
+                if (!isfinite(rel)) { fail(ctl, AMG_ERR_NAN); return; }
+                if (rel <= ctl->rtol) { ctl->done = 1; ctl->status = AMG_OK; return; }
+                ctl->restart = 1;
+                hist[ctl->iter] = rel;
+                if (ctl->iter >= ctl->maxit) fail(ctl, AMG_ERR_NOCONV);
+            }
+        }
+    }
+}
+
+__global__ void k_zero(double *a, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 0.0;
+}
+
+inline int grid_rows(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
+
+// CUDA-event spans around kernel launches (only when profiling is on).
+constexpr int kEvPairs = 64;
+
+void prof_begin(amg_hier *h, int kind, cudaStream_t s) {
+    if (!h->profile || h->ev_used + 2 > (int)h->ev.size()) return;
+    h->ev_kind[h->ev_used / 2] = kind;
+    cudaEventRecord(h->ev[h->ev_used], s);
+}
+
+void prof_end(amg_hier *h, cudaStream_t s) {
+    if (!h->profile || h->ev_used + 2 > (int)h->ev.size()) return;
+    cudaEventRecord(h->ev[h->ev_used + 1], s);
+    h->ev_used += 2;
+}
+
+// Fold the recorded spans into the per-kind totals (stream already synchronised).
+void prof_collect(amg_hier *h) {
+    for (int k = 0; k + 1 < h->ev_used; k += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]) == cudaSuccess) {
+            h->prof_ms[h->ev_kind[k / 2]] += ms;
+            h->prof_n[h->ev_kind[k / 2]] += 1;
+        }
+    }
+    h->ev_used = 0;
+}
+
+// ------------------------------------------------------------ one iteration
+template <typename T>
+struct LevelPtrs;
+template <>
+struct LevelPtrs<double> {
+    static const double *val(const Level &l) { return l.S.v64; }
+    static const double *dinv(const Level &l) { return l.dinv; }
+    static const double *p(const Level &l) { return l.p; }
+    static double *b(Level &l) { return l.b64; }
+    static double *x(Level &l) { return l.x64; }
+    static double *t(Level &l) { return l.t64; }
+};
+template <>
+struct LevelPtrs<float> {
+    static const float *val(const Level &l) { return l.S.v32; }
+    static const float *dinv(const Level &l) { return l.dinv32; }
+    static const float *p(const Level &l) { return l.p32; }
+    static float *b(Level &l) { return l.b32; }
+    static float *x(Level &l) { return l.x32; }
+    static float *t(Level &l) { return l.t32; }
+};
+
+// z = B r (one V-cycle), including rho / beta for the Krylov step.
+template <typename T, bool FCG>
+int launch_vcycle(amg_hier *h, cudaStream_t s) {
+    using LP = LevelPtrs<T>;
+    auto &lev = h->lev;
+    int L = (int)lev.size() - 1;
+    Ctl *ctl = h->ctl;
+    if (L == 0) {
+        h->launches += 1;
+        k_coarse_only<std::is_same<T, float>::value, FCG>
+            <<<h->nblk, kBlock, 0, s>>>(h->nL, h->Ainv, h->r, h->z, h->q, h->partials, ctl);
+        PCG_LAUNCH_CK();
+        return AMG_OK;
+    }
+    // down: level 0 reads r (float64)
+    {
+        Level &l0 = lev[0];
+        prof_begin(h, 0, s);
+        k_down<T, double><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, LP::val(l0), h->r,
+                                                     LP::dinv(l0), LP::p(l0), LP::t(l0), ctl);
+        prof_end(h, s);
+    }
+    prof_begin(h, 5, s);
+    h->launches += 3 * L + 1;
+    for (int l = 0; l < L; l++) {
+        Level &lv = lev[l];
+        if (l > 0)
+            k_down<T, T><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.S.sptr, lv.S.col, LP::val(lv),
+                                                               LP::b(lv), LP::dinv(lv), LP::p(lv), LP::t(lv), ctl);
+        if (l + 1 == L)
+            k_restrict<T, double><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, LP::t(lv),
+                                                                      h->bL, ctl);
+        else
+            k_restrict<T, T><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, LP::t(lv),
+                                                                 LP::b(lev[l + 1]), ctl);
+    }
+    k_coarse<T><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, LP::x(lev[L]), ctl);
+    for (int l = L - 1; l >= 1; l--) {
+        Level &lv = lev[l];
+        k_up<T, T, false, false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
+            lv.A.n, lv.S.sptr, lv.S.col, LP::val(lv), LP::b(lv), LP::dinv(lv), LP::p(lv), lv.agg,
+            LP::x(lev[l + 1]), LP::x(lv), nullptr, nullptr, ctl);
+    }
+    prof_end(h, s);
+    {
+        Level &l0 = lev[0];
+        prof_begin(h, 1, s);
+        k_up<T, double, true, FCG><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, LP::val(l0), h->r,
+                                                               LP::dinv(l0), LP::p(l0), l0.agg, LP::x(lev[1]),
+                                                               h->z, h->q, h->partials, ctl);
+        prof_end(h, s);
+    }
+    PCG_LAUNCH_CK();
+    return AMG_OK;
+}
+
+int launch_iteration(amg_hier *h, int parity, cudaStream_t s) {
+    if (h->mode == AMG_MODE_FCG32) PCG_TRY((launch_vcycle<float, true>(h, s)));
+    else PCG_TRY((launch_vcycle<double, false>(h, s)));
+    Level &l0 = h->lev[0];
+    int n = l0.A.n;
+    double *pold = h->pv[parity], *pnew = h->pv[parity ^ 1];
+    prof_begin(h, 2, s);
+    k_spmv_p<<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->z, pold, pnew, h->q, h->partials,
+                                        h->ctl);
+    prof_end(h, s);
+    prof_begin(h, 3, s);
+    k_update<<<h->nblk, kBlock, 0, s>>>(n, pnew, h->q, h->x, h->r, h->partials, h->ctl, h->hist);
+    prof_end(h, s);
+    prof_begin(h, 4, s);
+    k_residual<false><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r,
+                                                 h->partials, h->ctl, h->hist);
+    prof_end(h, s);
+    h->launches += 3;
+    PCG_LAUNCH_CK();
+    return AMG_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+int set_profile(amg_hier *h, int enable) {
+    if (enable && h->ev.empty()) {
+        h->ev.resize(2 * kEvPairs);
+        for (auto &e : h->ev) PCG_CK(cudaEventCreate(&e));
+    }
+    h->profile = enable ? 1 : 0;
+    h->ev_used = 0;
+    return AMG_OK;
+}
+
+void free_profile(amg_hier *h) {
+    for (auto &e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+}
+
+int alloc_solve_workspace(amg_hier *h) {
+    Mem &M = h->mem;
+    int n = h->lev[0].A.n;
+    int dev = 0, sms = 0;
+    PCG_CK(cudaGetDevice(&dev));
+    PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    h->device = dev;
+    int64_t want = ((int64_t)n + kBlock - 1) / kBlock;
+    int64_t cap = (int64_t)sms * 8;
+    h->nblk = (int)(want < cap ? want : cap);
+    if (h->nblk < 1) h->nblk = 1;
+    PCG_TRY(alloc(M, &h->b, n));
+    PCG_TRY(alloc(M, &h->x, n));
+    PCG_TRY(alloc(M, &h->r, n));
+    PCG_TRY(alloc(M, &h->z, n));
+    PCG_TRY(alloc(M, &h->q, n));
+    PCG_TRY(alloc(M, &h->pv[0], n));
+    PCG_TRY(alloc(M, &h->pv[1], n));
+    PCG_TRY(alloc(M, &h->partials, 2 * (size_t)h->nblk));
+    PCG_TRY(alloc(M, &h->ctl, 1));
+    PCG_CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), M.stream));
+    PCG_CK(cudaMallocHost(&h->ctl_host, sizeof(Ctl)));
+    h->hist_cap = 1001;
+    PCG_TRY(alloc(M, &h->hist, h->hist_cap));
+    return AMG_OK;
+}
+
+int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, int *iters, double *res_hist,
+               cudaStream_t s) {
+    if (!b || !x || !(rtol >= 0.0) || maxit < 0) {
+        set_error("pcg_solve: bad arguments");
+        return AMG_ERR_ARG;
+    }
+    Level &l0 = h->lev[0];
+    int n = l0.A.n;
+    h->mem.stream = s;
+    if (maxit + 1 > h->hist_cap) {
+        release(h->mem, h->hist);
+        h->hist_cap = maxit + 1;
+        PCG_TRY(alloc(h->mem, &h->hist, h->hist_cap));
+    }
+    bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    PCG_CK(cudaMemcpyAsync(h->b, b, sizeof(double) * n, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    PCG_CK(cudaMemcpyAsync(h->x, x, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    Ctl c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.rtol = rtol;
+    c0.maxit = maxit;
+    c0.mode = h->mode;
+    c0.restart = 1;
+    *h->ctl_host = c0;
+    PCG_CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->pv[0], n);
+    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->pv[1], n);
+    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->q, n);
+    k_residual<true><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r, h->partials,
+                                                h->ctl, h->hist);
+    h->launches += 4;
+    PCG_LAUNCH_CK();
+    // Iterate in chunks; finished iterations turn every later kernel into a no-op.
+    const int chunk = 4;
+    int launched = 0;
+    for (;;) {
+        PCG_CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaStreamSynchronize(s));
+        if (h->profile) prof_collect(h);
+        if (h->ctl_host->done || launched >= maxit) break;
+        for (int k = 0; k < chunk && launched < maxit; k++, launched++) PCG_TRY(launch_iteration(h, launched & 1, s));
+    }
+    Ctl &c = *h->ctl_host;
+    if (c.done == 1 && c.bnorm == 0.0) k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->x, n);
+    PCG_LAUNCH_CK();
+    PCG_CK(cudaMemcpyAsync(x, h->x, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (res_hist) PCG_CK(cudaMemcpyAsync(res_hist, h->hist, sizeof(double) * (c.iter + 1), cudaMemcpyDefault, s));
+    PCG_CK(cudaStreamSynchronize(s));
+    if (iters) *iters = c.iter;
+    h->last_true_rel = c.true_rel;
+    int st = c.done ? c.status : AMG_ERR_NOCONV;
+    if (st == AMG_ERR_NOCONV) set_error("pcg_solve: no convergence in %d iterations (rel %.3e)", maxit, c.rel);
+    else if (st == AMG_ERR_BREAKDOWN) set_error("pcg_solve: breakdown (r.z <= 0 or p.Ap <= 0) at iteration %d", c.iter);
+    else if (st == AMG_ERR_NAN) set_error("pcg_solve: NaN/Inf at iteration %d", c.iter);
+    return st;
+}
+
+}  // namespace pcgamg
