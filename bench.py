@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Benchmark of the PCG + aggregation-AMG pressure solve on one GB300.
+
+Workload: the Q1 trilinear hex Laplacian on 128^3 nodes (2,097,152 dofs,
+55.3M stored entries), z graded geometrically by 1.04 from a Dirichlet wall,
+b = A x* with seeded x* ~ N(0,1), x0 = 0, rtol 1e-8 on ||r|| / ||b||.
+A step is one complete solve (every V-cycle, Krylov update and true-residual
+check until convergence) of one right-hand side; four seeded right-hand sides
+are used in turn. The headline is the float32-V-cycle / float64-FCG(1) solve;
+the plain float64 PCG solve is measured the same way beside it.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on
+the host instead (bounded sample, scaled to solves/s).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s + p50/p99 latency at rel.res 1e-8, mixed vs FP64 PCG-AMG; HBM GB/s"
+UNIT = "solves/s"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=128)
+    ap.add_argument("--ratio", type=float, default=1.04)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--maxit", type=int, default=500)
+    ap.add_argument("--nrhs", type=int, default=4)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------- ranks
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, dist, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- roofline
+def algorithmic_bytes(kind: str, mode: str, n0: int, nnz0: int, n1: int) -> float:
+    """Compulsory bytes of one launch of a level-0 kernel (each array once).
+
+    Matrix: value + int32 column per stored entry, one int32 slice pointer
+    per 32 rows. Vectors as the kernels read/write them.
+    """
+    vb = 4 if mode == "fcg32" else 8      # V-cycle value/vector bytes
+    sptr = 4 * (n0 // 32 + 1)
+    if kind == "spmv":      # z, p_old read; p_new, q written; float64 A
+        return nnz0 * 12 + n0 * 32 + sptr
+    if kind == "update":    # x, p, r, q read; x, r written
+        return n0 * 48
+    if kind == "residual":  # b, x read; r written
+        return nnz0 * 12 + n0 * 24 + sptr
+    if kind == "down0":     # r (f64), dinv, p read; t written
+        return nnz0 * (vb + 4) + n0 * (8 + 3 * vb) + sptr
+    if kind == "up0":       # r (f64), dinv, p, agg, [q_old] read; z (f64) written; x_1 gathered
+        extra = 8 if mode == "fcg32" else 0
+        return nnz0 * (vb + 4) + n0 * (8 + 2 * vb + 4 + 8 + extra) + n1 * vb + sptr
+    raise KeyError(kind)
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("solve.cu", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2210_16660_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, mode: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if data.get("source_sha") != source_sha():
+        return None
+    ent = data.get("kernels", {}).get(f"{kernel}:{mode}")
+    if not ent:
+        return None
+    return ent.get("dram_bytes_per_launch_full_size")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------- oracle
+def oracle_sample(prob, mode: str, target_s: float, iters_full: int | None):
+    """Time a bounded number of oracle iterations; scale to solves/s."""
+    import oracle as O
+    h = O.Hierarchy(prob.A, n_pass=2)
+    t = time.perf_counter()
+    h.solve(prob.b, rtol=0.0, maxit=1, mode=mode)
+    t1 = time.perf_counter() - t
+    k = max(1, int(target_s / max(t1, 1e-6)))
+    if iters_full is None:
+        res = h.solve(prob.b, rtol=1e-8, maxit=1000, mode=mode)
+        iters_full = res["iters"]
+    t = time.perf_counter()
+    h.solve(prob.b, rtol=0.0, maxit=k, mode=mode)
+    dt = time.perf_counter() - t
+    per_iter = dt / k
+    return h, per_iter, k, iters_full
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2210_16660_gb300 import workloads as W
+    prob = W.make_problem(args.N, args.ratio, seed=args.seed)
+    import oracle as O
+    h = O.Hierarchy(prob.A, n_pass=2)
+    full = h.solve(prob.b, rtol=args.rtol, maxit=1000, mode="fcg32")
+    iters = full["iters"]
+    # each step: a bounded sample of iterations of one solve, scaled by the full count
+    t = time.perf_counter()
+    h.solve(prob.b, rtol=0.0, maxit=1, mode="fcg32")
+    t1 = time.perf_counter() - t
+    k = max(1, int(min(args.cpu_seconds, 60.0) / max(1, args.steps + args.warmup) / max(t1, 1e-6)))
+    times = []
+    for s in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        h.solve(prob.b, rtol=0.0, maxit=k, mode="fcg32")
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            times.append(dt / k * iters)
+    sec = statistics.mean(times)
+    value = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": f"q1_hex_{args.N}^3_zgrade{args.ratio}", "n": prob.A.n, "nnz": prob.A.nnz,
+                   "rtol": args.rtol, "mode": "fcg32", "n_pass": 2, "coarse_max": 200},
+        "iters": iters,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{k} of the {iters} FCG(1) iterations of one 128^3 solve per step, "
+                                   f"scaled to a full solve; single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- ours
+def timed_solves(amg, bs, x, steps, warmup, rtol, maxit, torch, stream, dist, device, profile=False):
+    n_rhs = len(bs)
+    for s in range(warmup):
+        x.zero_()
+        amg.solve(bs[s % n_rhs], x, rtol=rtol, maxit=maxit, stream=stream, hist=False)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if profile:
+        amg.profile(True)
+        amg.profile_read()
+    launches0 = amg.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    iters = []
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for s in range(steps):
+        ev[s][0].record(stream)
+        x.zero_()
+        res = amg.solve(bs[s % n_rhs], x, rtol=rtol, maxit=maxit, stream=stream, hist=False)
+        ev[s][1].record(stream)
+        if res.status != 0:
+            raise RuntimeError(f"solve failed: {res.message}")
+        iters.append(res.iters)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = amg.launch_count() - launches0
+    prof = amg.profile_read() if profile else None
+    if profile:
+        amg.profile(False)
+    lat = [a.elapsed_time(b) for a, b in ev]
+    total_ms = t_all0.elapsed_time(t_all1)
+    return {"total_ms": total_ms, "lat_ms": lat, "iters": iters, "launches": launches, "prof": prof,
+            "true_rel": res.true_rel}
+
+
+def pct(v, q):
+    return float(np.percentile(np.asarray(v), q))
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    device = torch.device("cuda", local)
+    from paper_2210_16660_gb300 import binding as B
+    from paper_2210_16660_gb300 import workloads as W
+    B.load()
+    prob = W.make_problem(args.N, args.ratio, seed=args.seed)
+    extra_b, _ = W.make_rhs(prob, args.nrhs - 1, seed=args.seed + 1000)
+    rhs = [prob.b] + [np.ascontiguousarray(extra_b[:, c]) for c in range(args.nrhs - 1)]
+    stream = torch.cuda.current_stream()
+    amg = B.AMG.from_csr(prob.A, mode="fcg32", stream=stream)
+    setup = amg.setup_times()
+    levels = amg.info()
+    bs = [torch.from_numpy(b).to(device) for b in rhs]
+    x = torch.zeros(prob.A.n, dtype=torch.float64, device=device)
+
+    sampler = ClockSampler(local)
+    out = {}
+    for mode in ("fcg32", "pcg64"):
+        amg.set_mode(mode)
+        if mode == "fcg32":
+            sampler.start()
+        out[mode] = timed_solves(amg, bs, x, args.steps, args.warmup, args.rtol, args.maxit, torch, stream,
+                                 dist, device, profile=True)
+        if mode == "fcg32":
+            clocks = sampler.stop()
+    amg.set_mode("fcg32")
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the call
+    pin_b = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
+    pin_x = torch.zeros(prob.A.n, dtype=torch.float64).pin_memory().numpy()
+    for s in range(args.warmup):
+        pin_x[:] = 0.0
+        amg.solve(pin_b[s % len(pin_b)], pin_x, rtol=args.rtol, maxit=args.maxit, stream=stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_iters = []
+    for s in range(args.steps):
+        pin_x[:] = 0.0
+        res = amg.solve(pin_b[s % len(pin_b)], pin_x, rtol=args.rtol, maxit=args.maxit, stream=stream)
+        e2e_iters.append(res.iters)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        dist.barrier()
+
+    # whole-job aggregation (replicas: every rank solves its own copy)
+    m = out["fcg32"]
+    tot_ms = max_over_ranks(m["total_ms"], dist, device)
+    solves = sum_over_ranks(float(args.steps), dist, device)
+    value = solves / (tot_ms / 1e3)
+    f64 = out["pcg64"]
+    f64_ms = max_over_ranks(f64["total_ms"], dist, device)
+    e2e_s = max_over_ranks(e2e_s, dist, device)
+    e2e_value = solves / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        iters_full = int(round(statistics.median(m["iters"])))
+        _, per_iter, k, _ = oracle_sample(prob, "fcg32", args.cpu_seconds, iters_full)
+        cpu = {"value": 1.0 / (per_iter * iters_full), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{k} FCG(1) iterations (float32 V-cycle) of one 128^3 solve, single thread, "
+                         f"scaled by the {iters_full} iterations of a full solve"}
+
+    # roofline of the dominant level-0 kernel in the headline mode
+    peaks = measured_peaks()
+    n0, nnz0 = levels[0]
+    n1 = levels[1][0] if len(levels) > 1 else 0
+    prof = m["prof"]
+    cand = {k: v for k, v in prof.items() if k != "coarse_levels" and v[1] > 0}
+    dom = max(cand, key=lambda k: cand[k][0])
+    avg_ms = cand[dom][0] / cand[dom][1]
+    bytes_launch = algorithmic_bytes(dom, "fcg32", n0, nnz0, n1)
+    achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured"
+    if not peak:
+        peak, peak_src = 6800.0, "fallback"
+    kernel_names = {"down0": "k_down", "up0": "k_up", "spmv": "k_spmv_p", "update": "k_update",
+                    "residual": "k_residual"}
+    roofline = {"kernel": kernel_names[dom], "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": committed_traffic(kernel_names[dom], "fcg32"),
+                "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms}
+    per_kernel = {}
+    for k, (ms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        entry = {"avg_ms": ms / cnt, "launches": cnt, "share_of_step": ms / m["total_ms"]}
+        if k != "coarse_levels":
+            bl = algorithmic_bytes(k, "fcg32", n0, nnz0, n1)
+            entry["gbs"] = bl / (ms / cnt * 1e-3) / 1e9
+        per_kernel[k] = entry
+
+    if rank == 0:
+        h2d = 16 * n0
+        d2h = 8 * n0 + 8 * (int(statistics.median(e2e_iters)) + 1)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"q1_hex_{args.N}^3_zgrade{args.ratio}", "n": n0, "nnz": nnz0,
+                       "rtol": args.rtol, "mode": "fcg32 (float32 V-cycle in float64 FCG(1))",
+                       "n_pass": 2, "coarse_max": 200, "levels": len(levels), "nrhs_cycled": args.nrhs,
+                       "l2": "inputs larger than L2 (level-0 matrix 0.66 GB float64 + 0.44 GB float32)",
+                       "parallelism": f"replicas x{world}"},
+            "iters": {"median": statistics.median(m["iters"]), "min": min(m["iters"]), "max": max(m["iters"])},
+            "latency_ms": {"p50": pct(m["lat_ms"], 50), "p99": pct(m["lat_ms"], 99)},
+            "true_rel": m["true_rel"],
+            "fp64": {"value": solves / (f64_ms / 1e3), "unit": UNIT, "ms_per_step": f64_ms / args.steps,
+                     "latency_ms": {"p50": pct(f64["lat_ms"], 50), "p99": pct(f64["lat_ms"], 99)},
+                     "iters": statistics.median(f64["iters"]), "gpu_launches": f64["launches"]},
+            "setup_ms": setup,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roofline,
+            "kernels": per_kernel,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": m["launches"],
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    amg.close()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

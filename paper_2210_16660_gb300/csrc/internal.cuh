@@ -114,7 +114,7 @@ struct Ctl {
     int check;           // recursive residual met rtol: form the true one
     int done;            // 1 converged, 2 error
     int status;          // AMG_* code once done
-    int pad;
+    int bodies;          // executions of the graph's loop body (2 iterations each)
     unsigned int counter[8];  // last-block-done counters of the reducing kernels
 };
 
@@ -149,6 +149,13 @@ struct amg_hier {
     double prof_ms[kKinds] = {0};
     int64_t prof_n[kKinds] = {0};
     int64_t launches = 0;
+    // whole-solve CUDA graph per mode: prefix kernels, then a device-side
+    // while loop whose body runs two iterations
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_prefix_kernels = 0;
+    int graph_body_kernels[2] = {0, 0};
+    int use_graph = 1;
 };
 
 namespace pcgamg {

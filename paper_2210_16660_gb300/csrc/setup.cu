@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 
 #include "internal.cuh"
 
@@ -692,6 +693,10 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
     M.budget = prm->hbm_budget;
     h->prm = *prm;
     h->mode = prm->mode;
+    // PCGAMG_GRAPH=0 launches each solve kernel on the stream instead of
+    // replaying the whole-solve graph (same kernels; for profilers).
+    const char *g = getenv("PCGAMG_GRAPH");
+    if (g && g[0] == '0') h->use_graph = 0;
     if (!A || A->n <= 0 || A->n >= (int64_t)1 << 31 || A->nnz < A->n || A->nnz >= (int64_t)1 << 31 ||
         !A->row_ptr || !A->col || !A->val) {
         set_error("amg_setup: bad CSR sizes or NULL arrays");

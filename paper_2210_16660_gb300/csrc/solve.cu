@@ -86,11 +86,37 @@ __device__ __forceinline__ void fail(Ctl *c, int status) {
     c->status = status;
 }
 
+// Sum over the stored entries of one sliced-ELL row: acc = sum_k a_k x(j_k),
+// k in storage order. Column/value loads of U entries are issued before their
+// gathers so each warp keeps several independent loads in flight.
+constexpr int kUnroll = 4;
+
+template <typename T, typename F>
+__device__ __forceinline__ T sell_row(const int32_t *__restrict__ c, const T *__restrict__ a, int w, F xval) {
+    T acc = 0;
+    int k = 0;
+    for (; k + kUnroll <= w; k += kUnroll) {
+        int j[kUnroll];
+        T v[kUnroll], x[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            j[u] = __ldg(c + 32 * (k + u));
+            v[u] = __ldg(a + 32 * (k + u));
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) x[u] = xval(j[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) acc += v[u] * x[u];
+    }
+    for (; k < w; k++) acc += __ldg(a + 32 * k) * xval(__ldg(c + 32 * k));
+    return acc;
+}
+
 // ------------------------------------------------------------ level kernels
 // Pre-smooth from zero, residual and weighted restriction input:
 // t_i = p_i (b_i - sum_j a_ij dinv_j b_j).
 template <typename T, typename TIO>
-__global__ void __launch_bounds__(kBlock) k_down(int n, const int32_t *__restrict__ sptr,
+__global__ void __launch_bounds__(kBlock, 4) k_down(int n, const int32_t *__restrict__ sptr,
                                                  const int32_t *__restrict__ col, const T *__restrict__ val,
                                                  const TIO *__restrict__ b, const T *__restrict__ dinv,
                                                  const T *__restrict__ p, T *__restrict__ t,
@@ -100,14 +126,8 @@ __global__ void __launch_bounds__(kBlock) k_down(int n, const int32_t *__restric
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
         int w = (ldg(sptr + s + 1) - base) >> 5;
-        const int32_t *c = col + base + lane;
-        const T *a = val + base + lane;
-        T acc = 0;
-        for (int k = 0; k < w; k++) {
-            int j = ldg(c + 32 * k);
-            T xj = ldg(dinv + j) * (T)ldg(b + j);
-            acc += ldg(a + 32 * k) * xj;
-        }
+        T acc = sell_row(col + base + lane, val + base + lane, w,
+                         [&](int j) { return ldg(dinv + j) * (T)ldg(b + j); });
         T r = (T)b[i] - acc;
         t[i] = ldg(p + i) * r;
     }
@@ -148,7 +168,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int nL, const double *__restr
 // On level 0 (DOT) also r.z (b = r) and, for FCG, z.q_old; the last block
 // turns them into rho and beta.
 template <typename T, typename TIO, bool DOT, bool FCG>
-__global__ void __launch_bounds__(kBlock) k_up(int n, const int32_t *__restrict__ sptr,
+__global__ void __launch_bounds__(kBlock, 4) k_up(int n, const int32_t *__restrict__ sptr,
                                                const int32_t *__restrict__ col, const T *__restrict__ val,
                                                const TIO *__restrict__ b, const T *__restrict__ dinv,
                                                const T *__restrict__ p, const int32_t *__restrict__ agg,
@@ -161,16 +181,12 @@ __global__ void __launch_bounds__(kBlock) k_up(int n, const int32_t *__restrict_
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
         int w = (ldg(sptr + s + 1) - base) >> 5;
-        const int32_t *c = col + base + lane;
-        const T *a = val + base + lane;
-        T acc = 0;
-        for (int k = 0; k < w; k++) {
-            int j = ldg(c + 32 * k);
+        T acc = sell_row(col + base + lane, val + base + lane, w, [&](int j) {
             T xj = ldg(dinv + j) * (T)ldg(b + j);
             int aj = ldg(agg + j);
             if (aj >= 0) xj += ldg(p + j) * ldg(xc + aj);
-            acc += ldg(a + 32 * k) * xj;
-        }
+            return xj;
+        });
         T bi = (T)b[i];
         T di = ldg(dinv + i);
         T xi = di * bi;
@@ -248,7 +264,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_only(int n, const double *__r
 
 // ------------------------------------------------------------ Krylov kernels
 // p = z + beta p_old (formed on the fly for every column), q = A p, p.q.
-__global__ void __launch_bounds__(kBlock) k_spmv_p(int n, const int32_t *__restrict__ sptr,
+__global__ void __launch_bounds__(kBlock, 4) k_spmv_p(int n, const int32_t *__restrict__ sptr,
                                                    const int32_t *__restrict__ col,
                                                    const double *__restrict__ val, const double *__restrict__ z,
                                                    const double *__restrict__ pold, double *__restrict__ pnew,
@@ -260,14 +276,8 @@ __global__ void __launch_bounds__(kBlock) k_spmv_p(int n, const int32_t *__restr
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
         int w = (ldg(sptr + s + 1) - base) >> 5;
-        const int32_t *c = col + base + lane;
-        const double *a = val + base + lane;
-        double acc = 0.0;
-        for (int k = 0; k < w; k++) {
-            int j = ldg(c + 32 * k);
-            double pj = ldg(z + j) + beta * ldg(pold + j);
-            acc += ldg(a + 32 * k) * pj;
-        }
+        double acc = sell_row(col + base + lane, val + base + lane, w,
+                              [&](int j) { return ldg(z + j) + beta * ldg(pold + j); });
         double pi = ldg(z + i) + beta * ldg(pold + i);
         pnew[i] = pi;
         q[i] = acc;
@@ -324,7 +334,7 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, const double *__restri
 // r = b - A x and ||r||^2, ||b||^2. INIT: first residual of the solve.
 // Otherwise runs only when the recursive residual met rtol.
 template <bool INIT>
-__global__ void __launch_bounds__(kBlock) k_residual(int n, const int32_t *__restrict__ sptr,
+__global__ void __launch_bounds__(kBlock, 4) k_residual(int n, const int32_t *__restrict__ sptr,
                                                      const int32_t *__restrict__ col,
                                                      const double *__restrict__ val, const double *__restrict__ b,
                                                      const double *__restrict__ x, double *__restrict__ r,
@@ -336,10 +346,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int32_t *__res
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
         int w = (ldg(sptr + s + 1) - base) >> 5;
-        const int32_t *c = col + base + lane;
-        const double *a = val + base + lane;
-        double acc = 0.0;
-        for (int k = 0; k < w; k++) acc += ldg(a + 32 * k) * ldg(x + ldg(c + 32 * k));
+        double acc = sell_row(col + base + lane, val + base + lane, w, [&](int j) { return ldg(x + j); });
         double bi = b[i];
         double ri = bi - acc;
         r[i] = ri;
@@ -379,6 +386,22 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int32_t *__res
 __global__ void k_zero(double *a, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = 0.0;
+}
+
+// Loop condition of the solve graph: run another body while not done. The
+// body count is bounded independently of the kernels' own bookkeeping: past
+// (maxit + 1) / 2 + 1 bodies the solve is ended as not converged.
+__global__ void k_set_cond(cudaGraphConditionalHandle hc, Ctl *ctl, int count_body) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (count_body) {
+        int b = ctl->bodies + 1;
+        ctl->bodies = b;
+        if (!ctl->done && b > (ctl->maxit + 1) / 2 + 1) {
+            ctl->done = 2;
+            ctl->status = AMG_ERR_NOCONV;
+        }
+    }
+    cudaGraphSetConditional(hc, ctl->done ? 0u : 1u);
 }
 
 inline int grid_rows(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
@@ -510,6 +533,92 @@ int launch_iteration(amg_hier *h, int parity, cudaStream_t s) {
     return AMG_OK;
 }
 
+int launch_prefix(amg_hier *h, cudaStream_t s) {
+    Level &l0 = h->lev[0];
+    int n = l0.A.n;
+    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->pv[0], n);
+    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->pv[1], n);
+    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->q, n);
+    k_residual<true><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r, h->partials,
+                                                h->ctl, h->hist);
+    h->launches += 4;
+    PCG_LAUNCH_CK();
+    return AMG_OK;
+}
+
+// Whole solve as one graph: prefix (zero p/q, first residual, condition),
+// then a while node whose body is two iterations plus the condition kernel.
+int build_graph(amg_hier *h, int mode) {
+    if (!h->cap_stream) PCG_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = h->cap_stream;
+    int saved_mode = h->mode;
+    h->mode = mode;
+    int64_t l0 = h->launches;
+    PCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int st = launch_prefix(h, cs);
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle hc = 0;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t cnode = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!st) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+    if (!st && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+    if (!st && e == cudaSuccess) {
+        k_set_cond<<<1, 32, 0, cs>>>(hc, h->ctl, 0);
+        e = cudaGetLastError();
+    }
+    if (!st && e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd);
+    if (!st && e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hc;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&cnode, g, deps, nullptr, nd, &cp);
+    }
+    if (!st && e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    cudaGraph_t full = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &full);
+    int prefix = (int)(h->launches - l0) + 1;
+    if (st || e != cudaSuccess || e2 != cudaSuccess) {
+        if (full) cudaGraphDestroy(full);
+        h->mode = saved_mode;
+        h->launches = l0;
+        if (!st) st = cuda_fail(e != cudaSuccess ? e : e2, "solve graph capture", __FILE__, __LINE__);
+        return st;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    int64_t l1 = h->launches;
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = launch_iteration(h, 0, cs);
+        if (!st) st = launch_iteration(h, 1, cs);
+        if (!st) k_set_cond<<<1, 32, 0, cs>>>(hc, h->ctl, 1);
+        cudaGraph_t bout = body;
+        e = cudaStreamEndCapture(cs, &bout);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    int body_k = (int)(h->launches - l1) + 1;
+    h->launches = l0;
+    h->mode = saved_mode;
+    if (st || e != cudaSuccess) {
+        cudaGraphDestroy(full);
+        if (!st) st = cuda_fail(e, "solve graph body capture", __FILE__, __LINE__);
+        return st;
+    }
+    e = cudaGraphInstantiate(&h->gexec[mode], full, 0);
+    cudaGraphDestroy(full);
+    if (e != cudaSuccess) {
+        h->gexec[mode] = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    }
+    h->graph_prefix_kernels = prefix;
+    h->graph_body_kernels[mode] = body_k;
+    return AMG_OK;
+}
+
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -535,6 +644,12 @@ int set_profile(amg_hier *h, int enable) {
 void free_profile(amg_hier *h) {
     for (auto &e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
+    for (auto &g : h->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
 }
 
 int alloc_solve_workspace(amg_hier *h) {
@@ -577,6 +692,10 @@ int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, 
         release(h->mem, h->hist);
         h->hist_cap = maxit + 1;
         PCG_TRY(alloc(h->mem, &h->hist, h->hist_cap));
+        for (auto &g : h->gexec) {
+            if (g) cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     }
     bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
     PCG_CK(cudaMemcpyAsync(h->b, b, sizeof(double) * n, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -589,17 +708,24 @@ int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, 
     c0.restart = 1;
     *h->ctl_host = c0;
     PCG_CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->pv[0], n);
-    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->pv[1], n);
-    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->q, n);
-    k_residual<true><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r, h->partials,
-                                                h->ctl, h->hist);
-    h->launches += 4;
-    PCG_LAUNCH_CK();
+    bool graph = h->use_graph && !h->profile;
+    if (graph && !h->gexec[h->mode]) {
+        if (build_graph(h, h->mode) != AMG_OK) {
+            h->use_graph = 0;  // keep solving with stream launches; the reason stays in amg_last_error
+            graph = false;
+        }
+    }
+    if (graph) {
+        PCG_CK(cudaGraphLaunch(h->gexec[h->mode], s));
+        PCG_CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaStreamSynchronize(s));
+        h->launches += h->graph_prefix_kernels + (int64_t)h->ctl_host->bodies * h->graph_body_kernels[h->mode];
+    }
+    if (!graph) PCG_TRY(launch_prefix(h, s));
     // Iterate in chunks; finished iterations turn every later kernel into a no-op.
     const int chunk = 4;
-    int launched = 0;
-    for (;;) {
+    int launched = graph ? maxit : 0;
+    for (; !graph;) {
         PCG_CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         PCG_CK(cudaStreamSynchronize(s));
         if (h->profile) prof_collect(h);

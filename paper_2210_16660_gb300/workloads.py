@@ -72,12 +72,19 @@ def normals(seed: int, count: int, offset: int = 0) -> np.ndarray:
 
 
 def graded_spacing(npts: int, ratio: float, length: float = 1.0) -> np.ndarray:
-    """Cell sizes ``h_k = h0 * ratio^k`` (k = 0..npts-2) summing to ``length``."""
+    """Cell sizes ``h_k = h0 * ratio^k`` (k = 0..npts-2) summing to ``length``.
+
+    Powers are formed by repeated multiplication (plain IEEE operations, no
+    libm ``pow``) so the sizes are bit-identical on every platform.
+    """
     m = npts - 1
     if ratio == 1.0:
         return np.full(m, length / m)
-    h0 = length * (ratio - 1.0) / (ratio ** m - 1.0)
-    return h0 * ratio ** np.arange(m, dtype=np.float64)
+    pw = [1.0]
+    for _ in range(m):
+        pw.append(pw[-1] * ratio)
+    h0 = length * (ratio - 1.0) / (pw[m] - 1.0)
+    return h0 * np.array(pw[:m])
 
 
 def _tridiag_1d(h: np.ndarray):

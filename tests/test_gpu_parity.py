@@ -109,10 +109,13 @@ def test_host_vectors_and_warm_start(mode):
 
 
 def test_single_level_converges_in_one_iteration():
+    # one level: B = A^{-1}; in float64 one iteration suffices, while the
+    # float32 V-cycle rounds r and z to float32 (~1e-7), so it takes two
     prob = W.make_problem(5, 1.04, seed=2)
-    for mode in ("pcg64", "fcg32"):
-        res, ref, _, _ = _solve_parity(prob, mode, coarse_max=200)
-        assert res.iters == 1 and ref["iters"] == 1
+    res, ref, _, _ = _solve_parity(prob, "pcg64", coarse_max=200)
+    assert res.iters == 1 and ref["iters"] == 1
+    res, ref, _, _ = _solve_parity(prob, "fcg32", coarse_max=200)
+    assert res.iters <= 2 and ref["iters"] <= 2
 
 
 def test_special_cases():
@@ -171,15 +174,38 @@ def test_deterministic_repeat():
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
+def test_graph_and_stream_launch_paths_agree():
+    """The whole-solve graph and plain stream launches run the same kernels."""
+    prob = W.make_problem(28, 1.04, seed=6)
+    b = torch.from_numpy(prob.b).cuda()
+    for mode in ("pcg64", "fcg32"):
+        amg = B.AMG.from_csr(prob.A, mode=mode)
+        x1 = torch.zeros_like(b)
+        n0 = amg.launch_count()
+        r1 = amg.solve(b, x1)
+        n_graph = amg.launch_count() - n0
+        amg.profile(True)
+        x2 = torch.zeros_like(b)
+        r2 = amg.solve(b, x2)
+        prof = amg.profile_read()
+        amg.profile(False)
+        assert r1.status == r2.status == 0 and r1.iters == r2.iters
+        assert torch.equal(x1, x2)
+        assert np.array_equal(r1.hist, r2.hist)
+        assert n_graph > 10 * r1.iters
+        assert prof["spmv"][1] >= r1.iters and prof["spmv"][0] > 0
+
+
 def test_torch_allocator_route():
     prob = W.make_problem(10, 1.04, seed=5)
     B.use_torch_allocator(True)
     try:
+        b = torch.from_numpy(prob.b).cuda()
+        x = torch.zeros(prob.A.n, dtype=torch.float64, device="cuda")
         before = torch.cuda.memory_allocated()
         amg = B.AMG.from_csr(prob.A)
         assert torch.cuda.memory_allocated() > before
-        x = torch.zeros(prob.A.n, dtype=torch.float64, device="cuda")
-        assert amg.solve(torch.from_numpy(prob.b).cuda(), x).status == 0
+        assert amg.solve(b, x).status == 0
         amg.close()
         assert torch.cuda.memory_allocated() == before
     finally:
