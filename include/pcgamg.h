@@ -149,9 +149,10 @@ int amg_profile(amg_handle h, int enable);
 
 /* Accumulated device time (ms) and launch count per kernel kind since the
  * last read, then reset. kinds: 0 level-0 pre-smooth/residual, 1 level-0
- * prolong/post-smooth (+ r.z), 2 q = A p, 3 x/r update, 4 true residual,
- * 5 levels >= 1 incl. restriction and coarsest solve (one span per V-cycle).
- * ms and counts are host arrays of length nkinds (<= 6). */
+ * prolong/post-smooth (+ r.z), 2 q = A p (+ p.q), 3 x/r update, 4 true
+ * residual, 5 levels >= 1 incl. restriction and coarsest solve (one span per
+ * V-cycle), 6 p = z + beta p. ms and counts are host arrays of length
+ * nkinds (<= 7). */
 int amg_profile_read(amg_handle h, double *ms, int64_t *counts, int nkinds);
 
 /* Kernels launched by solves on h since setup (every launch, including the

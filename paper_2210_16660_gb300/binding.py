@@ -262,7 +262,7 @@ class AMG:
             raise AmgError(st, last_error())
         return rp, ci, v
 
-    KINDS = ("down0", "up0", "spmv", "update", "residual", "coarse_levels")
+    KINDS = ("down0", "up0", "spmv", "update", "residual", "coarse_levels", "axpy")
 
     def profile(self, enable: bool = True):
         st = load().amg_profile(self._h, int(enable))
@@ -270,9 +270,9 @@ class AMG:
             raise AmgError(st, last_error())
 
     def profile_read(self) -> dict:
-        ms = np.zeros(6)
-        cnt = np.zeros(6, np.int64)
-        load().amg_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, 6)
+        ms = np.zeros(7)
+        cnt = np.zeros(7, np.int64)
+        load().amg_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, 7)
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KINDS)}
 
     def launch_count(self) -> int:

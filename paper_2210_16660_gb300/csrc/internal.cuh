@@ -91,8 +91,9 @@ struct Level {
     int32_t *ridx = nullptr;
     std::vector<int32_t *> pass_agg;
     std::vector<int> pass_n;  // rows entering pass k; pass_n[npass] = nc
-    // V-cycle work vectors: right-hand side, solution, restricted residual
-    double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr;
+    // V-cycle work vectors: right-hand side, solution, restriction input;
+    // float64 only: D^-1 b (xpre) and the prolongated guess (xp)
+    double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr, *xpre64 = nullptr, *xp64 = nullptr;
     float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr;
 };
 
@@ -130,8 +131,8 @@ struct amg_hier {
     double *Ainv = nullptr;   // inverse of the coarsest matrix, row-major
     double *bL = nullptr;     // coarsest right-hand side in float64
     // Krylov workspace (level-0 length)
-    double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr;
-    double *pv[2] = {nullptr, nullptr};
+    double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr, *p = nullptr;
+    float *r32 = nullptr;        // float32 copy of r read by the float32 V-cycle
     double *partials = nullptr;  // per-block partial sums (several slots)
     double *hist = nullptr;      // device history, maxit_cap + 1
     int hist_cap = 0;
@@ -141,7 +142,7 @@ struct amg_hier {
     double last_true_rel = 0.0;
     double setup_ms[4] = {0, 0, 0, 0};
     // kernel timing (amg_profile)
-    static constexpr int kKinds = 6;
+    static constexpr int kKinds = 7;
     int profile = 0;
     std::vector<cudaEvent_t> ev;      // pool: pairs per kind per iteration of a chunk
     int ev_used = 0;

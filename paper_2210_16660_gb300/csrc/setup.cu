@@ -656,6 +656,8 @@ int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
     PCG_TRY(alloc(M, &lv.b64, n));
     PCG_TRY(alloc(M, &lv.x64, n));
     PCG_TRY(alloc(M, &lv.t64, n));
+    PCG_TRY(alloc(M, &lv.xpre64, n));
+    PCG_TRY(alloc(M, &lv.xp64, n));
     PCG_TRY(alloc(M, &lv.b32, n));
     PCG_TRY(alloc(M, &lv.x32, n));
     PCG_TRY(alloc(M, &lv.t32, n));

@@ -2,20 +2,33 @@
 // (arxiv 2210.16660, Sec. 3.1 Eq. (multiplicative composition) with nu = 1
 // and M = D_l1; Sec. 5 flexible CG with a relative-residual stop).
 //
-// Every kernel streams a sliced-ELL matrix (one warp per 32-row slice,
-// coalesced value/column loads) and fuses the vector work around it:
-//   down  : x = D^-1 b on the fly, t = p .* (b - A x)        (pre-smooth, residual)
-//   restr : b_{l+1}[I] = sum_{i in G_I} t_i, members in index order
-//   coarse: x_L = A_L^{-1} b_L (dense float64 inverse)
-//   up    : x = D^-1 b + P x_{l+1} on the fly, z = x + D^-1 (b - A x)
-//           (prolongation + post-smooth; on level 0 also r.z and z.q_old)
-//   spmv  : p = z + beta p_old on the fly, q = A p, p.q
-//   update: x += alpha p, r -= alpha q, ||r||^2
-//   check : r = b - A x and ||r||^2 when the recursive residual met rtol
+// Every sweep streams a sliced-ELL matrix (one warp per 32-row slice,
+// coalesced value/column loads, 4 entries of a row loaded ahead of their
+// gathers) and fuses the vector work around it.
+//
+// GB300 note: float64 FMA throughput (~1.25 TFLOP/s) is about what one FMA per
+// stored entry needs at full HBM bandwidth, so every float64 sweep does
+// exactly one float64 operation per stored entry; anything else is formed
+// once per row (D^-1 b, D^-1 b + P x_c, p = z + beta p). The float32 V-cycle
+// reads a float32 copy of r so that no conversion happens per entry.
+//
+// float32 V-cycle (FCG(1)):
+//   down  : t = p .* (b - A (D^-1 b))          (D^-1 b formed per entry)
+//   restr : b_{l+1}[I] = sum_{i in G_I} t_i    (members in index order)
+//   coarse: x_L = A_L^{-1} b_L                 (float64 dense inverse)
+//   up    : x = D^-1 b + P x_{l+1}, z = x + D^-1 (b - A x)  (x per entry)
+// float64 V-cycle (PCG):
+//   down  : t = p .* (b - A xpre), xpre = D^-1 b from the producer of b
+//   restr : as above, and xpre_{l+1} = D^-1 b_{l+1}
+//   prolong: xp = xpre + P x_{l+1}
+//   post  : z = xp + D^-1 (b - A xp)
+// Krylov (float64): p = z + beta p; q = A p, p.q; x += alpha p,
+// r -= alpha q, ||r||^2 (+ r32 or xpre_0); true residual when rtol is met.
+//
 // Reductions are two-stage and deterministic: each block writes a partial,
 // the last block to finish (atomic ticket) sums the partials in index order
-// and updates the scalars of the iteration in device memory (struct Ctl), so
-// a whole iteration runs without a host round trip.
+// and updates the iteration's scalars in device memory (struct Ctl), so an
+// iteration needs no host round trip.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,7 +43,7 @@ namespace {
 template <typename T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 
-// Block-wide sum of two doubles (blockDim.x == kBlock); result in thread 0.
+// Block-wide sum of two doubles (blockDim.x == kBlock); result in warp 0.
 __device__ __forceinline__ void block_sum2(double &a, double &b) {
     __shared__ double sa[kBlock / 32], sb[kBlock / 32];
 #pragma unroll
@@ -86,6 +99,19 @@ __device__ __forceinline__ void fail(Ctl *c, int status) {
     c->status = status;
 }
 
+// rho = r.z and beta of the next direction (last block of the kernel that
+// produced z): PCG beta = rho / rho_old, FCG(1) beta = -(z.q_old) / (p.q)_old.
+__device__ __forceinline__ void finish_rho(Ctl *ctl, double rz, double zq) {
+    ctl->counter[0] = 0;
+    if (!isfinite(rz) || !isfinite(zq)) { fail(ctl, AMG_ERR_NAN); return; }
+    if (!(rz > 0.0)) { fail(ctl, AMG_ERR_BREAKDOWN); return; }
+    ctl->rho = rz;
+    ctl->zq = zq;
+    double beta = 0.0;
+    if (!ctl->restart) beta = ctl->mode == AMG_MODE_FCG32 ? -zq / ctl->pq_old : rz / ctl->rho_old;
+    ctl->beta = beta;
+}
+
 // Sum over the stored entries of one sliced-ELL row: acc = sum_k a_k x(j_k),
 // k in storage order. Column/value loads of U entries are issued before their
 // gathers so each warp keeps several independent loads in flight.
@@ -112,39 +138,145 @@ __device__ __forceinline__ T sell_row(const int32_t *__restrict__ c, const T *__
     return acc;
 }
 
-// ------------------------------------------------------------ level kernels
-// Pre-smooth from zero, residual and weighted restriction input:
-// t_i = p_i (b_i - sum_j a_ij dinv_j b_j).
-template <typename T, typename TIO>
+#define SELL_ROW_BEGIN                                               \
+    int s_ = i >> 5, lane_ = i & 31;                                 \
+    int32_t base_ = ldg(sptr + s_);                                  \
+    int w_ = (ldg(sptr + s_ + 1) - base_) >> 5;                      \
+    const int32_t *c_ = col + base_ + lane_;                         \
+    const auto *a_ = val + base_ + lane_;
+
+// ------------------------------------------------------------ float32 V-cycle
+// Pre-smooth from zero, residual, weighted restriction input:
+// t_i = p_i (b_i - sum_j a_ij dinv_j b_j). L0 marks the level-0 instance
+// (same code; a separate symbol for profilers).
+template <typename T, bool L0>
 __global__ void __launch_bounds__(kBlock, 4) k_down(int n, const int32_t *__restrict__ sptr,
-                                                 const int32_t *__restrict__ col, const T *__restrict__ val,
-                                                 const TIO *__restrict__ b, const T *__restrict__ dinv,
-                                                 const T *__restrict__ p, T *__restrict__ t,
-                                                 const Ctl *__restrict__ ctl) {
+                                                    const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                    const T *__restrict__ b, const T *__restrict__ dinv,
+                                                    const T *__restrict__ p, T *__restrict__ t,
+                                                    const Ctl *__restrict__ ctl) {
     if (ctl->done) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int s = i >> 5, lane = i & 31;
-        int32_t base = ldg(sptr + s);
-        int w = (ldg(sptr + s + 1) - base) >> 5;
-        T acc = sell_row(col + base + lane, val + base + lane, w,
-                         [&](int j) { return ldg(dinv + j) * (T)ldg(b + j); });
-        T r = (T)b[i] - acc;
-        t[i] = ldg(p + i) * r;
+        SELL_ROW_BEGIN
+        T acc = sell_row(c_, a_, w_, [&](int j) { return ldg(dinv + j) * ldg(b + j); });
+        t[i] = ldg(p + i) * (ldg(b + i) - acc);
     }
 }
 
-// b_c[I] = sum of t over the members of aggregate I, in increasing index order.
-template <typename T, typename TO>
+// Prolongation + post-smooth: x_j = dinv_j b_j + p_j xc[agg_j] for every
+// column j, z_i = x_i + dinv_i (b_i - sum_j a_ij x_j). On level 0 (DOT) z is
+// written in float64 and the kernel also forms r.z (float64 r) and, for
+// FCG(1), z.q_old; its last block turns them into rho and beta.
+template <typename T, typename TZ, bool DOT, bool FCG>
+__global__ void __launch_bounds__(kBlock, 4) k_up(int n, const int32_t *__restrict__ sptr,
+                                                  const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                  const T *__restrict__ b, const T *__restrict__ dinv,
+                                                  const T *__restrict__ p, const int32_t *__restrict__ agg,
+                                                  const T *__restrict__ xc, TZ *__restrict__ z,
+                                                  const double *__restrict__ r64, const double *__restrict__ qold,
+                                                  double *partials, Ctl *ctl) {
+    if (ctl->done) return;
+    double rz = 0.0, zq = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        SELL_ROW_BEGIN
+        T acc = sell_row(c_, a_, w_, [&](int j) {
+            T xj = ldg(dinv + j) * ldg(b + j);
+            int aj = ldg(agg + j);
+            if (aj >= 0) xj += ldg(p + j) * ldg(xc + aj);
+            return xj;
+        });
+        T bi = ldg(b + i), di = ldg(dinv + i);
+        T xi = di * bi;
+        int ai = ldg(agg + i);
+        if (ai >= 0) xi += ldg(p + i) * ldg(xc + ai);
+        TZ zo = (TZ)(xi + di * (bi - acc));
+        z[i] = zo;
+        if (DOT) {
+            rz += ldg(r64 + i) * (double)zo;
+            if (FCG) zq += (double)zo * ldg(qold + i);
+        }
+    }
+    if (DOT) {
+        if (publish_partials(rz, zq, partials, &ctl->counter[0])) {
+            double a, bb;
+            final_sum2(partials, a, bb);
+            if (threadIdx.x == 0) finish_rho(ctl, a, bb);
+        }
+    }
+}
+
+// ------------------------------------------------------------ float64 V-cycle
+// t_i = p_i (b_i - sum_j a_ij xpre_j), xpre = D^-1 b. L0 as in k_down.
+template <bool L0>
+__global__ void __launch_bounds__(kBlock, 4) k_down_pre(int n, const int32_t *__restrict__ sptr,
+                                                        const int32_t *__restrict__ col,
+                                                        const double *__restrict__ val,
+                                                        const double *__restrict__ xpre,
+                                                        const double *__restrict__ b, const double *__restrict__ p,
+                                                        double *__restrict__ t, const Ctl *__restrict__ ctl) {
+    if (ctl->done) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        SELL_ROW_BEGIN
+        double acc = sell_row(c_, a_, w_, [&](int j) { return ldg(xpre + j); });
+        t[i] = ldg(p + i) * (ldg(b + i) - acc);
+    }
+}
+
+// xp_i = xpre_i + p_i xc[agg_i].
+__global__ void __launch_bounds__(kBlock) k_prolong(int n, const double *__restrict__ xpre,
+                                                    const double *__restrict__ p, const int32_t *__restrict__ agg,
+                                                    const double *__restrict__ xc, double *__restrict__ xp,
+                                                    const Ctl *__restrict__ ctl) {
+    if (ctl->done) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double x = ldg(xpre + i);
+        int a = ldg(agg + i);
+        if (a >= 0) x += ldg(p + i) * ldg(xc + a);
+        xp[i] = x;
+    }
+}
+
+// z_i = xp_i + dinv_i (b_i - sum_j a_ij xp_j); DOT: r.z on level 0 (b = r).
+template <bool DOT>
+__global__ void __launch_bounds__(kBlock, 4) k_post(int n, const int32_t *__restrict__ sptr,
+                                                    const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                    const double *__restrict__ xp, const double *__restrict__ b,
+                                                    const double *__restrict__ dinv, double *__restrict__ z,
+                                                    double *partials, Ctl *ctl) {
+    if (ctl->done) return;
+    double rz = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        SELL_ROW_BEGIN
+        double acc = sell_row(c_, a_, w_, [&](int j) { return ldg(xp + j); });
+        double bi = ldg(b + i);
+        double zi = ldg(xp + i) + ldg(dinv + i) * (bi - acc);
+        z[i] = zi;
+        if (DOT) rz += bi * zi;
+    }
+    if (DOT) {
+        if (publish_partials(rz, 0.0, partials, &ctl->counter[0])) {
+            double a, unused;
+            final_sum2(partials, a, unused);
+            if (threadIdx.x == 0) finish_rho(ctl, a, 0.0);
+        }
+    }
+}
+
+// ------------------------------------------------------------ shared pieces
+// b_c[I] = sum of t over the members of aggregate I, in increasing index
+// order; PRE also forms xpre_c = dinv_c b_c for the next float64 down sweep.
+template <typename T, typename TO, bool PRE>
 __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t *__restrict__ rptr,
-                                                     const int32_t *__restrict__ ridx,
-                                                     const T *__restrict__ t, TO *__restrict__ bc,
-                                                     const Ctl *__restrict__ ctl) {
+                                                     const int32_t *__restrict__ ridx, const T *__restrict__ t,
+                                                     TO *__restrict__ bc, const T *__restrict__ dinvc,
+                                                     T *__restrict__ xprec, const Ctl *__restrict__ ctl) {
     if (ctl->done) return;
     int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
     T s = 0;
     for (int32_t k = ldg(rptr + I); k < ldg(rptr + I + 1); k++) s += ldg(t + ldg(ridx + k));
     bc[I] = (TO)s;
+    if (PRE) xprec[I] = ldg(dinvc + I) * s;
 }
 
 // x_L = A_L^{-1} b_L, one warp per row; TO = float rounds the float64 result.
@@ -163,63 +295,8 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int nL, const double *__restr
     if (lane == 0) xL[row] = (TO)s;
 }
 
-// Prolongation + post-smooth: x_j = dinv_j b_j + p_j xc[agg_j] (formed on
-// the fly for every column j), z_i = x_i + dinv_i (b_i - sum_j a_ij x_j).
-// On level 0 (DOT) also r.z (b = r) and, for FCG, z.q_old; the last block
-// turns them into rho and beta.
-template <typename T, typename TIO, bool DOT, bool FCG>
-__global__ void __launch_bounds__(kBlock, 4) k_up(int n, const int32_t *__restrict__ sptr,
-                                               const int32_t *__restrict__ col, const T *__restrict__ val,
-                                               const TIO *__restrict__ b, const T *__restrict__ dinv,
-                                               const T *__restrict__ p, const int32_t *__restrict__ agg,
-                                               const T *__restrict__ xc, TIO *__restrict__ z,
-                                               const double *__restrict__ qold, double *partials,
-                                               Ctl *ctl) {
-    if (ctl->done) return;
-    double rz = 0.0, zq = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int s = i >> 5, lane = i & 31;
-        int32_t base = ldg(sptr + s);
-        int w = (ldg(sptr + s + 1) - base) >> 5;
-        T acc = sell_row(col + base + lane, val + base + lane, w, [&](int j) {
-            T xj = ldg(dinv + j) * (T)ldg(b + j);
-            int aj = ldg(agg + j);
-            if (aj >= 0) xj += ldg(p + j) * ldg(xc + aj);
-            return xj;
-        });
-        T bi = (T)b[i];
-        T di = ldg(dinv + i);
-        T xi = di * bi;
-        int ai = ldg(agg + i);
-        if (ai >= 0) xi += ldg(p + i) * ldg(xc + ai);
-        T zi = xi + di * (bi - acc);
-        TIO zo = (TIO)zi;
-        z[i] = zo;
-        if (DOT) {
-            rz += (double)b[i] * (double)zo;
-            if (FCG) zq += (double)zo * ldg(qold + i);
-        }
-    }
-    if (DOT) {
-        if (publish_partials(rz, zq, partials, &ctl->counter[0])) {
-            double a, bb;
-            final_sum2(partials, a, bb);
-            if (threadIdx.x == 0) {
-                ctl->counter[0] = 0;
-                if (!isfinite(a) || !isfinite(bb)) { fail(ctl, AMG_ERR_NAN); return; }
-                if (!(a > 0.0)) { fail(ctl, AMG_ERR_BREAKDOWN); return; }
-                ctl->rho = a;
-                ctl->zq = bb;
-                double beta = 0.0;
-                if (!ctl->restart) beta = ctl->mode == AMG_MODE_FCG32 ? -bb / ctl->pq_old : a / ctl->rho_old;
-                ctl->beta = beta;
-            }
-        }
-    }
-}
-
-// Single-level hierarchy: z = A^{-1} r (optionally through float32 as the
-// float32 V-cycle would round it), then r.z / z.q_old as in k_up.
+// Single-level hierarchy: z = A^{-1} r (through float32 as the float32
+// V-cycle would round it when F32), then r.z / z.q_old as on level 0.
 template <bool F32, bool FCG>
 __global__ void __launch_bounds__(kBlock) k_coarse_only(int n, const double *__restrict__ ainv,
                                                         const double *__restrict__ r, double *__restrict__ z,
@@ -249,39 +326,32 @@ __global__ void __launch_bounds__(kBlock) k_coarse_only(int n, const double *__r
     if (publish_partials(rz, zq, partials, &ctl->counter[0])) {
         double a, bb;
         final_sum2(partials, a, bb);
-        if (threadIdx.x == 0) {
-            ctl->counter[0] = 0;
-            if (!isfinite(a) || !isfinite(bb)) { fail(ctl, AMG_ERR_NAN); return; }
-            if (!(a > 0.0)) { fail(ctl, AMG_ERR_BREAKDOWN); return; }
-            ctl->rho = a;
-            ctl->zq = bb;
-            double beta = 0.0;
-            if (!ctl->restart) beta = ctl->mode == AMG_MODE_FCG32 ? -bb / ctl->pq_old : a / ctl->rho_old;
-            ctl->beta = beta;
-        }
+        if (threadIdx.x == 0) finish_rho(ctl, a, bb);
     }
 }
 
 // ------------------------------------------------------------ Krylov kernels
-// p = z + beta p_old (formed on the fly for every column), q = A p, p.q.
-__global__ void __launch_bounds__(kBlock, 4) k_spmv_p(int n, const int32_t *__restrict__ sptr,
-                                                   const int32_t *__restrict__ col,
-                                                   const double *__restrict__ val, const double *__restrict__ z,
-                                                   const double *__restrict__ pold, double *__restrict__ pnew,
-                                                   double *__restrict__ q, double *partials, Ctl *ctl) {
+// p = z + beta p (beta = 0 on a restart gives p = z).
+__global__ void __launch_bounds__(kBlock) k_axpy_p(int n, const double *__restrict__ z, double *__restrict__ p,
+                                                   const Ctl *__restrict__ ctl) {
     if (ctl->done) return;
     double beta = ctl->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+// q = A p and p.q; the last block forms alpha = rho / p.q.
+__global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int32_t *__restrict__ sptr,
+                                                    const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                    const double *__restrict__ p, double *__restrict__ q,
+                                                    double *partials, Ctl *ctl) {
+    if (ctl->done) return;
     double pq = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int s = i >> 5, lane = i & 31;
-        int32_t base = ldg(sptr + s);
-        int w = (ldg(sptr + s + 1) - base) >> 5;
-        double acc = sell_row(col + base + lane, val + base + lane, w,
-                              [&](int j) { return ldg(z + j) + beta * ldg(pold + j); });
-        double pi = ldg(z + i) + beta * ldg(pold + i);
-        pnew[i] = pi;
+        SELL_ROW_BEGIN
+        double acc = sell_row(c_, a_, w_, [&](int j) { return ldg(p + j); });
         q[i] = acc;
-        pq += pi * acc;
+        pq += ldg(p + i) * acc;
     }
     if (publish_partials(pq, 0.0, partials, &ctl->counter[1])) {
         double a, unused;
@@ -296,12 +366,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_spmv_p(int n, const int32_t *__re
     }
 }
 
+// What the V-cycle of the mode reads besides r: FCG32 a float32 copy of r,
+// PCG64 xpre_0 = D_0^{-1} r.
+template <int MODE>
+__device__ __forceinline__ void emit_r(int i, double ri, float *r32, const double *dinv0, double *xpre0) {
+    if (MODE == AMG_MODE_FCG32) r32[i] = (float)ri;
+    else xpre0[i] = ldg(dinv0 + i) * ri;
+}
+
 // x += alpha p, r -= alpha q, ||r||^2; the last block records the relative
 // residual, advances the iteration and decides whether to check the true one.
+template <int MODE>
 __global__ void __launch_bounds__(kBlock) k_update(int n, const double *__restrict__ p,
                                                    const double *__restrict__ q, double *__restrict__ x,
-                                                   double *__restrict__ r, double *partials, Ctl *ctl,
-                                                   double *hist) {
+                                                   double *__restrict__ r, float *__restrict__ r32,
+                                                   const double *__restrict__ dinv0, double *__restrict__ xpre0,
+                                                   double *partials, Ctl *ctl, double *hist) {
     if (ctl->done) return;
     double alpha = ctl->alpha;
     double rr = 0.0;
@@ -309,6 +389,7 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, const double *__restri
         x[i] = x[i] + alpha * p[i];
         double ri = r[i] - alpha * q[i];
         r[i] = ri;
+        emit_r<MODE>(i, ri, r32, dinv0, xpre0);
         rr += ri * ri;
     }
     if (publish_partials(rr, 0.0, partials, &ctl->counter[2])) {
@@ -331,25 +412,26 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, const double *__restri
     }
 }
 
-// r = b - A x and ||r||^2, ||b||^2. INIT: first residual of the solve.
-// Otherwise runs only when the recursive residual met rtol.
-template <bool INIT>
+// r = b - A x, ||r||^2 (and ||b||^2 on INIT); also the mode's copy of r.
+// Otherwise (not INIT) it runs only when the recursive residual met rtol.
+template <bool INIT, int MODE>
 __global__ void __launch_bounds__(kBlock, 4) k_residual(int n, const int32_t *__restrict__ sptr,
-                                                     const int32_t *__restrict__ col,
-                                                     const double *__restrict__ val, const double *__restrict__ b,
-                                                     const double *__restrict__ x, double *__restrict__ r,
-                                                     double *partials, Ctl *ctl, double *hist) {
+                                                        const int32_t *__restrict__ col,
+                                                        const double *__restrict__ val, const double *__restrict__ b,
+                                                        const double *__restrict__ x, double *__restrict__ r,
+                                                        float *__restrict__ r32, const double *__restrict__ dinv0,
+                                                        double *__restrict__ xpre0, double *partials, Ctl *ctl,
+                                                        double *hist) {
     if (ctl->done) return;
     if (!INIT && !ctl->check) return;
     double rr = 0.0, bb = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int s = i >> 5, lane = i & 31;
-        int32_t base = ldg(sptr + s);
-        int w = (ldg(sptr + s + 1) - base) >> 5;
-        double acc = sell_row(col + base + lane, val + base + lane, w, [&](int j) { return ldg(x + j); });
-        double bi = b[i];
+        SELL_ROW_BEGIN
+        double acc = sell_row(c_, a_, w_, [&](int j) { return ldg(x + j); });
+        double bi = ldg(b + i);
         double ri = bi - acc;
         r[i] = ri;
+        emit_r<MODE>(i, ri, r32, dinv0, xpre0);
         rr += ri * ri;
         if (INIT) bb += bi * bi;
     }
@@ -406,8 +488,11 @@ __global__ void k_set_cond(cudaGraphConditionalHandle hc, Ctl *ctl, int count_bo
 
 inline int grid_rows(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
+// ------------------------------------------------------------ profiling
 // CUDA-event spans around kernel launches (only when profiling is on).
-constexpr int kEvPairs = 64;
+// kinds: 0 down0, 1 up0 (float64: prolong0 + post0), 2 q = A p, 3 update,
+// 4 true residual, 5 levels >= 1 and the coarsest solve, 6 p = z + beta p.
+constexpr int kEvPairs = 96;
 
 void prof_begin(amg_hier *h, int kind, cudaStream_t s) {
     if (!h->profile || h->ev_used + 2 > (int)h->ev.size()) return;
@@ -434,114 +519,142 @@ void prof_collect(amg_hier *h) {
 }
 
 // ------------------------------------------------------------ one iteration
-template <typename T>
-struct LevelPtrs;
-template <>
-struct LevelPtrs<double> {
-    static const double *val(const Level &l) { return l.S.v64; }
-    static const double *dinv(const Level &l) { return l.dinv; }
-    static const double *p(const Level &l) { return l.p; }
-    static double *b(Level &l) { return l.b64; }
-    static double *x(Level &l) { return l.x64; }
-    static double *t(Level &l) { return l.t64; }
-};
-template <>
-struct LevelPtrs<float> {
-    static const float *val(const Level &l) { return l.S.v32; }
-    static const float *dinv(const Level &l) { return l.dinv32; }
-    static const float *p(const Level &l) { return l.p32; }
-    static float *b(Level &l) { return l.b32; }
-    static float *x(Level &l) { return l.x32; }
-    static float *t(Level &l) { return l.t32; }
-};
-
-// z = B r (one V-cycle), including rho / beta for the Krylov step.
-template <typename T, bool FCG>
-int launch_vcycle(amg_hier *h, cudaStream_t s) {
-    using LP = LevelPtrs<T>;
+// z = B r with the float32 V-cycle (rho / beta included).
+template <bool FCG>
+int launch_vcycle32(amg_hier *h, cudaStream_t s) {
     auto &lev = h->lev;
     int L = (int)lev.size() - 1;
     Ctl *ctl = h->ctl;
-    if (L == 0) {
-        h->launches += 1;
-        k_coarse_only<std::is_same<T, float>::value, FCG>
-            <<<h->nblk, kBlock, 0, s>>>(h->nL, h->Ainv, h->r, h->z, h->q, h->partials, ctl);
-        PCG_LAUNCH_CK();
-        return AMG_OK;
-    }
-    // down: level 0 reads r (float64)
-    {
-        Level &l0 = lev[0];
-        prof_begin(h, 0, s);
-        k_down<T, double><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, LP::val(l0), h->r,
-                                                     LP::dinv(l0), LP::p(l0), LP::t(l0), ctl);
-        prof_end(h, s);
-    }
+    Level &l0 = lev[0];
+    prof_begin(h, 0, s);
+    k_down<float, true><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, l0.S.v32, h->r32, l0.dinv32, l0.p32,
+                                             l0.t32, ctl);
+    prof_end(h, s);
     prof_begin(h, 5, s);
-    h->launches += 3 * L + 1;
     for (int l = 0; l < L; l++) {
         Level &lv = lev[l];
         if (l > 0)
-            k_down<T, T><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.S.sptr, lv.S.col, LP::val(lv),
-                                                               LP::b(lv), LP::dinv(lv), LP::p(lv), LP::t(lv), ctl);
+            k_down<float, false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.S.sptr, lv.S.col, lv.S.v32, lv.b32,
+                                                                lv.dinv32, lv.p32, lv.t32, ctl);
         if (l + 1 == L)
-            k_restrict<T, double><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, LP::t(lv),
-                                                                      h->bL, ctl);
+            k_restrict<float, double, false><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, lv.t32,
+                                                                                 h->bL, nullptr, nullptr, ctl);
         else
-            k_restrict<T, T><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, LP::t(lv),
-                                                                 LP::b(lev[l + 1]), ctl);
+            k_restrict<float, float, false><<<grid_rows(lv.nc), kBlock, 0, s>>>(
+                lv.nc, lv.rptr, lv.ridx, lv.t32, lev[l + 1].b32, nullptr, nullptr, ctl);
     }
-    k_coarse<T><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, LP::x(lev[L]), ctl);
+    k_coarse<float><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, lev[L].x32, ctl);
     for (int l = L - 1; l >= 1; l--) {
         Level &lv = lev[l];
-        k_up<T, T, false, false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
-            lv.A.n, lv.S.sptr, lv.S.col, LP::val(lv), LP::b(lv), LP::dinv(lv), LP::p(lv), lv.agg,
-            LP::x(lev[l + 1]), LP::x(lv), nullptr, nullptr, ctl);
+        k_up<float, float, false, false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
+            lv.A.n, lv.S.sptr, lv.S.col, lv.S.v32, lv.b32, lv.dinv32, lv.p32, lv.agg, lev[l + 1].x32, lv.x32,
+            nullptr, nullptr, nullptr, ctl);
     }
     prof_end(h, s);
-    {
-        Level &l0 = lev[0];
-        prof_begin(h, 1, s);
-        k_up<T, double, true, FCG><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, LP::val(l0), h->r,
-                                                               LP::dinv(l0), LP::p(l0), l0.agg, LP::x(lev[1]),
-                                                               h->z, h->q, h->partials, ctl);
-        prof_end(h, s);
-    }
+    prof_begin(h, 1, s);
+    k_up<float, double, true, FCG><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, l0.S.v32, h->r32,
+                                                              l0.dinv32, l0.p32, l0.agg, lev[1].x32, h->z, h->r,
+                                                              h->q, h->partials, ctl);
+    prof_end(h, s);
+    h->launches += 3 * L + 1;
     PCG_LAUNCH_CK();
     return AMG_OK;
 }
 
-int launch_iteration(amg_hier *h, int parity, cudaStream_t s) {
-    if (h->mode == AMG_MODE_FCG32) PCG_TRY((launch_vcycle<float, true>(h, s)));
-    else PCG_TRY((launch_vcycle<double, false>(h, s)));
-    Level &l0 = h->lev[0];
-    int n = l0.A.n;
-    double *pold = h->pv[parity], *pnew = h->pv[parity ^ 1];
-    prof_begin(h, 2, s);
-    k_spmv_p<<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->z, pold, pnew, h->q, h->partials,
-                                        h->ctl);
+// z = B r with the float64 V-cycle.
+int launch_vcycle64(amg_hier *h, cudaStream_t s) {
+    auto &lev = h->lev;
+    int L = (int)lev.size() - 1;
+    Ctl *ctl = h->ctl;
+    Level &l0 = lev[0];
+    prof_begin(h, 0, s);
+    k_down_pre<true><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, l0.S.v64, l0.xpre64, h->r, l0.p, l0.t64,
+                                          ctl);
     prof_end(h, s);
-    prof_begin(h, 3, s);
-    k_update<<<h->nblk, kBlock, 0, s>>>(n, pnew, h->q, h->x, h->r, h->partials, h->ctl, h->hist);
+    prof_begin(h, 5, s);
+    for (int l = 0; l < L; l++) {
+        Level &lv = lev[l];
+        if (l > 0)
+            k_down_pre<false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.S.sptr, lv.S.col, lv.S.v64, lv.xpre64,
+                                                            lv.b64, lv.p, lv.t64, ctl);
+        if (l + 1 == L)
+            k_restrict<double, double, false><<<grid_rows(lv.nc), kBlock, 0, s>>>(
+                lv.nc, lv.rptr, lv.ridx, lv.t64, h->bL, nullptr, nullptr, ctl);
+        else
+            k_restrict<double, double, true><<<grid_rows(lv.nc), kBlock, 0, s>>>(
+                lv.nc, lv.rptr, lv.ridx, lv.t64, lev[l + 1].b64, lev[l + 1].dinv, lev[l + 1].xpre64, ctl);
+    }
+    k_coarse<double><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, lev[L].x64, ctl);
+    for (int l = L - 1; l >= 1; l--) {
+        Level &lv = lev[l];
+        k_prolong<<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.xpre64, lv.p, lv.agg, lev[l + 1].x64, lv.xp64,
+                                                       ctl);
+        k_post<false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.S.sptr, lv.S.col, lv.S.v64, lv.xp64, lv.b64,
+                                                           lv.dinv, lv.x64, nullptr, ctl);
+    }
     prof_end(h, s);
-    prof_begin(h, 4, s);
-    k_residual<false><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r,
-                                                 h->partials, h->ctl, h->hist);
+    prof_begin(h, 1, s);
+    k_prolong<<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.xpre64, l0.p, l0.agg, lev[1].x64, l0.xp64, ctl);
+    k_post<true><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, l0.S.v64, l0.xp64, h->r, l0.dinv, h->z,
+                                            h->partials, ctl);
     prof_end(h, s);
-    h->launches += 3;
+    h->launches += 4 * L + 1;
     PCG_LAUNCH_CK();
     return AMG_OK;
+}
+
+template <int MODE>
+int launch_iteration_t(amg_hier *h, cudaStream_t s) {
+    int L = (int)h->lev.size() - 1;
+    Level &l0 = h->lev[0];
+    int n = l0.A.n;
+    if (L == 0) {
+        k_coarse_only<MODE == AMG_MODE_FCG32, MODE == AMG_MODE_FCG32>
+            <<<h->nblk, kBlock, 0, s>>>(h->nL, h->Ainv, h->r, h->z, h->q, h->partials, h->ctl);
+        h->launches += 1;
+    } else if (MODE == AMG_MODE_FCG32) {
+        PCG_TRY(launch_vcycle32<true>(h, s));
+    } else {
+        PCG_TRY(launch_vcycle64(h, s));
+    }
+    prof_begin(h, 6, s);
+    k_axpy_p<<<h->nblk, kBlock, 0, s>>>(n, h->z, h->p, h->ctl);
+    prof_end(h, s);
+    prof_begin(h, 2, s);
+    k_spmv<<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->p, h->q, h->partials, h->ctl);
+    prof_end(h, s);
+    prof_begin(h, 3, s);
+    k_update<MODE><<<h->nblk, kBlock, 0, s>>>(n, h->p, h->q, h->x, h->r, h->r32, l0.dinv, l0.xpre64, h->partials,
+                                              h->ctl, h->hist);
+    prof_end(h, s);
+    prof_begin(h, 4, s);
+    k_residual<false, MODE><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r, h->r32,
+                                                       l0.dinv, l0.xpre64, h->partials, h->ctl, h->hist);
+    prof_end(h, s);
+    h->launches += 4;
+    PCG_LAUNCH_CK();
+    return AMG_OK;
+}
+
+int launch_iteration(amg_hier *h, cudaStream_t s) {
+    if (h->mode == AMG_MODE_FCG32) return launch_iteration_t<AMG_MODE_FCG32>(h, s);
+    return launch_iteration_t<AMG_MODE_PCG64>(h, s);
 }
 
 int launch_prefix(amg_hier *h, cudaStream_t s) {
     Level &l0 = h->lev[0];
     int n = l0.A.n;
-    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->pv[0], n);
-    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->pv[1], n);
+    k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->p, n);
     k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->q, n);
-    k_residual<true><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r, h->partials,
-                                                h->ctl, h->hist);
-    h->launches += 4;
+    if (h->mode == AMG_MODE_FCG32)
+        k_residual<true, AMG_MODE_FCG32><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x,
+                                                                    h->r, h->r32, l0.dinv, l0.xpre64, h->partials,
+                                                                    h->ctl, h->hist);
+    else
+        k_residual<true, AMG_MODE_PCG64><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x,
+                                                                    h->r, h->r32, l0.dinv, l0.xpre64, h->partials,
+                                                                    h->ctl, h->hist);
+    h->launches += 3;
     PCG_LAUNCH_CK();
     return AMG_OK;
 }
@@ -578,7 +691,8 @@ int build_graph(amg_hier *h, int mode) {
         cp.conditional.size = 1;
         e = cudaGraphAddNode(&cnode, g, deps, nullptr, nd, &cp);
     }
-    if (!st && e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (!st && e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
     cudaGraph_t full = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &full);
     int prefix = (int)(h->launches - l0) + 1;
@@ -593,8 +707,8 @@ int build_graph(amg_hier *h, int mode) {
     int64_t l1 = h->launches;
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        st = launch_iteration(h, 0, cs);
-        if (!st) st = launch_iteration(h, 1, cs);
+        st = launch_iteration(h, cs);
+        if (!st) st = launch_iteration(h, cs);
         if (!st) k_set_cond<<<1, 32, 0, cs>>>(hc, h->ctl, 1);
         cudaGraph_t bout = body;
         e = cudaStreamEndCapture(cs, &bout);
@@ -666,10 +780,10 @@ int alloc_solve_workspace(amg_hier *h) {
     PCG_TRY(alloc(M, &h->b, n));
     PCG_TRY(alloc(M, &h->x, n));
     PCG_TRY(alloc(M, &h->r, n));
+    PCG_TRY(alloc(M, &h->r32, n));
     PCG_TRY(alloc(M, &h->z, n));
     PCG_TRY(alloc(M, &h->q, n));
-    PCG_TRY(alloc(M, &h->pv[0], n));
-    PCG_TRY(alloc(M, &h->pv[1], n));
+    PCG_TRY(alloc(M, &h->p, n));
     PCG_TRY(alloc(M, &h->partials, 2 * (size_t)h->nblk));
     PCG_TRY(alloc(M, &h->ctl, 1));
     PCG_CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), M.stream));
@@ -720,17 +834,18 @@ int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, 
         PCG_CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         PCG_CK(cudaStreamSynchronize(s));
         h->launches += h->graph_prefix_kernels + (int64_t)h->ctl_host->bodies * h->graph_body_kernels[h->mode];
-    }
-    if (!graph) PCG_TRY(launch_prefix(h, s));
-    // Iterate in chunks; finished iterations turn every later kernel into a no-op.
-    const int chunk = 4;
-    int launched = graph ? maxit : 0;
-    for (; !graph;) {
-        PCG_CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-        PCG_CK(cudaStreamSynchronize(s));
-        if (h->profile) prof_collect(h);
-        if (h->ctl_host->done || launched >= maxit) break;
-        for (int k = 0; k < chunk && launched < maxit; k++, launched++) PCG_TRY(launch_iteration(h, launched & 1, s));
+    } else {
+        PCG_TRY(launch_prefix(h, s));
+        // Iterate in chunks; once done, every later kernel returns at once.
+        const int chunk = 4;
+        int launched = 0;
+        for (;;) {
+            PCG_CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+            PCG_CK(cudaStreamSynchronize(s));
+            if (h->profile) prof_collect(h);
+            if (h->ctl_host->done || launched >= maxit) break;
+            for (int k = 0; k < chunk && launched < maxit; k++, launched++) PCG_TRY(launch_iteration(h, s));
+        }
     }
     Ctl &c = *h->ctl_host;
     if (c.done == 1 && c.bnorm == 0.0) k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->x, n);
