@@ -153,24 +153,25 @@ def algorithmic_bytes(kind: str, mode: str, n0: int, nnz0: int, n1: int) -> floa
     counted once).
     """
     sptr = 4 * (n0 // 32 + 1)
+    vb = 4 if mode == "fcg32" else 8          # V-cycle value / vector bytes
+    remit = 12 if mode == "fcg32" else 16     # r32 + xpre32 written, dinv32 read | xpre64 written, dinv read
     if kind == "spmv":      # p read, q written; float64 A
         return nnz0 * 12 + n0 * 16 + sptr
     if kind == "axpy":      # z, p read; p written
         return n0 * 24
-    if kind == "update":    # x, p, r, q read; x, r written; + r32 (fcg32) or dinv read, xpre written
-        return n0 * 48 + (4 if mode == "fcg32" else 16) * n0
-    if kind == "residual":  # b, x read; r (+ r32 / xpre) written
-        return nnz0 * 12 + n0 * (24 + (4 if mode == "fcg32" else 16)) + sptr
-    if mode == "fcg32":
-        if kind == "down0":  # r32, dinv, p read; t written (float32 A)
-            return nnz0 * 8 + n0 * 16 + sptr
-        if kind == "up0":    # r32, dinv, p, agg, r, q_old read; z written; x_1 gathered
-            return nnz0 * 8 + n0 * (16 + 8 + 8 + 8) + n1 * 4 + sptr
-    else:
-        if kind == "down0":  # xpre, r, p read; t written (float64 A)
-            return nnz0 * 12 + n0 * 32 + sptr
-        if kind == "up0":    # prolong (xpre, p, agg -> xp) + post (xp, r, dinv -> z)
-            return n0 * 28 + n1 * 8 + nnz0 * 12 + n0 * 32 + sptr
+    if kind == "update":    # x, p, r, q read; x, r written; + the V-cycle's copy of r
+        return n0 * (48 + remit)
+    if kind == "residual":  # b, x read; r written; + the V-cycle's copy of r
+        return nnz0 * 12 + n0 * (24 + remit) + sptr
+    if kind == "down0":     # xpre, b (r32 / r), p read; t written
+        return nnz0 * (vb + 4) + n0 * 4 * vb + sptr
+    if kind == "up0":       # prolong: xpre, p, agg read, xp written, x_1 gathered;
+        #                     post: xp, b, dinv, r64 [, q_old] read, z (float64) written
+        prolong = n0 * (3 * vb + 4) + n1 * vb
+        post = nnz0 * (vb + 4) + n0 * (3 * vb + 8 + 8) + sptr
+        if mode == "fcg32":
+            post += n0 * (8 + 8)             # float64 r for r.z and q_old for z.q_old
+        return prolong + post
     raise KeyError(kind)
 
 

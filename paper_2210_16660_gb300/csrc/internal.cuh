@@ -91,10 +91,10 @@ struct Level {
     int32_t *ridx = nullptr;
     std::vector<int32_t *> pass_agg;
     std::vector<int> pass_n;  // rows entering pass k; pass_n[npass] = nc
-    // V-cycle work vectors: right-hand side, solution, restriction input;
-    // float64 only: D^-1 b (xpre) and the prolongated guess (xp)
+    // V-cycle work vectors: right-hand side, solution, restriction input,
+    // D^-1 b (xpre) and the prolongated guess (xp)
     double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr, *xpre64 = nullptr, *xp64 = nullptr;
-    float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr;
+    float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *xpre32 = nullptr, *xp32 = nullptr;
 };
 
 // Device-resident Krylov state; every scalar of the iteration lives here so

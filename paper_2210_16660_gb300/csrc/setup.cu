@@ -661,6 +661,8 @@ int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
     PCG_TRY(alloc(M, &lv.b32, n));
     PCG_TRY(alloc(M, &lv.x32, n));
     PCG_TRY(alloc(M, &lv.t32, n));
+    PCG_TRY(alloc(M, &lv.xpre32, n));
+    PCG_TRY(alloc(M, &lv.xp32, n));
     if (!coarsest) {
         PCG_TRY(alloc(M, &lv.p32, n));
         k_to_f32<<<grid_for(n), kBlock, 0, s>>>(lv.p, lv.p32, n);

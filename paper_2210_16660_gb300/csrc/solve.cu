@@ -10,18 +10,16 @@
 // stored entry needs at full HBM bandwidth, so every float64 sweep does
 // exactly one float64 operation per stored entry; anything else is formed
 // once per row (D^-1 b, D^-1 b + P x_c, p = z + beta p). The float32 V-cycle
-// reads a float32 copy of r so that no conversion happens per entry.
+// reads a float32 copy of r (and of D^-1 r) so no conversion happens per entry.
 //
-// float32 V-cycle (FCG(1)):
-//   down  : t = p .* (b - A (D^-1 b))          (D^-1 b formed per entry)
-//   restr : b_{l+1}[I] = sum_{i in G_I} t_i    (members in index order)
-//   coarse: x_L = A_L^{-1} b_L                 (float64 dense inverse)
-//   up    : x = D^-1 b + P x_{l+1}, z = x + D^-1 (b - A x)  (x per entry)
-// float64 V-cycle (PCG):
-//   down  : t = p .* (b - A xpre), xpre = D^-1 b from the producer of b
-//   restr : as above, and xpre_{l+1} = D^-1 b_{l+1}
+// V-cycle (T = float for FCG(1), double for PCG; one structure for both):
+//   down   : t = p .* (b - A xpre), xpre = D^-1 b formed by the producer of b
+//   restr  : b_{l+1}[I] = sum_{i in G_I} t_i (members in index order), and
+//            xpre_{l+1} = D^-1 b_{l+1}
+//   coarse : x_L = A_L^{-1} b_L (float64 dense inverse)
 //   prolong: xp = xpre + P x_{l+1}
-//   post  : z = xp + D^-1 (b - A xp)
+//   post   : z = xp + D^-1 (b - A xp)
+// so every sweep gathers one vector per stored entry.
 // Krylov (float64): p = z + beta p; q = A p, p.q; x += alpha p,
 // r -= alpha q, ||r||^2 (+ r32 or xpre_0); true residual when rtol is met.
 //
@@ -114,25 +112,29 @@ __device__ __forceinline__ void finish_rho(Ctl *ctl, double rz, double zq) {
 
 // Sum over the stored entries of one sliced-ELL row: acc = sum_k a_k x(j_k),
 // k in storage order. Column/value loads of U entries are issued before their
-// gathers so each warp keeps several independent loads in flight.
+// gathers so each warp keeps several independent loads in flight. Large
+// levels use U = 4 (bandwidth-bound, keeps registers low); small levels
+// U = 16 so a row's loads take about two dependent round trips.
 constexpr int kUnroll = 4;
+constexpr int kUnrollSmall = 16;
+constexpr int kSmallRows = 65536;
 
-template <typename T, typename F>
+template <int U, typename T, typename F>
 __device__ __forceinline__ T sell_row(const int32_t *__restrict__ c, const T *__restrict__ a, int w, F xval) {
     T acc = 0;
     int k = 0;
-    for (; k + kUnroll <= w; k += kUnroll) {
-        int j[kUnroll];
-        T v[kUnroll], x[kUnroll];
+    for (; k + U <= w; k += U) {
+        int j[U];
+        T v[U], x[U];
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
+        for (int u = 0; u < U; u++) {
             j[u] = __ldg(c + 32 * (k + u));
             v[u] = __ldg(a + 32 * (k + u));
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) x[u] = xval(j[u]);
+        for (int u = 0; u < U; u++) x[u] = xval(j[u]);
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) acc += v[u] * x[u];
+        for (int u = 0; u < U; u++) acc += v[u] * x[u];
     }
     for (; k < w; k++) acc += __ldg(a + 32 * k) * xval(__ldg(c + 32 * k));
     return acc;
@@ -145,51 +147,54 @@ __device__ __forceinline__ T sell_row(const int32_t *__restrict__ c, const T *__
     const int32_t *c_ = col + base_ + lane_;                         \
     const auto *a_ = val + base_ + lane_;
 
-// ------------------------------------------------------------ float32 V-cycle
+// ------------------------------------------------------------ V-cycle sweeps
+template <typename T>
+struct Occ { static constexpr int kMinBlocks = sizeof(T) == 4 ? 6 : 4; };
+
 // Pre-smooth from zero, residual, weighted restriction input:
-// t_i = p_i (b_i - sum_j a_ij dinv_j b_j). L0 marks the level-0 instance
-// (same code; a separate symbol for profilers).
-template <typename T, bool L0>
-__global__ void __launch_bounds__(kBlock, 4) k_down(int n, const int32_t *__restrict__ sptr,
-                                                    const int32_t *__restrict__ col, const T *__restrict__ val,
-                                                    const T *__restrict__ b, const T *__restrict__ dinv,
-                                                    const T *__restrict__ p, T *__restrict__ t,
-                                                    const Ctl *__restrict__ ctl) {
+// t_i = p_i (b_i - sum_j a_ij xpre_j), xpre = D^-1 b. L0 marks the level-0
+// instance (same code; a separate symbol for profilers).
+template <typename T, bool L0, int U>
+__global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_down(
+    int n, const int32_t *__restrict__ sptr, const int32_t *__restrict__ col, const T *__restrict__ val,
+    const T *__restrict__ xpre, const T *__restrict__ b, const T *__restrict__ p, T *__restrict__ t,
+    const Ctl *__restrict__ ctl) {
     if (ctl->done) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         SELL_ROW_BEGIN
-        T acc = sell_row(c_, a_, w_, [&](int j) { return ldg(dinv + j) * ldg(b + j); });
+        T acc = sell_row<U>(c_, a_, w_, [&](int j) { return ldg(xpre + j); });
         t[i] = ldg(p + i) * (ldg(b + i) - acc);
     }
 }
 
-// Prolongation + post-smooth: x_j = dinv_j b_j + p_j xc[agg_j] for every
-// column j, z_i = x_i + dinv_i (b_i - sum_j a_ij x_j). On level 0 (DOT) z is
-// written in float64 and the kernel also forms r.z (float64 r) and, for
+// xp_i = xpre_i + p_i xc[agg_i].
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_prolong(int n, const T *__restrict__ xpre, const T *__restrict__ p,
+                                                    const int32_t *__restrict__ agg, const T *__restrict__ xc,
+                                                    T *__restrict__ xp, const Ctl *__restrict__ ctl) {
+    if (ctl->done) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T x = ldg(xpre + i);
+        int a = ldg(agg + i);
+        if (a >= 0) x += ldg(p + i) * ldg(xc + a);
+        xp[i] = x;
+    }
+}
+
+// Post-smooth z_i = xp_i + dinv_i (b_i - sum_j a_ij xp_j). On level 0 (DOT)
+// z is written in float64 and the kernel also forms r.z (float64 r) and, for
 // FCG(1), z.q_old; its last block turns them into rho and beta.
-template <typename T, typename TZ, bool DOT, bool FCG>
-__global__ void __launch_bounds__(kBlock, 4) k_up(int n, const int32_t *__restrict__ sptr,
-                                                  const int32_t *__restrict__ col, const T *__restrict__ val,
-                                                  const T *__restrict__ b, const T *__restrict__ dinv,
-                                                  const T *__restrict__ p, const int32_t *__restrict__ agg,
-                                                  const T *__restrict__ xc, TZ *__restrict__ z,
-                                                  const double *__restrict__ r64, const double *__restrict__ qold,
-                                                  double *partials, Ctl *ctl) {
+template <typename T, typename TZ, bool DOT, bool FCG, int U>
+__global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_post(
+    int n, const int32_t *__restrict__ sptr, const int32_t *__restrict__ col, const T *__restrict__ val,
+    const T *__restrict__ xp, const T *__restrict__ b, const T *__restrict__ dinv, TZ *__restrict__ z,
+    const double *__restrict__ r64, const double *__restrict__ qold, double *partials, Ctl *ctl) {
     if (ctl->done) return;
     double rz = 0.0, zq = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         SELL_ROW_BEGIN
-        T acc = sell_row(c_, a_, w_, [&](int j) {
-            T xj = ldg(dinv + j) * ldg(b + j);
-            int aj = ldg(agg + j);
-            if (aj >= 0) xj += ldg(p + j) * ldg(xc + aj);
-            return xj;
-        });
-        T bi = ldg(b + i), di = ldg(dinv + i);
-        T xi = di * bi;
-        int ai = ldg(agg + i);
-        if (ai >= 0) xi += ldg(p + i) * ldg(xc + ai);
-        TZ zo = (TZ)(xi + di * (bi - acc));
+        T acc = sell_row<U>(c_, a_, w_, [&](int j) { return ldg(xp + j); });
+        TZ zo = (TZ)(ldg(xp + i) + ldg(dinv + i) * (ldg(b + i) - acc));
         z[i] = zo;
         if (DOT) {
             rz += ldg(r64 + i) * (double)zo;
@@ -201,63 +206,6 @@ __global__ void __launch_bounds__(kBlock, 4) k_up(int n, const int32_t *__restri
             double a, bb;
             final_sum2(partials, a, bb);
             if (threadIdx.x == 0) finish_rho(ctl, a, bb);
-        }
-    }
-}
-
-// ------------------------------------------------------------ float64 V-cycle
-// t_i = p_i (b_i - sum_j a_ij xpre_j), xpre = D^-1 b. L0 as in k_down.
-template <bool L0>
-__global__ void __launch_bounds__(kBlock, 4) k_down_pre(int n, const int32_t *__restrict__ sptr,
-                                                        const int32_t *__restrict__ col,
-                                                        const double *__restrict__ val,
-                                                        const double *__restrict__ xpre,
-                                                        const double *__restrict__ b, const double *__restrict__ p,
-                                                        double *__restrict__ t, const Ctl *__restrict__ ctl) {
-    if (ctl->done) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        SELL_ROW_BEGIN
-        double acc = sell_row(c_, a_, w_, [&](int j) { return ldg(xpre + j); });
-        t[i] = ldg(p + i) * (ldg(b + i) - acc);
-    }
-}
-
-// xp_i = xpre_i + p_i xc[agg_i].
-__global__ void __launch_bounds__(kBlock) k_prolong(int n, const double *__restrict__ xpre,
-                                                    const double *__restrict__ p, const int32_t *__restrict__ agg,
-                                                    const double *__restrict__ xc, double *__restrict__ xp,
-                                                    const Ctl *__restrict__ ctl) {
-    if (ctl->done) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double x = ldg(xpre + i);
-        int a = ldg(agg + i);
-        if (a >= 0) x += ldg(p + i) * ldg(xc + a);
-        xp[i] = x;
-    }
-}
-
-// z_i = xp_i + dinv_i (b_i - sum_j a_ij xp_j); DOT: r.z on level 0 (b = r).
-template <bool DOT>
-__global__ void __launch_bounds__(kBlock, 4) k_post(int n, const int32_t *__restrict__ sptr,
-                                                    const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                    const double *__restrict__ xp, const double *__restrict__ b,
-                                                    const double *__restrict__ dinv, double *__restrict__ z,
-                                                    double *partials, Ctl *ctl) {
-    if (ctl->done) return;
-    double rz = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        SELL_ROW_BEGIN
-        double acc = sell_row(c_, a_, w_, [&](int j) { return ldg(xp + j); });
-        double bi = ldg(b + i);
-        double zi = ldg(xp + i) + ldg(dinv + i) * (bi - acc);
-        z[i] = zi;
-        if (DOT) rz += bi * zi;
-    }
-    if (DOT) {
-        if (publish_partials(rz, 0.0, partials, &ctl->counter[0])) {
-            double a, unused;
-            final_sum2(partials, a, unused);
-            if (threadIdx.x == 0) finish_rho(ctl, a, 0.0);
         }
     }
 }
@@ -349,7 +297,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int32_t *__rest
     double pq = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         SELL_ROW_BEGIN
-        double acc = sell_row(c_, a_, w_, [&](int j) { return ldg(p + j); });
+        double acc = sell_row<kUnroll>(c_, a_, w_, [&](int j) { return ldg(p + j); });
         q[i] = acc;
         pq += ldg(p + i) * acc;
     }
@@ -366,12 +314,26 @@ __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int32_t *__rest
     }
 }
 
-// What the V-cycle of the mode reads besides r: FCG32 a float32 copy of r,
-// PCG64 xpre_0 = D_0^{-1} r.
+// What the V-cycle of the mode reads besides r: FCG32 a float32 copy of r
+// and xpre_0 = D_0^{-1} r in float32 (as the float32 V-cycle forms them);
+// PCG64 xpre_0 = D_0^{-1} r in float64.
+struct REmit {
+    float *r32;
+    const float *dinv32;
+    float *xpre32;
+    const double *dinv64;
+    double *xpre64;
+};
+
 template <int MODE>
-__device__ __forceinline__ void emit_r(int i, double ri, float *r32, const double *dinv0, double *xpre0) {
-    if (MODE == AMG_MODE_FCG32) r32[i] = (float)ri;
-    else xpre0[i] = ldg(dinv0 + i) * ri;
+__device__ __forceinline__ void emit_r(int i, double ri, const REmit &e) {
+    if (MODE == AMG_MODE_FCG32) {
+        float r = (float)ri;
+        e.r32[i] = r;
+        e.xpre32[i] = ldg(e.dinv32 + i) * r;
+    } else {
+        e.xpre64[i] = ldg(e.dinv64 + i) * ri;
+    }
 }
 
 // x += alpha p, r -= alpha q, ||r||^2; the last block records the relative
@@ -379,9 +341,8 @@ __device__ __forceinline__ void emit_r(int i, double ri, float *r32, const doubl
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) k_update(int n, const double *__restrict__ p,
                                                    const double *__restrict__ q, double *__restrict__ x,
-                                                   double *__restrict__ r, float *__restrict__ r32,
-                                                   const double *__restrict__ dinv0, double *__restrict__ xpre0,
-                                                   double *partials, Ctl *ctl, double *hist) {
+                                                   double *__restrict__ r, REmit em, double *partials, Ctl *ctl,
+                                                   double *hist) {
     if (ctl->done) return;
     double alpha = ctl->alpha;
     double rr = 0.0;
@@ -389,7 +350,7 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, const double *__restri
         x[i] = x[i] + alpha * p[i];
         double ri = r[i] - alpha * q[i];
         r[i] = ri;
-        emit_r<MODE>(i, ri, r32, dinv0, xpre0);
+        emit_r<MODE>(i, ri, em);
         rr += ri * ri;
     }
     if (publish_partials(rr, 0.0, partials, &ctl->counter[2])) {
@@ -419,19 +380,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_residual(int n, const int32_t *__
                                                         const int32_t *__restrict__ col,
                                                         const double *__restrict__ val, const double *__restrict__ b,
                                                         const double *__restrict__ x, double *__restrict__ r,
-                                                        float *__restrict__ r32, const double *__restrict__ dinv0,
-                                                        double *__restrict__ xpre0, double *partials, Ctl *ctl,
-                                                        double *hist) {
+                                                        REmit em, double *partials, Ctl *ctl, double *hist) {
     if (ctl->done) return;
     if (!INIT && !ctl->check) return;
     double rr = 0.0, bb = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         SELL_ROW_BEGIN
-        double acc = sell_row(c_, a_, w_, [&](int j) { return ldg(x + j); });
+        double acc = sell_row<kUnroll>(c_, a_, w_, [&](int j) { return ldg(x + j); });
         double bi = ldg(b + i);
         double ri = bi - acc;
         r[i] = ri;
-        emit_r<MODE>(i, ri, r32, dinv0, xpre0);
+        emit_r<MODE>(i, ri, em);
         rr += ri * ri;
         if (INIT) bb += bi * bi;
     }
@@ -490,7 +449,7 @@ inline int grid_rows(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
 // ------------------------------------------------------------ profiling
 // CUDA-event spans around kernel launches (only when profiling is on).
-// kinds: 0 down0, 1 up0 (float64: prolong0 + post0), 2 q = A p, 3 update,
+// kinds: 0 down0, 1 up0 (prolong0 + post0), 2 q = A p, 3 update,
 // 4 true residual, 5 levels >= 1 and the coarsest solve, 6 p = z + beta p.
 constexpr int kEvPairs = 96;
 
@@ -519,84 +478,87 @@ void prof_collect(amg_hier *h) {
 }
 
 // ------------------------------------------------------------ one iteration
-// z = B r with the float32 V-cycle (rho / beta included).
-template <bool FCG>
-int launch_vcycle32(amg_hier *h, cudaStream_t s) {
-    auto &lev = h->lev;
-    int L = (int)lev.size() - 1;
-    Ctl *ctl = h->ctl;
-    Level &l0 = lev[0];
-    prof_begin(h, 0, s);
-    k_down<float, true><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, l0.S.v32, h->r32, l0.dinv32, l0.p32,
-                                             l0.t32, ctl);
-    prof_end(h, s);
-    prof_begin(h, 5, s);
-    for (int l = 0; l < L; l++) {
-        Level &lv = lev[l];
-        if (l > 0)
-            k_down<float, false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.S.sptr, lv.S.col, lv.S.v32, lv.b32,
-                                                                lv.dinv32, lv.p32, lv.t32, ctl);
-        if (l + 1 == L)
-            k_restrict<float, double, false><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, lv.t32,
-                                                                                 h->bL, nullptr, nullptr, ctl);
-        else
-            k_restrict<float, float, false><<<grid_rows(lv.nc), kBlock, 0, s>>>(
-                lv.nc, lv.rptr, lv.ridx, lv.t32, lev[l + 1].b32, nullptr, nullptr, ctl);
-    }
-    k_coarse<float><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, lev[L].x32, ctl);
-    for (int l = L - 1; l >= 1; l--) {
-        Level &lv = lev[l];
-        k_up<float, float, false, false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
-            lv.A.n, lv.S.sptr, lv.S.col, lv.S.v32, lv.b32, lv.dinv32, lv.p32, lv.agg, lev[l + 1].x32, lv.x32,
-            nullptr, nullptr, nullptr, ctl);
-    }
-    prof_end(h, s);
-    prof_begin(h, 1, s);
-    k_up<float, double, true, FCG><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, l0.S.v32, h->r32,
-                                                              l0.dinv32, l0.p32, l0.agg, lev[1].x32, h->z, h->r,
-                                                              h->q, h->partials, ctl);
-    prof_end(h, s);
-    h->launches += 3 * L + 1;
-    PCG_LAUNCH_CK();
-    return AMG_OK;
+template <typename T>
+struct LP;
+template <>
+struct LP<float> {
+    static const float *val(const Level &l) { return l.S.v32; }
+    static const float *dinv(const Level &l) { return l.dinv32; }
+    static const float *p(const Level &l) { return l.p32; }
+    static float *b(Level &l) { return l.b32; }
+    static float *x(Level &l) { return l.x32; }
+    static float *t(Level &l) { return l.t32; }
+    static float *xpre(Level &l) { return l.xpre32; }
+    static float *xp(Level &l) { return l.xp32; }
+    static const float *r0(const amg_hier *h) { return h->r32; }
+};
+template <>
+struct LP<double> {
+    static const double *val(const Level &l) { return l.S.v64; }
+    static const double *dinv(const Level &l) { return l.dinv; }
+    static const double *p(const Level &l) { return l.p; }
+    static double *b(Level &l) { return l.b64; }
+    static double *x(Level &l) { return l.x64; }
+    static double *t(Level &l) { return l.t64; }
+    static double *xpre(Level &l) { return l.xpre64; }
+    static double *xp(Level &l) { return l.xp64; }
+    static const double *r0(const amg_hier *h) { return h->r; }
+};
+
+REmit remit(amg_hier *h) {
+    Level &l0 = h->lev[0];
+    return REmit{h->r32, l0.dinv32, l0.xpre32, l0.dinv, l0.xpre64};
 }
 
-// z = B r with the float64 V-cycle.
-int launch_vcycle64(amg_hier *h, cudaStream_t s) {
+// z = B r (one V-cycle in precision T), including rho / beta.
+template <typename T, bool FCG>
+int launch_vcycle(amg_hier *h, cudaStream_t s) {
+    using P = LP<T>;
     auto &lev = h->lev;
     int L = (int)lev.size() - 1;
     Ctl *ctl = h->ctl;
     Level &l0 = lev[0];
+    const T *b0 = P::r0(h);
     prof_begin(h, 0, s);
-    k_down_pre<true><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, l0.S.v64, l0.xpre64, h->r, l0.p, l0.t64,
-                                          ctl);
+    k_down<T, true, kUnroll><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, P::val(l0), P::xpre(l0), b0, P::p(l0),
+                                               P::t(l0), ctl);
     prof_end(h, s);
     prof_begin(h, 5, s);
     for (int l = 0; l < L; l++) {
         Level &lv = lev[l];
-        if (l > 0)
-            k_down_pre<false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.S.sptr, lv.S.col, lv.S.v64, lv.xpre64,
-                                                            lv.b64, lv.p, lv.t64, ctl);
+        if (l > 0 && lv.A.n > kSmallRows)
+            k_down<T, false, kUnroll><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
+                lv.A.n, lv.S.sptr, lv.S.col, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl);
+        else if (l > 0)
+            k_down<T, false, kUnrollSmall><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
+                lv.A.n, lv.S.sptr, lv.S.col, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl);
         if (l + 1 == L)
-            k_restrict<double, double, false><<<grid_rows(lv.nc), kBlock, 0, s>>>(
-                lv.nc, lv.rptr, lv.ridx, lv.t64, h->bL, nullptr, nullptr, ctl);
+            k_restrict<T, double, false><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, P::t(lv),
+                                                                             h->bL, nullptr, nullptr, ctl);
         else
-            k_restrict<double, double, true><<<grid_rows(lv.nc), kBlock, 0, s>>>(
-                lv.nc, lv.rptr, lv.ridx, lv.t64, lev[l + 1].b64, lev[l + 1].dinv, lev[l + 1].xpre64, ctl);
+            k_restrict<T, T, true><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, P::t(lv),
+                                                                       P::b(lev[l + 1]), P::dinv(lev[l + 1]),
+                                                                       P::xpre(lev[l + 1]), ctl);
     }
-    k_coarse<double><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, lev[L].x64, ctl);
+    k_coarse<T><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, P::x(lev[L]), ctl);
     for (int l = L - 1; l >= 1; l--) {
         Level &lv = lev[l];
-        k_prolong<<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.xpre64, lv.p, lv.agg, lev[l + 1].x64, lv.xp64,
-                                                       ctl);
-        k_post<false><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, lv.S.sptr, lv.S.col, lv.S.v64, lv.xp64, lv.b64,
-                                                           lv.dinv, lv.x64, nullptr, ctl);
+        k_prolong<T><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, P::xpre(lv), P::p(lv), lv.agg, P::x(lev[l + 1]),
+                                                          P::xp(lv), ctl);
+        if (lv.A.n > kSmallRows)
+            k_post<T, T, false, false, kUnroll><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
+                lv.A.n, lv.S.sptr, lv.S.col, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv), nullptr,
+                nullptr, nullptr, ctl);
+        else
+            k_post<T, T, false, false, kUnrollSmall><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
+                lv.A.n, lv.S.sptr, lv.S.col, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv), nullptr,
+                nullptr, nullptr, ctl);
     }
     prof_end(h, s);
     prof_begin(h, 1, s);
-    k_prolong<<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.xpre64, l0.p, l0.agg, lev[1].x64, l0.xp64, ctl);
-    k_post<true><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, l0.S.v64, l0.xp64, h->r, l0.dinv, h->z,
-                                            h->partials, ctl);
+    k_prolong<T><<<h->nblk, kBlock, 0, s>>>(l0.A.n, P::xpre(l0), P::p(l0), l0.agg, P::x(lev[1]), P::xp(l0), ctl);
+    k_post<T, double, true, FCG, kUnroll><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, P::val(l0), P::xp(l0), b0,
+                                                            P::dinv(l0), h->z, h->r, h->q, h->partials, ctl);
     prof_end(h, s);
     h->launches += 4 * L + 1;
     PCG_LAUNCH_CK();
@@ -613,9 +575,9 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
             <<<h->nblk, kBlock, 0, s>>>(h->nL, h->Ainv, h->r, h->z, h->q, h->partials, h->ctl);
         h->launches += 1;
     } else if (MODE == AMG_MODE_FCG32) {
-        PCG_TRY(launch_vcycle32<true>(h, s));
+        PCG_TRY((launch_vcycle<float, true>(h, s)));
     } else {
-        PCG_TRY(launch_vcycle64(h, s));
+        PCG_TRY((launch_vcycle<double, false>(h, s)));
     }
     prof_begin(h, 6, s);
     k_axpy_p<<<h->nblk, kBlock, 0, s>>>(n, h->z, h->p, h->ctl);
@@ -624,12 +586,11 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
     k_spmv<<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->p, h->q, h->partials, h->ctl);
     prof_end(h, s);
     prof_begin(h, 3, s);
-    k_update<MODE><<<h->nblk, kBlock, 0, s>>>(n, h->p, h->q, h->x, h->r, h->r32, l0.dinv, l0.xpre64, h->partials,
-                                              h->ctl, h->hist);
+    k_update<MODE><<<h->nblk, kBlock, 0, s>>>(n, h->p, h->q, h->x, h->r, remit(h), h->partials, h->ctl, h->hist);
     prof_end(h, s);
     prof_begin(h, 4, s);
-    k_residual<false, MODE><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r, h->r32,
-                                                       l0.dinv, l0.xpre64, h->partials, h->ctl, h->hist);
+    k_residual<false, MODE><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r,
+                                                       remit(h), h->partials, h->ctl, h->hist);
     prof_end(h, s);
     h->launches += 4;
     PCG_LAUNCH_CK();
@@ -648,12 +609,10 @@ int launch_prefix(amg_hier *h, cudaStream_t s) {
     k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->q, n);
     if (h->mode == AMG_MODE_FCG32)
         k_residual<true, AMG_MODE_FCG32><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x,
-                                                                    h->r, h->r32, l0.dinv, l0.xpre64, h->partials,
-                                                                    h->ctl, h->hist);
+                                                                    h->r, remit(h), h->partials, h->ctl, h->hist);
     else
         k_residual<true, AMG_MODE_PCG64><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x,
-                                                                    h->r, h->r32, l0.dinv, l0.xpre64, h->partials,
-                                                                    h->ctl, h->hist);
+                                                                    h->r, remit(h), h->partials, h->ctl, h->hist);
     h->launches += 3;
     PCG_LAUNCH_CK();
     return AMG_OK;
