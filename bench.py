@@ -145,30 +145,30 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- roofline
-def algorithmic_bytes(kind: str, mode: str, n0: int, nnz0: int, n1: int) -> float:
+def algorithmic_bytes(kind: str, mode: str, n0: int, nnz0: int, n1: int, ib: int = 4) -> float:
     """Compulsory bytes of one launch of a level-0 kernel (each array once).
 
-    Matrix: value + int32 column per stored entry, one int32 slice pointer
-    per 32 rows. Vectors as the kernels read/write them (gathered vectors
+    Matrix: value + column (ib = 2 bytes for int16 offsets, else 4) per
+    stored entry, one int32 slice pointer per 32 rows. Vectors as the kernels read/write them (gathered vectors
     counted once).
     """
     sptr = 4 * (n0 // 32 + 1)
     vb = 4 if mode == "fcg32" else 8          # V-cycle value / vector bytes
     remit = 12 if mode == "fcg32" else 16     # r32 + xpre32 written, dinv32 read | xpre64 written, dinv read
     if kind == "spmv":      # p read, q written; float64 A
-        return nnz0 * 12 + n0 * 16 + sptr
+        return nnz0 * (8 + ib) + n0 * 16 + sptr
     if kind == "axpy":      # z, p read; p written
         return n0 * 24
     if kind == "update":    # x, p, r, q read; x, r written; + the V-cycle's copy of r
         return n0 * (48 + remit)
     if kind == "residual":  # b, x read; r written; + the V-cycle's copy of r
-        return nnz0 * 12 + n0 * (24 + remit) + sptr
+        return nnz0 * (8 + ib) + n0 * (24 + remit) + sptr
     if kind == "down0":     # xpre, b (r32 / r), p read; t written
-        return nnz0 * (vb + 4) + n0 * 4 * vb + sptr
+        return nnz0 * (vb + ib) + n0 * 4 * vb + sptr
     if kind == "up0":       # prolong: xpre, p, agg read, xp written, x_1 gathered;
         #                     post: xp, b, dinv, r64 [, q_old] read, z (float64) written
         prolong = n0 * (3 * vb + 4) + n1 * vb
-        post = nnz0 * (vb + 4) + n0 * (3 * vb + 8 + 8) + sptr
+        post = nnz0 * (vb + ib) + n0 * (3 * vb + 8 + 8) + sptr
         if mode == "fcg32":
             post += n0 * (8 + 8)             # float64 r for r.z and q_old for z.q_old
         return prolong + post
@@ -387,6 +387,7 @@ def run_ours(args):
     peaks = measured_peaks()
     n0, nnz0 = levels[0]
     n1 = levels[1][0] if len(levels) > 1 else 0
+    ib0 = amg.level_layout(0)["index_bytes"]
     peak = peaks.get("hbm_gbs")
     peak_src = "measured"
     if not peak:
@@ -402,7 +403,7 @@ def run_ours(args):
                 continue
             entry = {"avg_ms": ms / cnt, "launches": cnt, "share_of_profiled": ms / prof[mode]["total_ms"]}
             if k != "coarse_levels":
-                bl = algorithmic_bytes(k, mode, n0, nnz0, n1)
+                bl = algorithmic_bytes(k, mode, n0, nnz0, n1, ib0)
                 entry["algorithmic_bytes"] = bl
                 entry["gbs"] = bl / (ms / cnt * 1e-3) / 1e9
                 entry["frac_of_hbm"] = entry["gbs"] / peak
@@ -430,6 +431,7 @@ def run_ours(args):
             "config": {"workload": f"q1_hex_{args.N}^3_zgrade{args.ratio}", "n": n0, "nnz": nnz0,
                        "rtol": args.rtol, "mode": "fcg32 (float32 V-cycle in float64 FCG(1))",
                        "n_pass": 2, "coarse_max": 200, "levels": len(levels), "nrhs_cycled": args.nrhs,
+                       "layout": [amg.level_layout(l) for l in range(len(levels))],
                        "l2": "inputs larger than L2 (level-0 matrix 0.66 GB float64 + 0.44 GB float32)",
                        "parallelism": f"replicas x{world}"},
             "iters": {"median": statistics.median(m["iters"]), "min": min(m["iters"]), "max": max(m["iters"])},

@@ -135,6 +135,12 @@ int amg_info(amg_handle h, int *levels, int64_t *n_l, int64_t *nnz_l);
 int amg_level_agg(amg_handle h, int level, int pass, int32_t *agg, int64_t *n_out,
                   int64_t *nc_out);
 
+/* Stored layout of level l's matrix as the solve kernels read it: sliced
+ * ELL with slice height *slice (32), *stored entries including padding, and
+ * *index_bytes per entry (2 when every |col - row| < 2^15 so columns are kept
+ * as int16 offsets from the row, else 4). Any pointer may be NULL. */
+int amg_level_layout(amg_handle h, int level, int *slice, int64_t *stored, int *index_bytes);
+
 /* Copy level l's matrix in CSR form to host buffers (row_ptr n+1, col/val nnz). */
 int amg_level_csr(amg_handle h, int level, int32_t *row_ptr, int32_t *col, double *val);
 

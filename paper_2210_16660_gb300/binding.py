@@ -23,7 +23,8 @@ _MODES = {"pcg64": MODE_PCG64, "fcg32": MODE_FCG32}
 # Every symbol the header declares (checked by the CPU tests).
 EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode", "pcg_solve",
            "amg_last_true_residual", "amg_info", "amg_level_agg", "amg_level_csr", "amg_setup_times",
-           "amg_destroy", "amg_last_error", "amg_profile", "amg_profile_read", "amg_launch_count")
+           "amg_destroy", "amg_last_error", "amg_profile", "amg_profile_read", "amg_launch_count",
+           "amg_level_layout")
 
 
 class AmgCsr(C.Structure):
@@ -70,6 +71,8 @@ def load(build_if_missing: bool = True):
     lib.amg_info.restype = I
     lib.amg_level_agg.argtypes = [P, I, I, P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.amg_level_agg.restype = I
+    lib.amg_level_layout.argtypes = [P, I, C.POINTER(I), C.POINTER(C.c_int64), C.POINTER(I)]
+    lib.amg_level_layout.restype = I
     lib.amg_level_csr.argtypes = [P, I, P, P, P]
     lib.amg_level_csr.restype = I
     lib.amg_setup_times.argtypes = [P, P]
@@ -251,6 +254,13 @@ class AMG:
         if st:
             raise AmgError(st, last_error())
         return a, nc.value
+
+    def level_layout(self, level: int) -> dict:
+        sl, st, ib = C.c_int(), C.c_int64(), C.c_int()
+        r = load().amg_level_layout(self._h, level, C.byref(sl), C.byref(st), C.byref(ib))
+        if r:
+            raise AmgError(r, last_error())
+        return {"slice": sl.value, "stored": st.value, "index_bytes": ib.value}
 
     def level_csr(self, level: int):
         n, z = self.info()[level]

@@ -197,6 +197,18 @@ int amg_level_agg(amg_handle h, int level, int pass, int32_t *agg, int64_t *n_ou
     return AMG_OK;
 }
 
+int amg_level_layout(amg_handle h, int level, int *slice, int64_t *stored, int *index_bytes) {
+    if (!h || level < 0 || level >= (int)h->lev.size()) {
+        set_error("amg_level_layout: bad handle or level");
+        return AMG_ERR_ARG;
+    }
+    const Sell &S = h->lev[level].S;
+    if (slice) *slice = kSlice;
+    if (stored) *stored = S.nnz_pad;
+    if (index_bytes) *index_bytes = S.col16 ? 2 : 4;
+    return AMG_OK;
+}
+
 int amg_level_csr(amg_handle h, int level, int32_t *row_ptr, int32_t *col, double *val) {
     if (!h || level < 0 || level >= (int)h->lev.size()) {
         set_error("amg_level_csr: bad handle or level");

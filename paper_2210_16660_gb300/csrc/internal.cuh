@@ -72,6 +72,7 @@ struct Sell {
     int64_t nnz_pad = 0;
     int32_t *sptr = nullptr;   // nslices + 1 element offsets
     int32_t *col = nullptr;
+    int16_t *col16 = nullptr;  // col - row when every |col - row| < 2^15, else null
     double *v64 = nullptr;
     float *v32 = nullptr;
 };
@@ -138,7 +139,8 @@ struct amg_hier {
     int hist_cap = 0;
     pcgamg::Ctl *ctl = nullptr;
     pcgamg::Ctl *ctl_host = nullptr;  // pinned mirror
-    int nblk = 0;                // blocks of the level-0 reducing kernels
+    int nblk = 0;                // largest level-0 grid (sizes the partial sums)
+    int grid32 = 0, grid64 = 0, gridv = 0;  // one wave of the float32 sweeps, float64 sweeps, vector kernels
     double last_true_rel = 0.0;
     double setup_ms[4] = {0, 0, 0, 0};
     // kernel timing (amg_profile)
@@ -157,6 +159,7 @@ struct amg_hier {
     int graph_prefix_kernels = 0;
     int graph_body_kernels[2] = {0, 0};
     int use_graph = 1;
+    int no_col16 = 0;
 };
 
 namespace pcgamg {

@@ -423,6 +423,35 @@ __global__ void k_sell_fill(int n, int nsl, const int32_t *__restrict__ rp, cons
     }
 }
 
+// flag = 1 when some stored |col - row| does not fit in int16.
+__global__ void k_col16_check(int n, int nsl, const int32_t *__restrict__ sptr, const int32_t *__restrict__ col,
+                              int *flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nsl * kSlice) return;
+    int s = i / kSlice, lane = i % kSlice;
+    int row = i < n ? i : 0;
+    int32_t base = sptr[s];
+    int w = (sptr[s + 1] - base) / kSlice;
+    for (int k = 0; k < w; k++) {
+        int d = col[base + k * kSlice + lane] - row;
+        if (d < -32768 || d > 32767) { atomicOr(flag, 1); return; }
+    }
+}
+
+__global__ void k_col16_fill(int n, int nsl, const int32_t *__restrict__ sptr, const int32_t *__restrict__ col,
+                             int16_t *__restrict__ col16) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nsl * kSlice) return;
+    int s = i / kSlice, lane = i % kSlice;
+    int row = i < n ? i : 0;
+    int32_t base = sptr[s];
+    int w = (sptr[s + 1] - base) / kSlice;
+    for (int k = 0; k < w; k++) {
+        int32_t e = base + k * kSlice + lane;
+        col16[e] = (int16_t)(col[e] - row);
+    }
+}
+
 __global__ void k_count_members(int n, const int32_t *__restrict__ agg, int32_t *__restrict__ cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -652,6 +681,23 @@ int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
     k_sell_fill<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(n, S.nslices, lv.A.rp, lv.A.ci,
                                                                          lv.A.v, S.sptr, S.col, S.v64, S.v32);
     PCG_LAUNCH_CK();
+    // 16-bit column offsets where they fit (2 bytes per entry instead of 4)
+    {
+        int *dflag = nullptr;
+        PCG_TRY(alloc(M, &dflag, 1));
+        PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+        k_col16_check<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(n, S.nslices, S.sptr, S.col, dflag);
+        PCG_LAUNCH_CK();
+        int wide = 0;
+        PCG_TRY(read_flag(dflag, s, &wide));
+        release(M, dflag);
+        if (!wide && !h->no_col16) {
+            PCG_TRY(alloc(M, &S.col16, tot));
+            k_col16_fill<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(n, S.nslices, S.sptr, S.col,
+                                                                                  S.col16);
+            PCG_LAUNCH_CK();
+        }
+    }
     // work vectors
     PCG_TRY(alloc(M, &lv.b64, n));
     PCG_TRY(alloc(M, &lv.x64, n));
@@ -701,6 +747,9 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
     // replaying the whole-solve graph (same kernels; for profilers).
     const char *g = getenv("PCGAMG_GRAPH");
     if (g && g[0] == '0') h->use_graph = 0;
+    // PCGAMG_COL16=0 keeps int32 columns on every level.
+    const char *c16 = getenv("PCGAMG_COL16");
+    if (c16 && c16[0] == '0') h->no_col16 = 1;
     if (!A || A->n <= 0 || A->n >= (int64_t)1 << 31 || A->nnz < A->n || A->nnz >= (int64_t)1 << 31 ||
         !A->row_ptr || !A->col || !A->val) {
         set_error("amg_setup: bad CSR sizes or NULL arrays");

@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -119,8 +120,22 @@ constexpr int kUnroll = 4;
 constexpr int kUnrollSmall = 16;
 constexpr int kSmallRows = 65536;
 
-template <int U, typename T, typename F>
-__device__ __forceinline__ T sell_row(const int32_t *__restrict__ c, const T *__restrict__ a, int w, F xval) {
+// Loads of the matrix stream: level-0 sweeps use evict-first loads (the
+// matrix is read once per sweep and is larger than L2), coarser levels keep
+// the default so the matrix can stay in L2 between the down and up sweeps.
+template <bool STREAM, typename X>
+__device__ __forceinline__ X ld_mat(const X *p) {
+    if (STREAM) return __ldcs(p);
+    return __ldg(p);
+}
+
+// Column of an entry: int32 column index, or an int16 offset from the row
+// for levels whose every |col - row| fits in 16 bits.
+__device__ __forceinline__ int col_of(int32_t c, int) { return c; }
+__device__ __forceinline__ int col_of(int16_t c, int row) { return row + (int)c; }
+
+template <int U, bool STREAM, typename IDX, typename T, typename F>
+__device__ __forceinline__ T sell_row(const IDX *__restrict__ c, const T *__restrict__ a, int w, int row, F xval) {
     T acc = 0;
     int k = 0;
     for (; k + U <= w; k += U) {
@@ -128,15 +143,15 @@ __device__ __forceinline__ T sell_row(const int32_t *__restrict__ c, const T *__
         T v[U], x[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            j[u] = __ldg(c + 32 * (k + u));
-            v[u] = __ldg(a + 32 * (k + u));
+            j[u] = col_of(ld_mat<STREAM>(c + 32 * (k + u)), row);
+            v[u] = ld_mat<STREAM>(a + 32 * (k + u));
         }
 #pragma unroll
         for (int u = 0; u < U; u++) x[u] = xval(j[u]);
 #pragma unroll
         for (int u = 0; u < U; u++) acc += v[u] * x[u];
     }
-    for (; k < w; k++) acc += __ldg(a + 32 * k) * xval(__ldg(c + 32 * k));
+    for (; k < w; k++) acc += ld_mat<STREAM>(a + 32 * k) * xval(col_of(ld_mat<STREAM>(c + 32 * k), row));
     return acc;
 }
 
@@ -144,7 +159,7 @@ __device__ __forceinline__ T sell_row(const int32_t *__restrict__ c, const T *__
     int s_ = i >> 5, lane_ = i & 31;                                 \
     int32_t base_ = ldg(sptr + s_);                                  \
     int w_ = (ldg(sptr + s_ + 1) - base_) >> 5;                      \
-    const int32_t *c_ = col + base_ + lane_;                         \
+    const IDX *c_ = col + base_ + lane_;                             \
     const auto *a_ = val + base_ + lane_;
 
 // ------------------------------------------------------------ V-cycle sweeps
@@ -152,17 +167,16 @@ template <typename T>
 struct Occ { static constexpr int kMinBlocks = sizeof(T) == 4 ? 6 : 4; };
 
 // Pre-smooth from zero, residual, weighted restriction input:
-// t_i = p_i (b_i - sum_j a_ij xpre_j), xpre = D^-1 b. L0 marks the level-0
-// instance (same code; a separate symbol for profilers).
-template <typename T, bool L0, int U>
+// t_i = p_i (b_i - sum_j a_ij xpre_j), xpre = D^-1 b.
+template <typename T, typename IDX, int U, bool STREAM>
 __global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_down(
-    int n, const int32_t *__restrict__ sptr, const int32_t *__restrict__ col, const T *__restrict__ val,
+    int n, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
     const T *__restrict__ xpre, const T *__restrict__ b, const T *__restrict__ p, T *__restrict__ t,
     const Ctl *__restrict__ ctl) {
     if (ctl->done) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         SELL_ROW_BEGIN
-        T acc = sell_row<U>(c_, a_, w_, [&](int j) { return ldg(xpre + j); });
+        T acc = sell_row<U, STREAM>(c_, a_, w_, i, [&](int j) { return ldg(xpre + j); });
         t[i] = ldg(p + i) * (ldg(b + i) - acc);
     }
 }
@@ -184,16 +198,16 @@ __global__ void __launch_bounds__(kBlock) k_prolong(int n, const T *__restrict__
 // Post-smooth z_i = xp_i + dinv_i (b_i - sum_j a_ij xp_j). On level 0 (DOT)
 // z is written in float64 and the kernel also forms r.z (float64 r) and, for
 // FCG(1), z.q_old; its last block turns them into rho and beta.
-template <typename T, typename TZ, bool DOT, bool FCG, int U>
+template <typename T, typename TZ, bool DOT, bool FCG, typename IDX, int U, bool STREAM>
 __global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_post(
-    int n, const int32_t *__restrict__ sptr, const int32_t *__restrict__ col, const T *__restrict__ val,
+    int n, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
     const T *__restrict__ xp, const T *__restrict__ b, const T *__restrict__ dinv, TZ *__restrict__ z,
     const double *__restrict__ r64, const double *__restrict__ qold, double *partials, Ctl *ctl) {
     if (ctl->done) return;
     double rz = 0.0, zq = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         SELL_ROW_BEGIN
-        T acc = sell_row<U>(c_, a_, w_, [&](int j) { return ldg(xp + j); });
+        T acc = sell_row<U, STREAM>(c_, a_, w_, i, [&](int j) { return ldg(xp + j); });
         TZ zo = (TZ)(ldg(xp + i) + ldg(dinv + i) * (ldg(b + i) - acc));
         z[i] = zo;
         if (DOT) {
@@ -289,15 +303,16 @@ __global__ void __launch_bounds__(kBlock) k_axpy_p(int n, const double *__restri
 }
 
 // q = A p and p.q; the last block forms alpha = rho / p.q.
+template <typename IDX>
 __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int32_t *__restrict__ sptr,
-                                                    const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                    const IDX *__restrict__ col, const double *__restrict__ val,
                                                     const double *__restrict__ p, double *__restrict__ q,
                                                     double *partials, Ctl *ctl) {
     if (ctl->done) return;
     double pq = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         SELL_ROW_BEGIN
-        double acc = sell_row<kUnroll>(c_, a_, w_, [&](int j) { return ldg(p + j); });
+        double acc = sell_row<kUnroll, true>(c_, a_, w_, i, [&](int j) { return ldg(p + j); });
         q[i] = acc;
         pq += ldg(p + i) * acc;
     }
@@ -375,9 +390,9 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, const double *__restri
 
 // r = b - A x, ||r||^2 (and ||b||^2 on INIT); also the mode's copy of r.
 // Otherwise (not INIT) it runs only when the recursive residual met rtol.
-template <bool INIT, int MODE>
+template <bool INIT, int MODE, typename IDX>
 __global__ void __launch_bounds__(kBlock, 4) k_residual(int n, const int32_t *__restrict__ sptr,
-                                                        const int32_t *__restrict__ col,
+                                                        const IDX *__restrict__ col,
                                                         const double *__restrict__ val, const double *__restrict__ b,
                                                         const double *__restrict__ x, double *__restrict__ r,
                                                         REmit em, double *partials, Ctl *ctl, double *hist) {
@@ -386,7 +401,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_residual(int n, const int32_t *__
     double rr = 0.0, bb = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         SELL_ROW_BEGIN
-        double acc = sell_row<kUnroll>(c_, a_, w_, [&](int j) { return ldg(x + j); });
+        double acc = sell_row<kUnroll, true>(c_, a_, w_, i, [&](int j) { return ldg(x + j); });
         double bi = ldg(b + i);
         double ri = bi - acc;
         r[i] = ri;
@@ -510,6 +525,20 @@ REmit remit(amg_hier *h) {
     return REmit{h->r32, l0.dinv32, l0.xpre32, l0.dinv, l0.xpre64};
 }
 
+// Launch with the level's column array: int16 offsets when present.
+#define WITH_COLS(S, BODY)                          \
+    do {                                            \
+        if ((S).col16) {                            \
+            using IDX = int16_t;                    \
+            const IDX *cols = (S).col16;            \
+            BODY;                                   \
+        } else {                                    \
+            using IDX = int32_t;                    \
+            const IDX *cols = (S).col;              \
+            BODY;                                   \
+        }                                           \
+    } while (0)
+
 // z = B r (one V-cycle in precision T), including rho / beta.
 template <typename T, bool FCG>
 int launch_vcycle(amg_hier *h, cudaStream_t s) {
@@ -519,19 +548,21 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     Ctl *ctl = h->ctl;
     Level &l0 = lev[0];
     const T *b0 = P::r0(h);
+    int g0 = sizeof(T) == 4 ? h->grid32 : h->grid64;
     prof_begin(h, 0, s);
-    k_down<T, true, kUnroll><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, P::val(l0), P::xpre(l0), b0, P::p(l0),
-                                               P::t(l0), ctl);
+    WITH_COLS(l0.S, (k_down<T, IDX, kUnroll, true><<<g0, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, cols, P::val(l0),
+                                                                         P::xpre(l0), b0, P::p(l0), P::t(l0), ctl)));
     prof_end(h, s);
     prof_begin(h, 5, s);
     for (int l = 0; l < L; l++) {
         Level &lv = lev[l];
-        if (l > 0 && lv.A.n > kSmallRows)
-            k_down<T, false, kUnroll><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
-                lv.A.n, lv.S.sptr, lv.S.col, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl);
+        int n = lv.A.n;
+        if (l > 0 && n > kSmallRows)
+            WITH_COLS(lv.S, (k_down<T, IDX, kUnroll, false><<<grid_rows(n), kBlock, 0, s>>>(
+                                n, lv.S.sptr, cols, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl)));
         else if (l > 0)
-            k_down<T, false, kUnrollSmall><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
-                lv.A.n, lv.S.sptr, lv.S.col, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl);
+            WITH_COLS(lv.S, (k_down<T, IDX, kUnrollSmall, false><<<grid_rows(n), kBlock, 0, s>>>(
+                                n, lv.S.sptr, cols, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl)));
         if (l + 1 == L)
             k_restrict<T, double, false><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, P::t(lv),
                                                                              h->bL, nullptr, nullptr, ctl);
@@ -543,22 +574,24 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     k_coarse<T><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, P::x(lev[L]), ctl);
     for (int l = L - 1; l >= 1; l--) {
         Level &lv = lev[l];
-        k_prolong<T><<<grid_rows(lv.A.n), kBlock, 0, s>>>(lv.A.n, P::xpre(lv), P::p(lv), lv.agg, P::x(lev[l + 1]),
-                                                          P::xp(lv), ctl);
-        if (lv.A.n > kSmallRows)
-            k_post<T, T, false, false, kUnroll><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
-                lv.A.n, lv.S.sptr, lv.S.col, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv), nullptr,
-                nullptr, nullptr, ctl);
+        int n = lv.A.n;
+        k_prolong<T><<<grid_rows(n), kBlock, 0, s>>>(n, P::xpre(lv), P::p(lv), lv.agg, P::x(lev[l + 1]), P::xp(lv),
+                                                     ctl);
+        if (n > kSmallRows)
+            WITH_COLS(lv.S, (k_post<T, T, false, false, IDX, kUnroll, false><<<grid_rows(n), kBlock, 0, s>>>(
+                                n, lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv), nullptr,
+                                nullptr, nullptr, ctl)));
         else
-            k_post<T, T, false, false, kUnrollSmall><<<grid_rows(lv.A.n), kBlock, 0, s>>>(
-                lv.A.n, lv.S.sptr, lv.S.col, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv), nullptr,
-                nullptr, nullptr, ctl);
+            WITH_COLS(lv.S, (k_post<T, T, false, false, IDX, kUnrollSmall, false><<<grid_rows(n), kBlock, 0, s>>>(
+                                n, lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv), nullptr,
+                                nullptr, nullptr, ctl)));
     }
     prof_end(h, s);
     prof_begin(h, 1, s);
-    k_prolong<T><<<h->nblk, kBlock, 0, s>>>(l0.A.n, P::xpre(l0), P::p(l0), l0.agg, P::x(lev[1]), P::xp(l0), ctl);
-    k_post<T, double, true, FCG, kUnroll><<<h->nblk, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, l0.S.col, P::val(l0), P::xp(l0), b0,
-                                                            P::dinv(l0), h->z, h->r, h->q, h->partials, ctl);
+    k_prolong<T><<<h->gridv, kBlock, 0, s>>>(l0.A.n, P::xpre(l0), P::p(l0), l0.agg, P::x(lev[1]), P::xp(l0), ctl);
+    WITH_COLS(l0.S, (k_post<T, double, true, FCG, IDX, kUnroll, true><<<g0, kBlock, 0, s>>>(
+                        l0.A.n, l0.S.sptr, cols, P::val(l0), P::xp(l0), b0, P::dinv(l0), h->z, h->r, h->q,
+                        h->partials, ctl)));
     prof_end(h, s);
     h->launches += 4 * L + 1;
     PCG_LAUNCH_CK();
@@ -572,7 +605,7 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
     int n = l0.A.n;
     if (L == 0) {
         k_coarse_only<MODE == AMG_MODE_FCG32, MODE == AMG_MODE_FCG32>
-            <<<h->nblk, kBlock, 0, s>>>(h->nL, h->Ainv, h->r, h->z, h->q, h->partials, h->ctl);
+            <<<h->gridv, kBlock, 0, s>>>(h->nL, h->Ainv, h->r, h->z, h->q, h->partials, h->ctl);
         h->launches += 1;
     } else if (MODE == AMG_MODE_FCG32) {
         PCG_TRY((launch_vcycle<float, true>(h, s)));
@@ -580,17 +613,18 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
         PCG_TRY((launch_vcycle<double, false>(h, s)));
     }
     prof_begin(h, 6, s);
-    k_axpy_p<<<h->nblk, kBlock, 0, s>>>(n, h->z, h->p, h->ctl);
+    k_axpy_p<<<h->gridv, kBlock, 0, s>>>(n, h->z, h->p, h->ctl);
     prof_end(h, s);
     prof_begin(h, 2, s);
-    k_spmv<<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->p, h->q, h->partials, h->ctl);
+    WITH_COLS(l0.S, (k_spmv<IDX><<<h->grid64, kBlock, 0, s>>>(n, l0.S.sptr, cols, l0.S.v64, h->p, h->q, h->partials,
+                                                               h->ctl)));
     prof_end(h, s);
     prof_begin(h, 3, s);
-    k_update<MODE><<<h->nblk, kBlock, 0, s>>>(n, h->p, h->q, h->x, h->r, remit(h), h->partials, h->ctl, h->hist);
+    k_update<MODE><<<h->gridv, kBlock, 0, s>>>(n, h->p, h->q, h->x, h->r, remit(h), h->partials, h->ctl, h->hist);
     prof_end(h, s);
     prof_begin(h, 4, s);
-    k_residual<false, MODE><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x, h->r,
-                                                       remit(h), h->partials, h->ctl, h->hist);
+    WITH_COLS(l0.S, (k_residual<false, MODE, IDX><<<h->grid64, kBlock, 0, s>>>(
+                        n, l0.S.sptr, cols, l0.S.v64, h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
     prof_end(h, s);
     h->launches += 4;
     PCG_LAUNCH_CK();
@@ -608,11 +642,11 @@ int launch_prefix(amg_hier *h, cudaStream_t s) {
     k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->p, n);
     k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->q, n);
     if (h->mode == AMG_MODE_FCG32)
-        k_residual<true, AMG_MODE_FCG32><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x,
-                                                                    h->r, remit(h), h->partials, h->ctl, h->hist);
+        WITH_COLS(l0.S, (k_residual<true, AMG_MODE_FCG32, IDX><<<h->grid64, kBlock, 0, s>>>(
+                            n, l0.S.sptr, cols, l0.S.v64, h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
     else
-        k_residual<true, AMG_MODE_PCG64><<<h->nblk, kBlock, 0, s>>>(n, l0.S.sptr, l0.S.col, l0.S.v64, h->b, h->x,
-                                                                    h->r, remit(h), h->partials, h->ctl, h->hist);
+        WITH_COLS(l0.S, (k_residual<true, AMG_MODE_PCG64, IDX><<<h->grid64, kBlock, 0, s>>>(
+                            n, l0.S.sptr, cols, l0.S.v64, h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
     h->launches += 3;
     PCG_LAUNCH_CK();
     return AMG_OK;
@@ -732,10 +766,21 @@ int alloc_solve_workspace(amg_hier *h) {
     PCG_CK(cudaGetDevice(&dev));
     PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     h->device = dev;
-    int64_t want = ((int64_t)n + kBlock - 1) / kBlock;
-    int64_t cap = (int64_t)sms * 8;
-    h->nblk = (int)(want < cap ? want : cap);
-    if (h->nblk < 1) h->nblk = 1;
+    // One wave of resident blocks per level-0 kernel family (grid = SMs x
+    // blocks resident per SM), capped by the rows available.
+    auto wave = [&](const void *fn, int *grid) -> int {
+        int per = 0;
+        PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kBlock, 0));
+        int64_t want = ((int64_t)n + kBlock - 1) / kBlock;
+        int64_t g = (int64_t)sms * (per > 0 ? per : 1);
+        *grid = (int)(want < g ? want : g);
+        if (*grid < 1) *grid = 1;
+        return AMG_OK;
+    };
+    PCG_TRY(wave((const void *)k_down<float, int32_t, kUnroll, true>, &h->grid32));
+    PCG_TRY(wave((const void *)k_spmv<int32_t>, &h->grid64));
+    PCG_TRY(wave((const void *)k_update<AMG_MODE_FCG32>, &h->gridv));
+    h->nblk = std::max(h->grid32, std::max(h->grid64, h->gridv));
     PCG_TRY(alloc(M, &h->b, n));
     PCG_TRY(alloc(M, &h->x, n));
     PCG_TRY(alloc(M, &h->r, n));

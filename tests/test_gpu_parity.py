@@ -196,6 +196,61 @@ def test_graph_and_stream_launch_paths_agree():
         assert prof["spmv"][1] >= r1.iters and prof["spmv"][0] > 0
 
 
+def _with_env(key, val, fn):
+    import os
+    old = os.environ.get(key)
+    os.environ[key] = val
+    try:
+        return fn()
+    finally:
+        if old is None:
+            del os.environ[key]
+        else:
+            os.environ[key] = old
+
+
+@pytest.mark.parametrize("mode", ["pcg64", "fcg32"])
+def test_int16_and_int32_columns_agree(mode):
+    """Columns stored as int16 offsets and as int32 give bitwise the same solve."""
+    prob = W.make_problem(30, 1.04, seed=8)
+    b = torch.from_numpy(prob.b).cuda()
+    a16 = B.AMG.from_csr(prob.A, mode=mode)
+    a32 = _with_env("PCGAMG_COL16", "0", lambda: B.AMG.from_csr(prob.A, mode=mode))
+    assert a16.level_layout(0)["index_bytes"] == 2
+    assert all(a32.level_layout(l)["index_bytes"] == 4 for l in range(len(a32.info())))
+    x16, x32 = torch.zeros_like(b), torch.zeros_like(b)
+    r16, r32 = a16.solve(b, x16), a32.solve(b, x32)
+    assert r16.status == r32.status == 0 and r16.iters == r32.iters
+    assert torch.equal(x16, x32)
+
+
+def _add_long_coupling(A, i, j, v):
+    """A with one extra symmetric pair a_ij = a_ji = v (columns kept sorted)."""
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    r = np.concatenate([rows, [i, j]])
+    c = np.concatenate([A.col, [j, i]]).astype(np.int64)
+    val = np.concatenate([A.val, [v, v]])
+    order = np.lexsort((c, r))
+    r, c, val = r[order], c[order], val[order]
+    rp = np.zeros(A.n + 1, np.int64)
+    np.cumsum(np.bincount(r, minlength=A.n), out=rp[1:])
+    return W.CSR(A.n, rp.astype(np.int32), c.astype(np.int32), val)
+
+
+@pytest.mark.parametrize("mode", ["pcg64", "fcg32"])
+def test_wide_columns_fall_back_to_int32(mode):
+    """A coupling further than 2^15 rows apart keeps int32 columns; parity holds."""
+    N = 33
+    A, wall, _ = W.q1_laplacian(N, 1.04)
+    i, j = N * N, A.n - 1
+    A2 = _add_long_coupling(A, i, j, -1e-3)
+    xs = W.normals(9, A2.n)
+    xs[wall] = 0.0
+    prob = W.Problem("long", N, A2, W.spmv(A2, xs), xs, wall, None)
+    res, ref, _, amg = _solve_parity(prob, mode)
+    assert amg.level_layout(0)["index_bytes"] == 4
+
+
 def test_torch_allocator_route():
     prob = W.make_problem(10, 1.04, seed=5)
     B.use_torch_allocator(True)
