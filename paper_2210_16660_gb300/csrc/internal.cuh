@@ -120,6 +120,18 @@ struct Ctl {
     unsigned int counter[8];  // last-block-done counters of the reducing kernels
 };
 
+// One level of the fused small-level tail of the V-cycle (device copy).
+template <typename T>
+struct TailLevel {
+    int n, nc;
+    const int32_t *sptr;
+    const int32_t *col;
+    const int16_t *col16;   // used when not null
+    const T *val, *dinv, *p;
+    const int32_t *agg, *rptr, *ridx;
+    T *b, *x, *t, *xpre;
+};
+
 }  // namespace pcgamg
 
 struct amg_hier {
@@ -160,6 +172,12 @@ struct amg_hier {
     int graph_body_kernels[2] = {0, 0};
     int use_graph = 1;
     int no_col16 = 0;
+    // fused tail: levels tail_first..L run in one cooperative kernel
+    int tail_first = 0;      // 0 = no tail (every level launched separately)
+    int tail_grid = 0;
+    pcgamg::TailLevel<float> *tail32 = nullptr;
+    pcgamg::TailLevel<double> *tail64 = nullptr;
+    unsigned *tail_bar = nullptr;  // grid barrier: arrivals, generation
 };
 
 namespace pcgamg {

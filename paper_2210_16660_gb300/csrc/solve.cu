@@ -29,6 +29,7 @@
 // iteration needs no host round trip.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <type_traits>
@@ -462,6 +463,147 @@ __global__ void k_set_cond(cudaGraphConditionalHandle hc, Ctl *ctl, int count_bo
 
 inline int grid_rows(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
+
+// ------------------------------------------------------------ fused tail
+// Levels with few rows are latency-bound: a separate launch per sweep costs
+// more than the sweep. The tail runs every V-cycle phase of levels
+// tail_first..L in one cooperative launch (one block per SM, guaranteed
+// co-resident), phases separated by a grid barrier:
+//   down_l, restrict_l (l = first..L-1), coarse solve, then
+//   prolong+post_l (l = L-1..first, prolongation formed per entry).
+// Data written in one phase and read in a later one is loaded with __ldcg
+// (L2, coherent across SMs); read-only data with __ldg.
+constexpr int kTailThreads = 512;
+constexpr int kTailRows = 40000;
+constexpr unsigned kBarrierSpins = 1u << 22;
+
+// Grid-wide barrier: arrival counter + generation word, bounded spin.
+// Returns false (in every thread of the block) when the wait gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *gen = bar + 1;
+        unsigned g = *gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned spins = 0;
+            while (*gen == g) {
+                if (++spins > kBarrierSpins) { ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename T, typename IDX, typename F>
+__device__ __forceinline__ T tail_row(int i, const int32_t *sptr, const IDX *col, const T *val, F xval) {
+    int s = i >> 5, lane = i & 31;
+    int32_t base = __ldg(sptr + s);
+    int w = (__ldg(sptr + s + 1) - base) >> 5;
+    return sell_row<kUnrollSmall, false>(col + base + lane, val + base + lane, w, i, xval);
+}
+
+template <typename T>
+__device__ __forceinline__ void tail_down(const TailLevel<T> &L, int tid, int nth) {
+    for (int i = tid; i < L.n; i += nth) {
+        auto xv = [&](int j) { return __ldcg(L.xpre + j); };
+        T acc = L.col16 ? tail_row<T>(i, L.sptr, L.col16, L.val, xv) : tail_row<T>(i, L.sptr, L.col, L.val, xv);
+        L.t[i] = __ldg(L.p + i) * (__ldcg(L.b + i) - acc);
+    }
+}
+
+// Fused prolongation + post-smooth: xp_j = xpre_j + p_j xc[agg_j] per entry.
+template <typename T>
+__device__ __forceinline__ void tail_up(const TailLevel<T> &L, const T *xc, int tid, int nth) {
+    for (int i = tid; i < L.n; i += nth) {
+        auto xp = [&](int j) {
+            T x = __ldcg(L.xpre + j);
+            int a = __ldg(L.agg + j);
+            if (a >= 0) x += __ldg(L.p + j) * __ldcg(xc + a);
+            return x;
+        };
+        T acc = L.col16 ? tail_row<T>(i, L.sptr, L.col16, L.val, xp) : tail_row<T>(i, L.sptr, L.col, L.val, xp);
+        L.x[i] = xp(i) + __ldg(L.dinv + i) * (__ldcg(L.b + i) - acc);
+    }
+}
+
+// lv[0..nt-1]: levels first..L (lv[nt-1] is the coarsest: only x is used).
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__restrict__ lv, int nt,
+                                                          const double *__restrict__ ainv, int nL, double *bL,
+                                                          Ctl *ctl, unsigned *bar) {
+    if (ctl->done) return;
+    int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    bool ok = true;
+    for (int k = 0; k + 1 < nt && ok; k++) {
+        TailLevel<T> L = lv[k];
+        tail_down(L, tid, nth);
+        ok = grid_barrier(bar);
+        if (!ok) break;
+        bool last = (k + 2 == nt);
+        TailLevel<T> C = lv[k + 1];
+        for (int I = tid; I < L.nc; I += nth) {
+            T sum = 0;
+            for (int32_t q = __ldg(L.rptr + I); q < __ldg(L.rptr + I + 1); q++) sum += __ldcg(L.t + __ldg(L.ridx + q));
+            if (last) {
+                bL[I] = (double)sum;
+            } else {
+                C.b[I] = sum;
+                C.xpre[I] = __ldg(C.dinv + I) * sum;
+            }
+        }
+        ok = grid_barrier(bar);
+    }
+    if (ok) {
+        // coarsest: x_L = A_L^{-1} b_L, one warp per row
+        int warp = tid >> 5, nwarp = nth >> 5, lane = threadIdx.x & 31;
+        T *xL = lv[nt - 1].x;
+        for (int row = warp; row < nL; row += nwarp) {
+            const double *a = ainv + (int64_t)row * nL;
+            double sacc = 0.0;
+            for (int j = lane; j < nL; j += 32) sacc += __ldg(a + j) * __ldcg(bL + j);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+            if (lane == 0) xL[row] = (T)sacc;
+        }
+        ok = grid_barrier(bar);
+    }
+    for (int k = nt - 2; k >= 0 && ok; k--) {
+        tail_up(lv[k], (const T *)lv[k + 1].x, tid, nth);
+        if (k > 0) ok = grid_barrier(bar);
+    }
+    if (!ok && threadIdx.x == 0) {
+        ctl->status = AMG_ERR_TIMEOUT;
+        ctl->done = 2;
+    }
+}
+
+template <typename T>
+int launch_tail(amg_hier *h, const TailLevel<T> *lv, int nt, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->tail_grid);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PCG_CK(cudaLaunchKernelEx(&cfg, k_tail<T>, lv, nt, (const double *)h->Ainv, h->nL, h->bL, h->ctl, h->tail_bar));
+    return AMG_OK;
+}
+
 // ------------------------------------------------------------ profiling
 // CUDA-event spans around kernel launches (only when profiling is on).
 // kinds: 0 down0, 1 up0 (prolong0 + post0), 2 q = A p, 3 update,
@@ -520,6 +662,17 @@ struct LP<double> {
     static const double *r0(const amg_hier *h) { return h->r; }
 };
 
+template <typename T>
+struct TailPick;
+template <>
+struct TailPick<float> {
+    static const TailLevel<float> *get(amg_hier *h) { return h->tail32; }
+};
+template <>
+struct TailPick<double> {
+    static const TailLevel<double> *get(amg_hier *h) { return h->tail64; }
+};
+
 REmit remit(amg_hier *h) {
     Level &l0 = h->lev[0];
     return REmit{h->r32, l0.dinv32, l0.xpre32, l0.dinv, l0.xpre64};
@@ -554,7 +707,9 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
                                                                          P::xpre(l0), b0, P::p(l0), P::t(l0), ctl)));
     prof_end(h, s);
     prof_begin(h, 5, s);
-    for (int l = 0; l < L; l++) {
+    // levels handled by separate launches: 0..F-1; the tail runs F..L
+    int F = h->tail_first > 0 ? h->tail_first : L;
+    for (int l = 0; l < F; l++) {
         Level &lv = lev[l];
         int n = lv.A.n;
         if (l > 0 && n > kSmallRows)
@@ -571,8 +726,12 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
                                                                        P::b(lev[l + 1]), P::dinv(lev[l + 1]),
                                                                        P::xpre(lev[l + 1]), ctl);
     }
-    k_coarse<T><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, P::x(lev[L]), ctl);
-    for (int l = L - 1; l >= 1; l--) {
+    if (F < L) {
+        PCG_TRY(launch_tail<T>(h, TailPick<T>::get(h), L - F + 1, s));
+    } else {
+        k_coarse<T><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, P::x(lev[L]), ctl);
+    }
+    for (int l = F - 1; l >= 1; l--) {
         Level &lv = lev[l];
         int n = lv.A.n;
         k_prolong<T><<<grid_rows(n), kBlock, 0, s>>>(n, P::xpre(lv), P::p(lv), lv.agg, P::x(lev[l + 1]), P::xp(lv),
@@ -593,7 +752,7 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
                         l0.A.n, l0.S.sptr, cols, P::val(l0), P::xp(l0), b0, P::dinv(l0), h->z, h->r, h->q,
                         h->partials, ctl)));
     prof_end(h, s);
-    h->launches += 4 * L + 1;
+    h->launches += (h->tail_first > 0) ? 4 * h->tail_first + 1 : 4 * L + 1;
     PCG_LAUNCH_CK();
     return AMG_OK;
 }
@@ -641,6 +800,7 @@ int launch_prefix(amg_hier *h, cudaStream_t s) {
     int n = l0.A.n;
     k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->p, n);
     k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->q, n);
+    if (h->tail_bar) PCG_CK(cudaMemsetAsync(h->tail_bar, 0, 2 * sizeof(unsigned), s));
     if (h->mode == AMG_MODE_FCG32)
         WITH_COLS(l0.S, (k_residual<true, AMG_MODE_FCG32, IDX><<<h->grid64, kBlock, 0, s>>>(
                             n, l0.S.sptr, cols, l0.S.v64, h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
@@ -738,6 +898,62 @@ bool is_device_ptr(const void *p) {
 
 }  // namespace
 
+// Fused tail: the first level (>= 1) with at most kTailRows rows through the
+// coarsest, when at least one level lies between it and the coarsest.
+// PCGAMG_TAIL=0 disables it.
+int setup_tail(amg_hier *h) {
+    int L = (int)h->lev.size() - 1;
+    h->tail_first = 0;
+    const char *e = getenv("PCGAMG_TAIL");
+    if (e && e[0] == '0') return AMG_OK;
+    int F = 0;
+    for (int l = 1; l < L; l++)
+        if (h->lev[l].A.n <= kTailRows) { F = l; break; }
+    if (F == 0) return AMG_OK;
+    int dev = h->device, sms = 0, per = 0, coop = 0;
+    PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PCG_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return AMG_OK;
+    PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tail<double>, kTailThreads, 0));
+    int per32 = 0;
+    PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, k_tail<float>, kTailThreads, 0));
+    if (per < 1 || per32 < 1) return AMG_OK;
+    h->tail_grid = sms;
+    int nt = L - F + 1;
+    std::vector<TailLevel<float>> t32(nt);
+    std::vector<TailLevel<double>> t64(nt);
+    for (int k = 0; k < nt; k++) {
+        Level &lv = h->lev[F + k];
+        TailLevel<float> &a = t32[k];
+        TailLevel<double> &b = t64[k];
+        a.n = b.n = lv.A.n;
+        a.nc = b.nc = lv.nc;
+        a.sptr = b.sptr = lv.S.sptr;
+        a.col = b.col = lv.S.col;
+        a.col16 = b.col16 = lv.S.col16;
+        a.val = lv.S.v32; b.val = lv.S.v64;
+        a.dinv = lv.dinv32; b.dinv = lv.dinv;
+        a.p = lv.p32; b.p = lv.p;
+        a.agg = b.agg = lv.agg;
+        a.rptr = b.rptr = lv.rptr;
+        a.ridx = b.ridx = lv.ridx;
+        a.b = lv.b32; b.b = lv.b64;
+        a.x = lv.x32; b.x = lv.x64;
+        a.t = lv.t32; b.t = lv.t64;
+        a.xpre = lv.xpre32; b.xpre = lv.xpre64;
+    }
+    Mem &M = h->mem;
+    PCG_TRY(alloc(M, &h->tail32, nt));
+    PCG_TRY(alloc(M, &h->tail64, nt));
+    PCG_TRY(alloc(M, &h->tail_bar, 2));
+    PCG_CK(cudaMemcpyAsync(h->tail32, t32.data(), sizeof(TailLevel<float>) * nt, cudaMemcpyHostToDevice, M.stream));
+    PCG_CK(cudaMemcpyAsync(h->tail64, t64.data(), sizeof(TailLevel<double>) * nt, cudaMemcpyHostToDevice, M.stream));
+    PCG_CK(cudaMemsetAsync(h->tail_bar, 0, 2 * sizeof(unsigned), M.stream));
+    PCG_CK(cudaStreamSynchronize(M.stream));
+    h->tail_first = F;
+    return AMG_OK;
+}
+
 int set_profile(amg_hier *h, int enable) {
     if (enable && h->ev.empty()) {
         h->ev.resize(2 * kEvPairs);
@@ -794,6 +1010,7 @@ int alloc_solve_workspace(amg_hier *h) {
     PCG_CK(cudaMallocHost(&h->ctl_host, sizeof(Ctl)));
     h->hist_cap = 1001;
     PCG_TRY(alloc(M, &h->hist, h->hist_cap));
+    PCG_TRY(setup_tail(h));
     return AMG_OK;
 }
 
