@@ -192,7 +192,7 @@ def test_graph_and_stream_launch_paths_agree():
         assert r1.status == r2.status == 0 and r1.iters == r2.iters
         assert torch.equal(x1, x2)
         assert np.array_equal(r1.hist, r2.hist)
-        assert n_graph > 10 * r1.iters
+        assert n_graph >= 5 * r1.iters
         assert prof["spmv"][1] >= r1.iters and prof["spmv"][0] > 0
 
 
