@@ -165,6 +165,24 @@ int amg_profile_read(amg_handle h, double *ms, int64_t *counts, int nkinds);
  * ones that find the solve finished and return at once). */
 int64_t amg_launch_count(amg_handle h);
 
+/* r = b - A x on the finest level of h, with norms[0] = ||r||_2 and
+ * norms[1] = ||b||_2, computed without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they solve, such as an application
+ * that gives the whole GPU to its own memory pool, or a time-step loop that
+ * cannot take the device synchronisation an allocation may cause.
+ * b, x, r: device pointers to n values (r is written); norms: 2 doubles,
+ * host or device (a host pointer makes the call wait for the result).
+ * Scratch: a fixed 512 KiB array inside the library (per GPU, kept until the
+ * process exits) holds one partial sum pair per 256 rows, so at most
+ * 8,388,608 rows are accepted; larger levels return AMG_ERR_ARG. The first
+ * call on a device looks up that array's device address, so make it before
+ * any stream capture. All calls share the array: calls that overlap on the
+ * GPU (different streams, threads or handles) race and must be ordered by
+ * the caller. Calls no cudaMalloc, cudaFree or allocating library routine. */
+int amg_residual_noalloc(amg_handle h, const double *b, const double *x, double *r, double *norms,
+                         void *stream);
+
 /* Release every device allocation of the handle (NULL is ignored). */
 void amg_destroy(amg_handle h);
 

@@ -24,7 +24,7 @@ _MODES = {"pcg64": MODE_PCG64, "fcg32": MODE_FCG32}
 EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode", "pcg_solve",
            "amg_last_true_residual", "amg_info", "amg_level_agg", "amg_level_csr", "amg_setup_times",
            "amg_destroy", "amg_last_error", "amg_profile", "amg_profile_read", "amg_launch_count",
-           "amg_level_layout")
+           "amg_level_layout", "amg_residual_noalloc")
 
 
 class AmgCsr(C.Structure):
@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
     lib.amg_profile_read.restype = I
     lib.amg_launch_count.argtypes = [P]
     lib.amg_launch_count.restype = C.c_int64
+    lib.amg_residual_noalloc.argtypes = [P, P, P, P, P, P]
+    lib.amg_residual_noalloc.restype = I
     lib.amg_destroy.argtypes = [P]
     lib.amg_destroy.restype = None
     lib.amg_last_error.argtypes = []
@@ -287,6 +289,17 @@ class AMG:
 
     def launch_count(self) -> int:
         return int(load().amg_launch_count(self._h))
+
+    def residual_noalloc(self, b, x, r, stream=None):
+        """``amg_residual_noalloc``: r = b - A x (device tensors); returns (||r||, ||b||)."""
+        norms = np.zeros(2)
+        bp, _ = _ptr(b, np.float64)
+        xp, _ = _ptr(x, np.float64)
+        rp, _ = _ptr(r, np.float64)
+        st = load().amg_residual_noalloc(self._h, bp, xp, rp, norms.ctypes.data, _stream_ptr(stream))
+        if st:
+            raise AmgError(st, last_error())
+        return float(norms[0]), float(norms[1])
 
     def setup_times(self):
         ms = np.zeros(4)
