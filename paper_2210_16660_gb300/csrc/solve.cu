@@ -900,12 +900,14 @@ bool is_device_ptr(const void *p) {
 
 // Fused tail: the first level (>= 1) with at most kTailRows rows through the
 // coarsest, when at least one level lies between it and the coarsest.
-// PCGAMG_TAIL=0 disables it.
+// Opt-in with PCGAMG_TAIL=1: inside the whole-solve graph a cooperative
+// kernel node measured slower on GB300 than the separate launches it
+// replaces, so the default keeps one launch per sweep.
 int setup_tail(amg_hier *h) {
     int L = (int)h->lev.size() - 1;
     h->tail_first = 0;
     const char *e = getenv("PCGAMG_TAIL");
-    if (e && e[0] == '0') return AMG_OK;
+    if (!e || e[0] != '1') return AMG_OK;
     int F = 0;
     for (int l = 1; l < L; l++)
         if (h->lev[l].A.n <= kTailRows) { F = l; break; }

@@ -230,15 +230,15 @@ def test_fused_tail_matches_separate_launches(mode, N):
     """Small levels in one cooperative kernel give the same solve as one launch per sweep."""
     prob = W.make_problem(N, 1.04, seed=10)
     b = torch.from_numpy(prob.b).cuda()
-    a1 = B.AMG.from_csr(prob.A, mode=mode)
-    a2 = _with_env("PCGAMG_TAIL", "0", lambda: B.AMG.from_csr(prob.A, mode=mode))
+    a1 = _with_env("PCGAMG_TAIL", "1", lambda: B.AMG.from_csr(prob.A, mode=mode))
+    a2 = B.AMG.from_csr(prob.A, mode=mode)
     x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
     r1, r2 = a1.solve(b, x1), a2.solve(b, x2)
     assert r1.status == r2.status == 0 and r1.iters == r2.iters
     d = (x1 - x2).norm().item() / x1.norm().item()
     assert d <= 1e-12, d
     # and the fused path itself still meets the oracle
-    _solve_parity(prob, mode)
+    _with_env("PCGAMG_TAIL", "1", lambda: _solve_parity(prob, mode))
 
 
 def _add_long_coupling(A, i, j, v):
