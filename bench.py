@@ -49,6 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--multi-k", type=int, default=32, help="right-hand sides of the multi-column form (0: skip)")
+    ap.add_argument("--multi-reps", type=int, default=3)
     return ap.parse_args(argv)
 
 
@@ -345,6 +347,37 @@ def run_ours(args):
                                   device, profile=True)
     amg.set_mode("fcg32")
 
+    # multi right-hand-side form: k columns of the same system in one solve
+    multi = {}
+    if args.multi_k > 0:
+        Bm, _ = W.make_rhs(prob, args.multi_k, seed=args.seed + 2000)
+        Bd = torch.from_numpy(Bm).to(device)
+        Xd = torch.zeros_like(Bd)
+        for mode in ("fcg32", "pcg64"):
+            amg.set_mode(mode)
+            for _ in range(max(1, min(args.warmup, 2))):
+                Xd.zero_()
+                amg.solve_multi(Bd, Xd, rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = args.multi_reps
+            its = []
+            e0.record(stream)
+            for _ in range(reps):
+                Xd.zero_()
+                st, it, _, sts, tr = amg.solve_multi(Bd, Xd, rtol=args.rtol, maxit=args.maxit, stream=stream,
+                                                     hist=False)
+                if st != 0:
+                    raise RuntimeError(f"multi solve failed: {sts}")
+                its.append(int(it.max()))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            multi[mode] = {"k": args.multi_k, "ms_per_multi_solve": ms,
+                           "solves_per_s": args.multi_k / (ms / 1e3), "max_iters": max(its),
+                           "max_true_rel": float(np.max(tr))}
+        amg.set_mode("fcg32")
+
     # end to end through the C ABI with host buffers (pinned), copies inside the call
     pin_b = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
     pin_x = torch.zeros(prob.A.n, dtype=torch.float64).pin_memory().numpy()
@@ -437,6 +470,7 @@ def run_ours(args):
             "iters": {"median": statistics.median(m["iters"]), "min": min(m["iters"]), "max": max(m["iters"])},
             "latency_ms": {"p50": pct(m["lat_ms"], 50), "p99": pct(m["lat_ms"], 99)},
             "true_rel": m["true_rel"],
+            "multi_rhs": multi,
             "fp64": {"value": solves / (f64_ms / 1e3), "unit": UNIT, "ms_per_step": f64_ms / args.steps,
                      "latency_ms": {"p50": pct(f64["lat_ms"], 50), "p99": pct(f64["lat_ms"], 99)},
                      "iters": statistics.median(f64["iters"]), "gpu_launches": f64["launches"]},

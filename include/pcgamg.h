@@ -120,6 +120,26 @@ int amg_set_mode(amg_handle h, int mode);
 int pcg_solve(amg_handle h, const double *b, double *x, double rtol, int maxit,
               int *iters, double *res_hist, void *stream);
 
+/* k right-hand sides at once (1 <= k <= 32), sharing the hierarchy: each
+ * stored entry of every level is read once per sweep for all columns (the
+ * multi-vector form of the same method). B and X are n x k row-major
+ * (column c of row i at [i*k + c]), host or device; X holds the initial
+ * guesses on entry and the solutions on exit. Each column runs its own
+ * recurrence (PCG or FCG(1) per amg_set_mode), stops on its own
+ * ||r_c|| / ||b_c|| <= rtol (confirmed on the true residual) and keeps its x
+ * while the others go on. iters: k values (host, may be NULL). res_hist
+ * (may be NULL, host or device): k rows of maxit+1 values, column c's
+ * history at [c*(maxit+1)]. Returns AMG_OK when every column converged, else
+ * the status of the first column that did not (per-column statuses from
+ * amg_multi_info). Needs a hierarchy with at least two levels. */
+int pcg_solve_multi(amg_handle h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
+                    double *res_hist, void *stream);
+
+/* Per-column outcome of the last pcg_solve_multi on h: *k columns, status[c]
+ * (AMG_* code) and true_rel[c] = ||b_c - A x_c|| / ||b_c||. Arrays of 32
+ * (host) or NULL. */
+int amg_multi_info(amg_handle h, int *k, int *status, double *true_rel);
+
 /* True relative residual ||b - A x|| / ||b|| at the end of the last solve on h. */
 double amg_last_true_residual(amg_handle h);
 

@@ -24,7 +24,7 @@ _MODES = {"pcg64": MODE_PCG64, "fcg32": MODE_FCG32}
 EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode", "pcg_solve",
            "amg_last_true_residual", "amg_info", "amg_level_agg", "amg_level_csr", "amg_setup_times",
            "amg_destroy", "amg_last_error", "amg_profile", "amg_profile_read", "amg_launch_count",
-           "amg_level_layout", "amg_residual_noalloc")
+           "amg_level_layout", "amg_residual_noalloc", "pcg_solve_multi", "amg_multi_info")
 
 
 class AmgCsr(C.Structure):
@@ -85,6 +85,10 @@ def load(build_if_missing: bool = True):
     lib.amg_launch_count.restype = C.c_int64
     lib.amg_residual_noalloc.argtypes = [P, P, P, P, P, P]
     lib.amg_residual_noalloc.restype = I
+    lib.pcg_solve_multi.argtypes = [P, I, P, P, D, I, P, P, P]
+    lib.pcg_solve_multi.restype = I
+    lib.amg_multi_info.argtypes = [P, C.POINTER(I), P, P]
+    lib.amg_multi_info.restype = I
     lib.amg_destroy.argtypes = [P]
     lib.amg_destroy.restype = None
     lib.amg_last_error.argtypes = []
@@ -235,6 +239,25 @@ class AMG:
             raise AmgError(st, msg)
         return SolveResult(st, it.value, h[: it.value + 1] if hist else None,
                            lib.amg_last_true_residual(self._h), msg)
+
+    def solve_multi(self, B, X, rtol: float = 1e-8, maxit: int = 1000, stream=None, hist: bool = True):
+        """``pcg_solve_multi``: B, X are (n, k) row-major; X is updated in place.
+
+        Returns (status, iters[k], hist[k, maxit+1] or None, statuses[k], true_rel[k]).
+        """
+        lib = load()
+        k = int(B.shape[1])
+        bp, _ = _ptr(B, np.float64)
+        xp, _ = _ptr(X, np.float64)
+        it = np.zeros(k, np.int32)
+        h = np.zeros((k, maxit + 1)) if hist else None
+        st = lib.pcg_solve_multi(self._h, k, bp, xp, rtol, maxit, it.ctypes.data,
+                                 h.ctypes.data if hist else None, _stream_ptr(stream))
+        kk = C.c_int(0)
+        sts = np.zeros(32, np.int32)
+        tr = np.zeros(32)
+        lib.amg_multi_info(self._h, C.byref(kk), sts.ctypes.data, tr.ctypes.data)
+        return st, it, h, sts[:k].copy(), tr[:k].copy()
 
     def info(self):
         lib = load()

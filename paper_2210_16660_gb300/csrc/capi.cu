@@ -154,6 +154,29 @@ int pcg_solve(amg_handle h, const double *b, double *x, double rtol, int maxit, 
 
 double amg_last_true_residual(amg_handle h) { return h ? h->last_true_rel : -1.0; }
 
+int pcg_solve_multi(amg_handle h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
+                    double *res_hist, void *stream) {
+    set_error("");
+    if (!h) {
+        set_error("pcg_solve_multi: NULL handle");
+        return AMG_ERR_ARG;
+    }
+    return solve_multi_impl(h, k, B, X, rtol, maxit, iters, res_hist, (cudaStream_t)stream);
+}
+
+int amg_multi_info(amg_handle h, int *k, int *status, double *true_rel) {
+    if (!h) {
+        set_error("amg_multi_info: NULL handle");
+        return AMG_ERR_ARG;
+    }
+    if (k) *k = h->multi_k;
+    for (int c = 0; c < h->multi_k; c++) {
+        if (status) status[c] = h->multi_status[c];
+        if (true_rel) true_rel[c] = h->multi_true_rel[c];
+    }
+    return AMG_OK;
+}
+
 int amg_info(amg_handle h, int *levels, int64_t *n_l, int64_t *nnz_l) {
     if (!h) {
         set_error("amg_info: NULL handle");
@@ -260,6 +283,7 @@ void amg_destroy(amg_handle h) {
     if (!h) return;
     cudaDeviceSynchronize();
     free_profile(h);
+    free_multi(h);
     h->mem.release_all();
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     delete h;

@@ -132,6 +132,34 @@ struct TailLevel {
     T *b, *x, *t, *xpre;
 };
 
+// Device-resident state of a multi right-hand-side solve (K <= 32 columns).
+struct CtlM {
+    double bnorm[32], rho[32], rho_old[32], pq[32], pq_old[32], alpha[32], beta[32], rel[32], true_rel[32];
+    double rtol;
+    int iter[32], active[32], restart[32], check[32], status[32];
+    int k, K, maxit, mode, iter_all, any_check, done, bodies;
+    unsigned int counter[8];
+};
+
+// Per-level n_l x K work blocks of the multi-column V-cycle.
+struct MultiLevel {
+    float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *xpre32 = nullptr, *xp32 = nullptr;
+    double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr, *xpre64 = nullptr, *xp64 = nullptr;
+};
+
+struct MultiWS {
+    int K = 0, hist_cap = 0, grid = 0;
+    double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    float *r32 = nullptr;
+    std::vector<MultiLevel> lev;
+    double *bL = nullptr;
+    double *partials = nullptr;
+    CtlM *ctl = nullptr;
+    CtlM *ctl_host = nullptr;
+    double *hist = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+};
+
 }  // namespace pcgamg
 
 struct amg_hier {
@@ -178,6 +206,11 @@ struct amg_hier {
     pcgamg::TailLevel<float> *tail32 = nullptr;
     pcgamg::TailLevel<double> *tail64 = nullptr;
     unsigned *tail_bar = nullptr;  // grid barrier: arrivals, generation
+    // multi right-hand-side solves
+    pcgamg::MultiWS multi;
+    int multi_k = 0;
+    int multi_status[32] = {0};
+    double multi_true_rel[32] = {0};
 };
 
 namespace pcgamg {
@@ -187,4 +220,7 @@ int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, 
 int alloc_solve_workspace(amg_hier *h);
 int set_profile(amg_hier *h, int enable);
 void free_profile(amg_hier *h);
+int solve_multi_impl(amg_hier *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
+                     double *res_hist, cudaStream_t s);
+void free_multi(amg_hier *h);
 }  // namespace pcgamg

@@ -1,0 +1,831 @@
+// Multi right-hand-side solve: k systems A x_c = b_c (c < k <= 32) sharing
+// one hierarchy, advanced together (arxiv 2210.16660, Sec. 3.1 / Sec. 5 per
+// column; the hierarchy is built once and reused, Sec. 2 / Sec. 4).
+//
+// Every vector is an n x K row-major block (the K values of a row are
+// contiguous; K = k rounded up to a power of two, at least 4, padding
+// columns are zero and inactive). One thread per (row, column): the K threads of a row read
+// the same matrix entry (one broadcast load) and K consecutive vector values
+// (one coalesced load), so each stored entry is read once per sweep for all
+// columns (SpMM). Each column keeps its own Krylov scalars, iteration count,
+// residual history and status; a column that has converged or failed stops
+// changing (alpha = 0) while the others go on. Same V-cycle structure and
+// reading of the method as the single right-hand-side path.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+#include "sell_row.cuh"
+
+namespace pcgamg {
+
+namespace {
+
+constexpr int kMB = 256;         // threads per block
+constexpr int kMaxK = 32;
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// Thread (row, column) of a K-column block; grid-stride over n * K.
+#define MK_FOR(nrows)                                                                       \
+    for (int64_t g_ = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g_ < (int64_t)(nrows) * K; \
+         g_ += (int64_t)gridDim.x * blockDim.x)
+
+// Per-column block sums of two doubles. Column c = threadIdx.x % K (blockDim
+// and the grid stride are multiples of K). Result: threads 0..K-1 hold the
+// block's sums for columns 0..K-1.
+template <int K>
+__device__ __forceinline__ void block_sum_cols(double &a, double &b) {
+    __shared__ double sa[kMB / 32][kMaxK], sb[kMB / 32][kMaxK];
+#pragma unroll
+    for (int o = 16; o >= K; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < K) { sa[w][lane] = a; sb[w][lane] = b; }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double x = 0.0, y = 0.0;
+        for (int q = 0; q < kMB / 32; q++) { x += sa[q][threadIdx.x]; y += sb[q][threadIdx.x]; }
+        a = x;
+        b = y;
+    }
+}
+
+// Writes the block's per-column partials (layout [slot][column][block]) and
+// returns true in every thread of the last block to finish.
+template <int K>
+__device__ __forceinline__ bool publish_cols(double a, double b, double *partials, unsigned *counter) {
+    __shared__ bool last;
+    block_sum_cols<K>(a, b);
+    int G = gridDim.x;
+    if (threadIdx.x < K) {
+        partials[(0 * K + threadIdx.x) * G + blockIdx.x] = a;
+        partials[(1 * K + threadIdx.x) * G + blockIdx.x] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return last;
+}
+
+// Last block: res[q] = sum over blocks of partials[q][.] in block order, for
+// q < 2K (slot 0 columns, then slot 1 columns).
+template <int K>
+__device__ __forceinline__ void final_cols(const double *partials, double *res) {
+    __threadfence();
+    int G = gridDim.x;
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = w; q < 2 * K; q += kMB / 32) {
+        double s = 0.0;
+        for (int k = lane; k < G; k += 32) s += __ldcg(partials + (int64_t)q * G + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) res[q] = s;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void col_fail(CtlM *c, int col, int status) {
+    c->status[col] = status;
+    c->active[col] = 0;
+}
+
+__device__ __forceinline__ void update_done(CtlM *c) {
+    int any = 0;
+    for (int q = 0; q < c->K; q++) any |= c->active[q];
+    if (!any) c->done = 1;
+}
+
+// ------------------------------------------------------------ V-cycle
+template <typename T, typename IDX, int K, int U, bool STREAM>
+__global__ void __launch_bounds__(kMB) k_down_m(int n, const int32_t *__restrict__ sptr,
+                                               const IDX *__restrict__ col, const T *__restrict__ val,
+                                               const T *__restrict__ xpre, const T *__restrict__ b,
+                                               const T *__restrict__ p, T *__restrict__ t,
+                                               const CtlM *__restrict__ ctl) {
+    if (ctl->done) return;
+    MK_FOR(n) {
+        int i = (int)(g_ / K), c = (int)(g_ % K);
+        int s = i >> 5, lane = i & 31;
+        int32_t base = ldg(sptr + s);
+        int w = (ldg(sptr + s + 1) - base) >> 5;
+        T acc = sell_row<U, STREAM>(col + base + lane, val + base + lane, w, i,
+                                    [&](int j) { return ldg(xpre + (int64_t)j * K + c); });
+        t[g_] = ldg(p + i) * (ldg(b + g_) - acc);
+    }
+}
+
+template <typename T, typename TO, bool PRE, int K>
+__global__ void __launch_bounds__(kMB) k_restrict_m(int nc, const int32_t *__restrict__ rptr,
+                                                   const int32_t *__restrict__ ridx, const T *__restrict__ t,
+                                                   TO *__restrict__ bc, const T *__restrict__ dinvc,
+                                                   T *__restrict__ xprec, const CtlM *__restrict__ ctl) {
+    if (ctl->done) return;
+    MK_FOR(nc) {
+        int I = (int)(g_ / K), c = (int)(g_ % K);
+        T s = 0;
+        for (int32_t q = ldg(rptr + I); q < ldg(rptr + I + 1); q++) s += ldg(t + (int64_t)ldg(ridx + q) * K + c);
+        bc[g_] = (TO)s;
+        if (PRE) xprec[g_] = ldg(dinvc + I) * s;
+    }
+}
+
+// x_L = A_L^{-1} b_L for K columns: one warp per (row, column-group).
+template <typename TO, int K>
+__global__ void __launch_bounds__(kMB) k_coarse_m(int nL, const double *__restrict__ ainv,
+                                                 const double *__restrict__ bL, TO *__restrict__ xL,
+                                                 const CtlM *__restrict__ ctl) {
+    if (ctl->done) return;
+    MK_FOR(nL) {
+        int row = (int)(g_ / K), c = (int)(g_ % K);
+        const double *a = ainv + (int64_t)row * nL;
+        double s = 0.0;
+        for (int j = 0; j < nL; j++) s += ldg(a + j) * ldg(bL + (int64_t)j * K + c);
+        xL[g_] = (TO)s;
+    }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kMB) k_prolong_m(int n, const T *__restrict__ xpre, const T *__restrict__ p,
+                                                  const int32_t *__restrict__ agg, const T *__restrict__ xc,
+                                                  T *__restrict__ xp, const CtlM *__restrict__ ctl) {
+    if (ctl->done) return;
+    MK_FOR(n) {
+        int i = (int)(g_ / K), c = (int)(g_ % K);
+        T x = ldg(xpre + g_);
+        int a = ldg(agg + i);
+        if (a >= 0) x += ldg(p + i) * ldg(xc + (int64_t)a * K + c);
+        xp[g_] = x;
+    }
+}
+
+// z = xp + D^-1 (b - A xp); DOT on level 0: per-column r.z and z.q_old, and
+// the last block forms rho_c and beta_c.
+template <typename T, typename TZ, bool DOT, bool FCG, typename IDX, int K, int U, bool STREAM>
+__global__ void __launch_bounds__(kMB) k_post_m(int n, const int32_t *__restrict__ sptr,
+                                               const IDX *__restrict__ col, const T *__restrict__ val,
+                                               const T *__restrict__ xp, const T *__restrict__ b,
+                                               const T *__restrict__ dinv, TZ *__restrict__ z,
+                                               const double *__restrict__ r64, const double *__restrict__ qold,
+                                               double *partials, CtlM *ctl) {
+    if (ctl->done) return;
+    double rz = 0.0, zq = 0.0;
+    MK_FOR(n) {
+        int i = (int)(g_ / K), c = (int)(g_ % K);
+        int s = i >> 5, lane = i & 31;
+        int32_t base = ldg(sptr + s);
+        int w = (ldg(sptr + s + 1) - base) >> 5;
+        T acc = sell_row<U, STREAM>(col + base + lane, val + base + lane, w, i,
+                                    [&](int j) { return ldg(xp + (int64_t)j * K + c); });
+        TZ zo = (TZ)(ldg(xp + g_) + ldg(dinv + i) * (ldg(b + g_) - acc));
+        z[g_] = zo;
+        if (DOT) {
+            rz += ldg(r64 + g_) * (double)zo;
+            if (FCG) zq += (double)zo * ldg(qold + g_);
+        }
+    }
+    if (DOT) {
+        __shared__ double res[2 * kMaxK];
+        if (publish_cols<K>(rz, zq, partials, &ctl->counter[0])) {
+            final_cols<K>(partials, res);
+            if (threadIdx.x == 0) ctl->counter[0] = 0;
+            int c = threadIdx.x;
+            if (c < K && ctl->active[c]) {
+                double rho = res[c], zqc = res[K + c];
+                if (!isfinite(rho) || !isfinite(zqc)) {
+                    col_fail(ctl, c, AMG_ERR_NAN);
+                } else if (!(rho > 0.0)) {
+                    col_fail(ctl, c, AMG_ERR_BREAKDOWN);
+                } else {
+                    ctl->rho[c] = rho;
+                    double beta = 0.0;
+                    if (!ctl->restart[c])
+                        beta = ctl->mode == AMG_MODE_FCG32 ? -zqc / ctl->pq_old[c] : rho / ctl->rho_old[c];
+                    ctl->beta[c] = beta;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ Krylov
+template <int K>
+__global__ void __launch_bounds__(kMB) k_axpy_m(int n, const double *__restrict__ z, double *__restrict__ p,
+                                               const CtlM *__restrict__ ctl) {
+    if (ctl->done) return;
+    MK_FOR(n) {
+        int c = (int)(g_ % K);
+        p[g_] = ctl->active[c] ? z[g_] + ctl->beta[c] * p[g_] : 0.0;
+    }
+}
+
+template <typename IDX, int K>
+__global__ void __launch_bounds__(kMB) k_spmm_m(int n, const int32_t *__restrict__ sptr,
+                                               const IDX *__restrict__ col, const double *__restrict__ val,
+                                               const double *__restrict__ p, double *__restrict__ q,
+                                               double *partials, CtlM *ctl) {
+    if (ctl->done) return;
+    double pq = 0.0;
+    MK_FOR(n) {
+        int i = (int)(g_ / K), c = (int)(g_ % K);
+        int s = i >> 5, lane = i & 31;
+        int32_t base = ldg(sptr + s);
+        int w = (ldg(sptr + s + 1) - base) >> 5;
+        double acc = sell_row<kUnroll, true>(col + base + lane, val + base + lane, w, i,
+                                             [&](int j) { return ldg(p + (int64_t)j * K + c); });
+        q[g_] = acc;
+        pq += ldg(p + g_) * acc;
+    }
+    __shared__ double res[2 * kMaxK];
+    if (publish_cols<K>(pq, 0.0, partials, &ctl->counter[1])) {
+        final_cols<K>(partials, res);
+        if (threadIdx.x == 0) ctl->counter[1] = 0;
+        int c = threadIdx.x;
+        if (c < K) {
+            if (!ctl->active[c]) {
+                ctl->alpha[c] = 0.0;
+            } else {
+                double a = res[c];
+                if (!isfinite(a)) col_fail(ctl, c, AMG_ERR_NAN);
+                else if (!(a > 0.0)) col_fail(ctl, c, AMG_ERR_BREAKDOWN);
+                else {
+                    ctl->pq[c] = a;
+                    ctl->alpha[c] = ctl->rho[c] / a;
+                }
+                if (!ctl->active[c]) ctl->alpha[c] = 0.0;
+            }
+        }
+    }
+}
+
+template <int MODE, int K>
+__device__ __forceinline__ void emit_r_m(int64_t g, int i, double ri, float *r32, const float *dinv32,
+                                         float *xpre32, const double *dinv64, double *xpre64) {
+    if (MODE == AMG_MODE_FCG32) {
+        float r = (float)ri;
+        r32[g] = r;
+        xpre32[g] = __ldg(dinv32 + i) * r;
+    } else {
+        xpre64[g] = __ldg(dinv64 + i) * ri;
+    }
+}
+
+template <int MODE, int K>
+__global__ void __launch_bounds__(kMB) k_update_m(int n, const double *__restrict__ p,
+                                                 const double *__restrict__ q, double *__restrict__ x,
+                                                 double *__restrict__ r, float *__restrict__ r32,
+                                                 const float *__restrict__ dinv32, float *__restrict__ xpre32,
+                                                 const double *__restrict__ dinv64, double *__restrict__ xpre64,
+                                                 double *partials, CtlM *ctl, double *hist, int hstride) {
+    if (ctl->done) return;
+    double rr = 0.0;
+    MK_FOR(n) {
+        int i = (int)(g_ / K), c = (int)(g_ % K);
+        double ri = r[g_];
+        if (ctl->active[c]) {
+            double al = ctl->alpha[c];
+            x[g_] = x[g_] + al * p[g_];
+            ri = ri - al * q[g_];
+            r[g_] = ri;
+            rr += ri * ri;
+        }
+        emit_r_m<MODE, K>(g_, i, ri, r32, dinv32, xpre32, dinv64, xpre64);
+    }
+    __shared__ double res[2 * kMaxK];
+    if (publish_cols<K>(rr, 0.0, partials, &ctl->counter[2])) {
+        final_cols<K>(partials, res);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ctl->counter[2] = 0;
+            ctl->iter_all += 1;
+            int anycheck = 0;
+            for (int c = 0; c < K; c++) {
+                if (!ctl->active[c]) continue;
+                int it = ctl->iter[c] + 1;
+                ctl->iter[c] = it;
+                double rel = sqrt(res[c]) / ctl->bnorm[c];
+                ctl->rel[c] = rel;
+                hist[(int64_t)c * hstride + it] = rel;
+                ctl->rho_old[c] = ctl->rho[c];
+                ctl->pq_old[c] = ctl->pq[c];
+                ctl->restart[c] = 0;
+                if (!isfinite(rel)) { col_fail(ctl, c, AMG_ERR_NAN); continue; }
+                if (rel <= ctl->rtol) { ctl->check[c] = 1; anycheck = 1; }
+                else if (it >= ctl->maxit) col_fail(ctl, c, AMG_ERR_NOCONV);
+            }
+            ctl->any_check = anycheck;
+            update_done(ctl);
+        }
+    }
+}
+
+// r = b - A x. INIT: every column, plus ||b||; otherwise only the columns
+// whose recursive residual met rtol (the others keep their r).
+template <bool INIT, int MODE, typename IDX, int K>
+__global__ void __launch_bounds__(kMB) k_residual_m(int n, const int32_t *__restrict__ sptr,
+                                                   const IDX *__restrict__ col, const double *__restrict__ val,
+                                                   const double *__restrict__ b, const double *__restrict__ x,
+                                                   double *__restrict__ r, float *__restrict__ r32,
+                                                   const float *__restrict__ dinv32, float *__restrict__ xpre32,
+                                                   const double *__restrict__ dinv64, double *__restrict__ xpre64,
+                                                   double *partials, CtlM *ctl, double *hist, int hstride) {
+    if (ctl->done) return;
+    if (!INIT && !ctl->any_check) return;
+    double rr = 0.0, bb = 0.0;
+    MK_FOR(n) {
+        int i = (int)(g_ / K), c = (int)(g_ % K);
+        if (!INIT && !ctl->check[c]) continue;
+        int s = i >> 5, lane = i & 31;
+        int32_t base = ldg(sptr + s);
+        int w = (ldg(sptr + s + 1) - base) >> 5;
+        double acc = sell_row<kUnroll, true>(col + base + lane, val + base + lane, w, i,
+                                             [&](int j) { return ldg(x + (int64_t)j * K + c); });
+        double bi = ldg(b + g_);
+        double ri = bi - acc;
+        r[g_] = ri;
+        emit_r_m<MODE, K>(g_, i, ri, r32, dinv32, xpre32, dinv64, xpre64);
+        rr += ri * ri;
+        if (INIT) bb += bi * bi;
+    }
+    __shared__ double res[2 * kMaxK];
+    if (publish_cols<K>(rr, bb, partials, &ctl->counter[3])) {
+        final_cols<K>(partials, res);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ctl->counter[3] = 0;
+            for (int c = 0; c < K; c++) {
+                if (INIT) {
+                    double bn = sqrt(res[K + c]);
+                    ctl->bnorm[c] = bn;
+                    ctl->active[c] = 0;
+                    ctl->status[c] = AMG_OK;
+                    if (c >= ctl->k) continue;
+                    if (!isfinite(bn) || !isfinite(res[c])) { col_fail(ctl, c, AMG_ERR_NAN); continue; }
+                    if (bn == 0.0) { ctl->true_rel[c] = 0.0; hist[(int64_t)c * hstride] = 0.0; continue; }
+                    double rel = sqrt(res[c]) / bn;
+                    ctl->rel[c] = rel;
+                    ctl->true_rel[c] = rel;
+                    hist[(int64_t)c * hstride] = rel;
+                    if (rel <= ctl->rtol) continue;
+                    if (ctl->maxit <= 0) { col_fail(ctl, c, AMG_ERR_NOCONV); continue; }
+                    ctl->active[c] = 1;
+                    ctl->restart[c] = 1;
+                } else {
+                    if (!ctl->check[c]) continue;
+                    ctl->check[c] = 0;
+                    double rel = sqrt(res[c]) / ctl->bnorm[c];
+                    ctl->true_rel[c] = rel;
+                    if (!isfinite(rel)) { col_fail(ctl, c, AMG_ERR_NAN); continue; }
+                    if (rel <= ctl->rtol) { ctl->active[c] = 0; ctl->status[c] = AMG_OK; continue; }
+                    ctl->restart[c] = 1;
+                    hist[(int64_t)c * hstride + ctl->iter[c]] = rel;
+                    if (ctl->iter[c] >= ctl->maxit) col_fail(ctl, c, AMG_ERR_NOCONV);
+                }
+            }
+            ctl->any_check = 0;
+            update_done(ctl);
+        }
+    }
+}
+
+__global__ void k_zero_m(double *a, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 0.0;
+}
+
+// Copies between the caller's n x k block and the internal n x K block.
+__global__ void k_pack(const double *__restrict__ src, int k, double *__restrict__ dst, int K, int64_t n) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n * K) return;
+    int64_t i = g / K;
+    int c = (int)(g % K);
+    dst[g] = c < k ? src[i * k + c] : 0.0;
+}
+
+// Unpack; columns with b = 0 get x = 0.
+__global__ void k_unpack(const double *__restrict__ src, int K, double *__restrict__ dst, int k, int64_t n,
+                         const CtlM *__restrict__ ctl) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n * k) return;
+    int64_t i = g / k;
+    int c = (int)(g % k);
+    dst[g] = ctl->bnorm[c] == 0.0 ? 0.0 : src[i * K + c];
+}
+
+__global__ void k_set_cond_m(cudaGraphConditionalHandle hc, CtlM *ctl, int count_body) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (count_body) {
+        int b = ctl->bodies + 1;
+        ctl->bodies = b;
+        if (!ctl->done && b > (ctl->maxit + 1) / 2 + 1) {
+            for (int c = 0; c < ctl->K; c++)
+                if (ctl->active[c]) col_fail(ctl, c, AMG_ERR_NOCONV);
+            ctl->done = 1;
+        }
+    }
+    cudaGraphSetConditional(hc, ctl->done ? 0u : 1u);
+}
+
+inline int grid_of(int64_t items) { return (int)((items + kMB - 1) / kMB); }
+
+template <typename T>
+struct MP;
+template <>
+struct MP<float> {
+    static const float *val(const Level &l) { return l.S.v32; }
+    static const float *dinv(const Level &l) { return l.dinv32; }
+    static const float *p(const Level &l) { return l.p32; }
+    static float *b(MultiLevel &m) { return m.b32; }
+    static float *x(MultiLevel &m) { return m.x32; }
+    static float *t(MultiLevel &m) { return m.t32; }
+    static float *xpre(MultiLevel &m) { return m.xpre32; }
+    static float *xp(MultiLevel &m) { return m.xp32; }
+};
+template <>
+struct MP<double> {
+    static const double *val(const Level &l) { return l.S.v64; }
+    static const double *dinv(const Level &l) { return l.dinv; }
+    static const double *p(const Level &l) { return l.p; }
+    static double *b(MultiLevel &m) { return m.b64; }
+    static double *x(MultiLevel &m) { return m.x64; }
+    static double *t(MultiLevel &m) { return m.t64; }
+    static double *xpre(MultiLevel &m) { return m.xpre64; }
+    static double *xp(MultiLevel &m) { return m.xp64; }
+};
+
+#define WITH_COLS_M(S, BODY)              \
+    do {                                  \
+        if ((S).col16) {                  \
+            using IDX = int16_t;          \
+            const IDX *cols = (S).col16;  \
+            BODY;                         \
+        } else {                          \
+            using IDX = int32_t;          \
+            const IDX *cols = (S).col;    \
+            BODY;                         \
+        }                                 \
+    } while (0)
+
+template <typename T, bool FCG, int K>
+int launch_vcycle_m(amg_hier *h, MultiWS &W, cudaStream_t s) {
+    using P = MP<T>;
+    auto &lev = h->lev;
+    int L = (int)lev.size() - 1;
+    CtlM *ctl = W.ctl;
+    Level &l0 = lev[0];
+    MultiLevel &m0 = W.lev[0];
+    const T *b0;
+    if constexpr (sizeof(T) == 4) b0 = W.r32;
+    else b0 = W.r;
+    int g0 = W.grid;
+    if (L == 0) {
+        // single level: z = A^{-1} r through the coarse kernel (float32 rounding as the V-cycle's)
+        set_error("pcg_solve_multi: single-level hierarchy not supported by the multi-column path");
+        return AMG_ERR_ARG;
+    }
+    WITH_COLS_M(l0.S, (k_down_m<T, IDX, K, kUnroll, true><<<g0, kMB, 0, s>>>(
+                          l0.A.n, l0.S.sptr, cols, P::val(l0), P::xpre(m0), b0, P::p(l0), P::t(m0), ctl)));
+    for (int l = 0; l < L; l++) {
+        Level &lv = lev[l];
+        MultiLevel &mv = W.lev[l];
+        int n = lv.A.n;
+        if (l > 0)
+            WITH_COLS_M(lv.S, (k_down_m<T, IDX, K, kUnroll, false><<<grid_of((int64_t)n * K), kMB, 0, s>>>(
+                                  n, lv.S.sptr, cols, P::val(lv), P::xpre(mv), P::b(mv), P::p(lv), P::t(mv), ctl)));
+        if (l + 1 == L)
+            k_restrict_m<T, double, false, K><<<grid_of((int64_t)lv.nc * K), kMB, 0, s>>>(
+                lv.nc, lv.rptr, lv.ridx, P::t(mv), W.bL, nullptr, nullptr, ctl);
+        else
+            k_restrict_m<T, T, true, K><<<grid_of((int64_t)lv.nc * K), kMB, 0, s>>>(
+                lv.nc, lv.rptr, lv.ridx, P::t(mv), P::b(W.lev[l + 1]), P::dinv(lev[l + 1]), P::xpre(W.lev[l + 1]),
+                ctl);
+    }
+    k_coarse_m<T, K><<<grid_of((int64_t)h->nL * K), kMB, 0, s>>>(h->nL, h->Ainv, W.bL, P::x(W.lev[L]), ctl);
+    for (int l = L - 1; l >= 1; l--) {
+        Level &lv = lev[l];
+        MultiLevel &mv = W.lev[l];
+        int n = lv.A.n;
+        k_prolong_m<T, K><<<grid_of((int64_t)n * K), kMB, 0, s>>>(n, P::xpre(mv), P::p(lv), lv.agg,
+                                                                  P::x(W.lev[l + 1]), P::xp(mv), ctl);
+        WITH_COLS_M(lv.S, (k_post_m<T, T, false, false, IDX, K, kUnroll, false>
+                           <<<grid_of((int64_t)n * K), kMB, 0, s>>>(n, lv.S.sptr, cols, P::val(lv), P::xp(mv),
+                                                                    P::b(mv), P::dinv(lv), P::x(mv), nullptr,
+                                                                    nullptr, nullptr, ctl)));
+    }
+    k_prolong_m<T, K><<<g0, kMB, 0, s>>>(l0.A.n, P::xpre(m0), P::p(l0), l0.agg, P::x(W.lev[1]), P::xp(m0), ctl);
+    WITH_COLS_M(l0.S, (k_post_m<T, double, true, FCG, IDX, K, kUnroll, true><<<g0, kMB, 0, s>>>(
+                          l0.A.n, l0.S.sptr, cols, P::val(l0), P::xp(m0), b0, P::dinv(l0), W.z, W.r, W.q,
+                          W.partials, ctl)));
+    PCG_LAUNCH_CK();
+    return AMG_OK;
+}
+
+template <int K>
+int launch_iteration_m(amg_hier *h, MultiWS &W, int mode, cudaStream_t s) {
+    Level &l0 = h->lev[0];
+    MultiLevel &m0 = W.lev[0];
+    int n = l0.A.n;
+    if (mode == AMG_MODE_FCG32) PCG_TRY((launch_vcycle_m<float, true, K>(h, W, s)));
+    else PCG_TRY((launch_vcycle_m<double, false, K>(h, W, s)));
+    k_axpy_m<K><<<W.grid, kMB, 0, s>>>(n, W.z, W.p, W.ctl);
+    WITH_COLS_M(l0.S, (k_spmm_m<IDX, K><<<W.grid, kMB, 0, s>>>(n, l0.S.sptr, cols, l0.S.v64, W.p, W.q, W.partials,
+                                                               W.ctl)));
+    int hs = W.hist_cap;
+    if (mode == AMG_MODE_FCG32) {
+        k_update_m<AMG_MODE_FCG32, K><<<W.grid, kMB, 0, s>>>(n, W.p, W.q, W.x, W.r, W.r32, l0.dinv32, m0.xpre32,
+                                                             l0.dinv, m0.xpre64, W.partials, W.ctl, W.hist, hs);
+        WITH_COLS_M(l0.S, (k_residual_m<false, AMG_MODE_FCG32, IDX, K><<<W.grid, kMB, 0, s>>>(
+                              n, l0.S.sptr, cols, l0.S.v64, W.b, W.x, W.r, W.r32, l0.dinv32, m0.xpre32, l0.dinv,
+                              m0.xpre64, W.partials, W.ctl, W.hist, hs)));
+    } else {
+        k_update_m<AMG_MODE_PCG64, K><<<W.grid, kMB, 0, s>>>(n, W.p, W.q, W.x, W.r, W.r32, l0.dinv32, m0.xpre32,
+                                                             l0.dinv, m0.xpre64, W.partials, W.ctl, W.hist, hs);
+        WITH_COLS_M(l0.S, (k_residual_m<false, AMG_MODE_PCG64, IDX, K><<<W.grid, kMB, 0, s>>>(
+                              n, l0.S.sptr, cols, l0.S.v64, W.b, W.x, W.r, W.r32, l0.dinv32, m0.xpre32, l0.dinv,
+                              m0.xpre64, W.partials, W.ctl, W.hist, hs)));
+    }
+    PCG_LAUNCH_CK();
+    return AMG_OK;
+}
+
+template <int K>
+int launch_prefix_m(amg_hier *h, MultiWS &W, int mode, cudaStream_t s) {
+    Level &l0 = h->lev[0];
+    MultiLevel &m0 = W.lev[0];
+    int n = l0.A.n;
+    int64_t nk = (int64_t)n * K;
+    k_zero_m<<<grid_of(nk), kMB, 0, s>>>(W.p, nk);
+    k_zero_m<<<grid_of(nk), kMB, 0, s>>>(W.q, nk);
+    int hs = W.hist_cap;
+    if (mode == AMG_MODE_FCG32)
+        WITH_COLS_M(l0.S, (k_residual_m<true, AMG_MODE_FCG32, IDX, K><<<W.grid, kMB, 0, s>>>(
+                              n, l0.S.sptr, cols, l0.S.v64, W.b, W.x, W.r, W.r32, l0.dinv32, m0.xpre32, l0.dinv,
+                              m0.xpre64, W.partials, W.ctl, W.hist, hs)));
+    else
+        WITH_COLS_M(l0.S, (k_residual_m<true, AMG_MODE_PCG64, IDX, K><<<W.grid, kMB, 0, s>>>(
+                              n, l0.S.sptr, cols, l0.S.v64, W.b, W.x, W.r, W.r32, l0.dinv32, m0.xpre32, l0.dinv,
+                              m0.xpre64, W.partials, W.ctl, W.hist, hs)));
+    PCG_LAUNCH_CK();
+    return AMG_OK;
+}
+
+// Whole multi-column solve as one graph (prefix, then a device-side while
+// loop of two iterations per body), as in the single-column path.
+template <int K>
+int build_graph_m(amg_hier *h, MultiWS &W, int mode) {
+    if (!h->cap_stream) PCG_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = h->cap_stream;
+    PCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int st = launch_prefix_m<K>(h, W, mode, cs);
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle hc = 0;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t cnode = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!st) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+    if (!st && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+    if (!st && e == cudaSuccess) {
+        k_set_cond_m<<<1, 32, 0, cs>>>(hc, W.ctl, 0);
+        e = cudaGetLastError();
+    }
+    if (!st && e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd);
+    if (!st && e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hc;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&cnode, g, deps, nullptr, nd, &cp);
+    }
+    if (!st && e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    cudaGraph_t full = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &full);
+    if (st || e != cudaSuccess || e2 != cudaSuccess) {
+        if (full) cudaGraphDestroy(full);
+        if (!st) st = cuda_fail(e != cudaSuccess ? e : e2, "multi solve graph capture", __FILE__, __LINE__);
+        return st;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = launch_iteration_m<K>(h, W, mode, cs);
+        if (!st) st = launch_iteration_m<K>(h, W, mode, cs);
+        if (!st) k_set_cond_m<<<1, 32, 0, cs>>>(hc, W.ctl, 1);
+        cudaGraph_t bout = body;
+        e = cudaStreamEndCapture(cs, &bout);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (st || e != cudaSuccess) {
+        cudaGraphDestroy(full);
+        if (!st) st = cuda_fail(e, "multi solve graph body capture", __FILE__, __LINE__);
+        return st;
+    }
+    e = cudaGraphInstantiate(&W.gexec[mode], full, 0);
+    cudaGraphDestroy(full);
+    if (e != cudaSuccess) {
+        W.gexec[mode] = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate (multi)", __FILE__, __LINE__);
+    }
+    return AMG_OK;
+}
+
+bool is_dev(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Workspace of K columns (reallocated when K or the history length grows).
+int ensure_ws(amg_hier *h, int K, int maxit) {
+    MultiWS &W = h->multi;
+    if (W.K == K && W.hist_cap >= maxit + 1) return AMG_OK;
+    free_multi(h);
+    Mem &M = h->mem;
+    int L = (int)h->lev.size() - 1;
+    int n0 = h->lev[0].A.n;
+    int64_t nk = (int64_t)n0 * K;
+    W.K = K;
+    W.hist_cap = maxit + 1 > 1001 ? maxit + 1 : 1001;
+    PCG_TRY(alloc(M, &W.b, nk));
+    PCG_TRY(alloc(M, &W.x, nk));
+    PCG_TRY(alloc(M, &W.r, nk));
+    PCG_TRY(alloc(M, &W.z, nk));
+    PCG_TRY(alloc(M, &W.p, nk));
+    PCG_TRY(alloc(M, &W.q, nk));
+    PCG_TRY(alloc(M, &W.r32, nk));
+    W.lev.assign(L + 1, MultiLevel{});
+    for (int l = 0; l <= L; l++) {
+        int64_t m = (int64_t)h->lev[l].A.n * K;
+        MultiLevel &v = W.lev[l];
+        PCG_TRY(alloc(M, &v.b32, m));
+        PCG_TRY(alloc(M, &v.x32, m));
+        PCG_TRY(alloc(M, &v.t32, m));
+        PCG_TRY(alloc(M, &v.xpre32, m));
+        PCG_TRY(alloc(M, &v.xp32, m));
+        PCG_TRY(alloc(M, &v.b64, m));
+        PCG_TRY(alloc(M, &v.x64, m));
+        PCG_TRY(alloc(M, &v.t64, m));
+        PCG_TRY(alloc(M, &v.xpre64, m));
+        PCG_TRY(alloc(M, &v.xp64, m));
+    }
+    PCG_TRY(alloc(M, &W.bL, (int64_t)h->nL * K));
+    int sms = 0;
+    PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    int64_t want = (nk + kMB - 1) / kMB;
+    int64_t cap = (int64_t)sms * 8;
+    W.grid = (int)(want < cap ? want : cap);
+    if (W.grid < 1) W.grid = 1;
+    PCG_TRY(alloc(M, &W.partials, (size_t)2 * K * W.grid));
+    PCG_TRY(alloc(M, &W.ctl, 1));
+    PCG_CK(cudaMemsetAsync(W.ctl, 0, sizeof(CtlM), M.stream));
+    PCG_CK(cudaMallocHost(&W.ctl_host, sizeof(CtlM)));
+    PCG_TRY(alloc(M, &W.hist, (size_t)K * W.hist_cap));
+    return AMG_OK;
+}
+
+template <int K>
+int solve_multi_k(amg_hier *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
+                  double *res_hist, cudaStream_t s) {
+    PCG_TRY(ensure_ws(h, K, maxit));
+    MultiWS &W = h->multi;
+    int n = h->lev[0].A.n;
+    int64_t nk = (int64_t)n * K;
+    int64_t nkk = (int64_t)n * k;
+    Mem &M = h->mem;
+    M.stream = s;
+    // inputs into the internal n x K block (through a device staging copy when on the host)
+    const double *bsrc = B, *xsrc = X;
+    double *stage = nullptr;
+    bool bdev = is_dev(B), xdev = is_dev(X);
+    if (!bdev || !xdev) PCG_TRY(alloc(M, &stage, (size_t)nkk));
+    if (!bdev) {
+        PCG_CK(cudaMemcpyAsync(stage, B, sizeof(double) * nkk, cudaMemcpyHostToDevice, s));
+        bsrc = stage;
+    }
+    k_pack<<<grid_of(nk), kMB, 0, s>>>(bsrc, k, W.b, K, n);
+    if (!xdev) {
+        PCG_CK(cudaMemcpyAsync(stage, X, sizeof(double) * nkk, cudaMemcpyHostToDevice, s));
+        xsrc = stage;
+    }
+    k_pack<<<grid_of(nk), kMB, 0, s>>>(xsrc, k, W.x, K, n);
+    PCG_LAUNCH_CK();
+    CtlM c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.rtol = rtol;
+    c0.maxit = maxit;
+    c0.mode = h->mode;
+    c0.k = k;
+    c0.K = K;
+    *W.ctl_host = c0;
+    PCG_CK(cudaMemcpyAsync(W.ctl, W.ctl_host, sizeof(CtlM), cudaMemcpyHostToDevice, s));
+    int mode = h->mode;
+    bool graph = h->use_graph;
+    if (graph && !W.gexec[mode]) {
+        if (build_graph_m<K>(h, W, mode) != AMG_OK) graph = false;
+    }
+    if (graph) {
+        PCG_CK(cudaGraphLaunch(W.gexec[mode], s));
+        PCG_CK(cudaMemcpyAsync(W.ctl_host, W.ctl, sizeof(CtlM), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaStreamSynchronize(s));
+    } else {
+        PCG_TRY(launch_prefix_m<K>(h, W, mode, s));
+        int launched = 0;
+        for (;;) {
+            PCG_CK(cudaMemcpyAsync(W.ctl_host, W.ctl, sizeof(CtlM), cudaMemcpyDeviceToHost, s));
+            PCG_CK(cudaStreamSynchronize(s));
+            if (W.ctl_host->done || launched >= maxit) break;
+            for (int q = 0; q < 4 && launched < maxit; q++, launched++) PCG_TRY(launch_iteration_m<K>(h, W, mode, s));
+        }
+    }
+    CtlM &c = *W.ctl_host;
+    double *xdst = xdev ? X : stage;
+    k_unpack<<<grid_of(nkk), kMB, 0, s>>>(W.x, K, xdst, k, n, W.ctl);
+    PCG_LAUNCH_CK();
+    if (!xdev) PCG_CK(cudaMemcpyAsync(X, stage, sizeof(double) * nkk, cudaMemcpyDeviceToHost, s));
+    if (res_hist) {
+        int hl = maxit + 1;
+        for (int q = 0; q < k; q++)
+            PCG_CK(cudaMemcpyAsync(res_hist + (int64_t)q * hl, W.hist + (int64_t)q * W.hist_cap,
+                                   sizeof(double) * (c.iter[q] + 1), cudaMemcpyDefault, s));
+    }
+    PCG_CK(cudaStreamSynchronize(s));
+    if (stage) release(M, stage);
+    int st = AMG_OK;
+    for (int q = 0; q < k; q++) {
+        if (iters) iters[q] = c.iter[q];
+        h->multi_status[q] = c.status[q];
+        h->multi_true_rel[q] = c.true_rel[q];
+        if (c.status[q] != AMG_OK && st == AMG_OK) st = c.status[q];
+    }
+    h->multi_k = k;
+    if (st) set_error("pcg_solve_multi: some columns failed (status %d; see amg_multi_info)", st);
+    return st;
+}
+
+}  // namespace
+
+void free_multi(amg_hier *h) {
+    MultiWS &W = h->multi;
+    Mem &M = h->mem;
+    for (auto &g : W.gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    release(M, W.b);
+    release(M, W.x);
+    release(M, W.r);
+    release(M, W.z);
+    release(M, W.p);
+    release(M, W.q);
+    release(M, W.r32);
+    for (auto &v : W.lev) {
+        release(M, v.b32); release(M, v.x32); release(M, v.t32); release(M, v.xpre32); release(M, v.xp32);
+        release(M, v.b64); release(M, v.x64); release(M, v.t64); release(M, v.xpre64); release(M, v.xp64);
+    }
+    W.lev.clear();
+    release(M, W.bL);
+    release(M, W.partials);
+    release(M, W.ctl);
+    release(M, W.hist);
+    if (W.ctl_host) cudaFreeHost(W.ctl_host);
+    W.ctl_host = nullptr;
+    W.K = 0;
+    W.hist_cap = 0;
+}
+
+int solve_multi_impl(amg_hier *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
+                     double *res_hist, cudaStream_t s) {
+    if (k < 1 || k > kMaxK || !B || !X || !(rtol >= 0.0) || maxit < 0) {
+        set_error("pcg_solve_multi: bad arguments (1 <= k <= 32, rtol >= 0, maxit >= 0)");
+        return AMG_ERR_ARG;
+    }
+    if (h->lev.size() < 2) {
+        set_error("pcg_solve_multi: the hierarchy has a single level; use pcg_solve per column");
+        return AMG_ERR_ARG;
+    }
+    int K = 4;
+    while (K < k) K <<= 1;
+    switch (K) {
+        case 4: return solve_multi_k<4>(h, k, B, X, rtol, maxit, iters, res_hist, s);
+        case 8: return solve_multi_k<8>(h, k, B, X, rtol, maxit, iters, res_hist, s);
+        case 16: return solve_multi_k<16>(h, k, B, X, rtol, maxit, iters, res_hist, s);
+        default: return solve_multi_k<32>(h, k, B, X, rtol, maxit, iters, res_hist, s);
+    }
+}
+
+}  // namespace pcgamg

@@ -201,11 +201,13 @@ def q1_laplacian(N: int, ratio: float = 1.0, lx: float = 1.0, ly: float = 1.0,
 
 
 def spmv(A: CSR, x: np.ndarray) -> np.ndarray:
-    """``A @ x`` for input generation (row sums in stored order)."""
-    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    """``A @ x`` for input generation (segment sums over each row's entries)."""
     prod = A.val * x[A.col]
     out = np.zeros(A.n)
-    np.add.at(out, rows, prod)
+    nonempty = np.diff(A.row_ptr) > 0
+    if prod.size:
+        sums = np.add.reduceat(prod, A.row_ptr[:-1][nonempty])
+        out[nonempty] = sums
     return out
 
 
