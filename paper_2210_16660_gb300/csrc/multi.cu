@@ -29,43 +29,130 @@ constexpr int kMaxK = 32;
 template <typename T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 
-// Thread (row, column) of a K-column block; grid-stride over n * K.
-#define MK_FOR(nrows)                                                                       \
-    for (int64_t g_ = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g_ < (int64_t)(nrows) * K; \
-         g_ += (int64_t)gridDim.x * blockDim.x)
+// Each thread owns V consecutive columns of one row (one 16-byte vector: 4
+// floats or 2 doubles), so a row takes K / V threads, a warp covers 32V/K
+// consecutive rows, a neighbour row's column group is one vector load, and
+// the matrix entry of a row is one broadcast load shared by its threads.
+template <typename T>
+struct VW {
+    static constexpr int V = 16 / (int)sizeof(T);
+};
 
-// Per-column block sums of two doubles. Column c = threadIdx.x % K (blockDim
-// and the grid stride are multiples of K). Result: threads 0..K-1 hold the
-// block's sums for columns 0..K-1.
-template <int K>
-__device__ __forceinline__ void block_sum_cols(double &a, double &b) {
+template <typename T, int V>
+__device__ __forceinline__ void ld_vec(const T *p, T (&o)[V]) {
+    if constexpr (sizeof(T) == 4) {
+        float4 u = __ldg(reinterpret_cast<const float4 *>(p));
+        o[0] = u.x; o[1] = u.y; o[2] = u.z; o[3] = u.w;
+    } else {
+        double2 u = __ldg(reinterpret_cast<const double2 *>(p));
+        o[0] = u.x; o[1] = u.y;
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void ld_vec_cg(const T *p, T (&o)[V]) {
+    if constexpr (sizeof(T) == 4) {
+        float4 u = __ldcg(reinterpret_cast<const float4 *>(p));
+        o[0] = u.x; o[1] = u.y; o[2] = u.z; o[3] = u.w;
+    } else {
+        double2 u = __ldcg(reinterpret_cast<const double2 *>(p));
+        o[0] = u.x; o[1] = u.y;
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void st_vec(T *p, const T (&o)[V]) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+        *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+    }
+}
+
+// acc[v] += sum_k a_k x(j_k)[v] over one sliced-ELL row, entries in storage
+// order; U entries' columns and values are loaded before their gathers.
+template <int U, bool STREAM, int V, typename IDX, typename T, typename F>
+__device__ __forceinline__ void sell_row_vec(const IDX *__restrict__ c, const T *__restrict__ a, int w, int row,
+                                             F xvec, T (&acc)[V]) {
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = 0;
+    int k = 0;
+    for (; k + U <= w; k += U) {
+        int j[U];
+        T av[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            j[u] = col_of(ld_mat<STREAM>(c + 32 * (k + u)), row);
+            av[u] = ld_mat<STREAM>(a + 32 * (k + u));
+        }
+        T x[U][V];
+#pragma unroll
+        for (int u = 0; u < U; u++) xvec(j[u], x[u]);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] += av[u] * x[u][v];
+    }
+    for (; k < w; k++) {
+        int j = col_of(ld_mat<STREAM>(c + 32 * k), row);
+        T av = ld_mat<STREAM>(a + 32 * k);
+        T x[V];
+        xvec(j, x);
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] += av * x[v];
+    }
+}
+
+// Thread (row i, first column c0) of a K-column block; grid-stride over
+// n * (K / V) threads.
+#define MK_FOR(nrows, V)                                                                      \
+    for (int64_t g_ = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;                         \
+         g_ < (int64_t)(nrows) * (K / (V)); g_ += (int64_t)gridDim.x * blockDim.x)
+#define MK_IDX(V)                                                                             \
+    int i = (int)(g_ / (K / (V)));                                                            \
+    int c0 = (int)(g_ % (K / (V))) * (V);                                                     \
+    int64_t e0 = (int64_t)i * K + c0;
+
+// Per-column block sums: a thread holds a[V] and b[V] for columns c0..c0+V-1
+// (c0 fixed per thread). Result: threads 0..K-1 hold the block's sums for
+// columns 0..K-1.
+template <int K, int V>
+__device__ __forceinline__ void block_sum_cols(double (&a)[V], double (&b)[V], double &ra, double &rb) {
+    constexpr int TPR = K / V;
     __shared__ double sa[kMB / 32][kMaxK], sb[kMB / 32][kMaxK];
 #pragma unroll
-    for (int o = 16; o >= K; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
+    for (int o = 16; o >= TPR; o >>= 1)
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            a[v] += __shfl_down_sync(0xffffffffu, a[v], o);
+            b[v] += __shfl_down_sync(0xffffffffu, b[v], o);
+        }
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane < K) { sa[w][lane] = a; sb[w][lane] = b; }
+    if (lane < TPR)
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            sa[w][lane * V + v] = a[v];
+            sb[w][lane * V + v] = b[v];
+        }
     __syncthreads();
+    ra = rb = 0.0;
     if (threadIdx.x < K) {
-        double x = 0.0, y = 0.0;
-        for (int q = 0; q < kMB / 32; q++) { x += sa[q][threadIdx.x]; y += sb[q][threadIdx.x]; }
-        a = x;
-        b = y;
+        for (int q = 0; q < kMB / 32; q++) { ra += sa[q][threadIdx.x]; rb += sb[q][threadIdx.x]; }
     }
 }
 
 // Writes the block's per-column partials (layout [slot][column][block]) and
 // returns true in every thread of the last block to finish.
-template <int K>
-__device__ __forceinline__ bool publish_cols(double a, double b, double *partials, unsigned *counter) {
+template <int K, int V>
+__device__ __forceinline__ bool publish_cols(double (&a)[V], double (&b)[V], double *partials,
+                                             unsigned *counter) {
     __shared__ bool last;
-    block_sum_cols<K>(a, b);
+    double ra, rb;
+    block_sum_cols<K, V>(a, b, ra, rb);
     int G = gridDim.x;
     if (threadIdx.x < K) {
-        partials[(0 * K + threadIdx.x) * G + blockIdx.x] = a;
-        partials[(1 * K + threadIdx.x) * G + blockIdx.x] = b;
+        partials[(0 * K + threadIdx.x) * G + blockIdx.x] = ra;
+        partials[(1 * K + threadIdx.x) * G + blockIdx.x] = rb;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -78,15 +165,25 @@ __device__ __forceinline__ bool publish_cols(double a, double b, double *partial
 }
 
 // Last block: res[q] = sum over blocks of partials[q][.] in block order, for
-// q < 2K (slot 0 columns, then slot 1 columns).
+// q < 2K (slot 0 columns, then slot 1 columns). Loads are unrolled so each
+// lane has several in flight.
 template <int K>
 __device__ __forceinline__ void final_cols(const double *partials, double *res) {
     __threadfence();
     int G = gridDim.x;
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = w; q < 2 * K; q += kMB / 32) {
-        double s = 0.0;
-        for (int k = lane; k < G; k += 32) s += __ldcg(partials + (int64_t)q * G + k);
+        const double *src = partials + (int64_t)q * G;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int k = lane;
+        for (; k + 96 < G; k += 128) {
+            s0 += __ldcg(src + k);
+            s1 += __ldcg(src + k + 32);
+            s2 += __ldcg(src + k + 64);
+            s3 += __ldcg(src + k + 96);
+        }
+        for (; k < G; k += 32) s0 += __ldcg(src + k);
+        double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) res[q] = s;
@@ -112,15 +209,22 @@ __global__ void __launch_bounds__(kMB) k_down_m(int n, const int32_t *__restrict
                                                const T *__restrict__ xpre, const T *__restrict__ b,
                                                const T *__restrict__ p, T *__restrict__ t,
                                                const CtlM *__restrict__ ctl) {
+    constexpr int V = VW<T>::V;
     if (ctl->done) return;
-    MK_FOR(n) {
-        int i = (int)(g_ / K), c = (int)(g_ % K);
+    MK_FOR(n, V) {
+        MK_IDX(V)
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
         int w = (ldg(sptr + s + 1) - base) >> 5;
-        T acc = sell_row<U, STREAM>(col + base + lane, val + base + lane, w, i,
-                                    [&](int j) { return ldg(xpre + (int64_t)j * K + c); });
-        t[g_] = ldg(p + i) * (ldg(b + g_) - acc);
+        T acc[V];
+        sell_row_vec<U, STREAM, V>(col + base + lane, val + base + lane, w, i,
+                                   [&](int j, T (&x)[V]) { ld_vec<T, V>(xpre + (int64_t)j * K + c0, x); }, acc);
+        T bv[V], o[V];
+        ld_vec<T, V>(b + e0, bv);
+        T pi = ldg(p + i);
+#pragma unroll
+        for (int v = 0; v < V; v++) o[v] = pi * (bv[v] - acc[v]);
+        st_vec<T, V>(t + e0, o);
     }
 }
 
@@ -129,28 +233,49 @@ __global__ void __launch_bounds__(kMB) k_restrict_m(int nc, const int32_t *__res
                                                    const int32_t *__restrict__ ridx, const T *__restrict__ t,
                                                    TO *__restrict__ bc, const T *__restrict__ dinvc,
                                                    T *__restrict__ xprec, const CtlM *__restrict__ ctl) {
+    constexpr int V = VW<T>::V;
     if (ctl->done) return;
-    MK_FOR(nc) {
-        int I = (int)(g_ / K), c = (int)(g_ % K);
-        T s = 0;
-        for (int32_t q = ldg(rptr + I); q < ldg(rptr + I + 1); q++) s += ldg(t + (int64_t)ldg(ridx + q) * K + c);
-        bc[g_] = (TO)s;
-        if (PRE) xprec[g_] = ldg(dinvc + I) * s;
+    MK_FOR(nc, V) {
+        MK_IDX(V)
+        T s[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) s[v] = 0;
+        for (int32_t q = ldg(rptr + i); q < ldg(rptr + i + 1); q++) {
+            T x[V];
+            ld_vec<T, V>(t + (int64_t)ldg(ridx + q) * K + c0, x);
+#pragma unroll
+            for (int v = 0; v < V; v++) s[v] += x[v];
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) bc[e0 + v] = (TO)s[v];
+        if (PRE) {
+            T d = ldg(dinvc + i), o[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) o[v] = d * s[v];
+            st_vec<T, V>(xprec + e0, o);
+        }
     }
 }
 
-// x_L = A_L^{-1} b_L for K columns: one warp per (row, column-group).
+// x_L = A_L^{-1} b_L for K columns (float64, two columns per thread).
 template <typename TO, int K>
 __global__ void __launch_bounds__(kMB) k_coarse_m(int nL, const double *__restrict__ ainv,
                                                  const double *__restrict__ bL, TO *__restrict__ xL,
                                                  const CtlM *__restrict__ ctl) {
+    constexpr int V = 2;
     if (ctl->done) return;
-    MK_FOR(nL) {
-        int row = (int)(g_ / K), c = (int)(g_ % K);
-        const double *a = ainv + (int64_t)row * nL;
-        double s = 0.0;
-        for (int j = 0; j < nL; j++) s += ldg(a + j) * ldg(bL + (int64_t)j * K + c);
-        xL[g_] = (TO)s;
+    MK_FOR(nL, V) {
+        MK_IDX(V)
+        const double *a = ainv + (int64_t)i * nL;
+        double s0 = 0.0, s1 = 0.0;
+        for (int j = 0; j < nL; j++) {
+            double aj = ldg(a + j);
+            double2 bj = __ldg(reinterpret_cast<const double2 *>(bL + (int64_t)j * K + c0));
+            s0 += aj * bj.x;
+            s1 += aj * bj.y;
+        }
+        xL[e0] = (TO)s0;
+        xL[e0 + 1] = (TO)s1;
     }
 }
 
@@ -158,13 +283,20 @@ template <typename T, int K>
 __global__ void __launch_bounds__(kMB) k_prolong_m(int n, const T *__restrict__ xpre, const T *__restrict__ p,
                                                   const int32_t *__restrict__ agg, const T *__restrict__ xc,
                                                   T *__restrict__ xp, const CtlM *__restrict__ ctl) {
+    constexpr int V = VW<T>::V;
     if (ctl->done) return;
-    MK_FOR(n) {
-        int i = (int)(g_ / K), c = (int)(g_ % K);
-        T x = ldg(xpre + g_);
+    MK_FOR(n, V) {
+        MK_IDX(V)
+        T x[V];
+        ld_vec<T, V>(xpre + e0, x);
         int a = ldg(agg + i);
-        if (a >= 0) x += ldg(p + i) * ldg(xc + (int64_t)a * K + c);
-        xp[g_] = x;
+        if (a >= 0) {
+            T pi = ldg(p + i), y[V];
+            ld_vec<T, V>(xc + (int64_t)a * K + c0, y);
+#pragma unroll
+            for (int v = 0; v < V; v++) x[v] += pi * y[v];
+        }
+        st_vec<T, V>(xp + e0, x);
     }
 }
 
@@ -177,25 +309,36 @@ __global__ void __launch_bounds__(kMB) k_post_m(int n, const int32_t *__restrict
                                                const T *__restrict__ dinv, TZ *__restrict__ z,
                                                const double *__restrict__ r64, const double *__restrict__ qold,
                                                double *partials, CtlM *ctl) {
+    constexpr int V = VW<T>::V;
     if (ctl->done) return;
-    double rz = 0.0, zq = 0.0;
-    MK_FOR(n) {
-        int i = (int)(g_ / K), c = (int)(g_ % K);
+    double rz[V], zq[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) rz[v] = zq[v] = 0.0;
+    MK_FOR(n, V) {
+        MK_IDX(V)
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
         int w = (ldg(sptr + s + 1) - base) >> 5;
-        T acc = sell_row<U, STREAM>(col + base + lane, val + base + lane, w, i,
-                                    [&](int j) { return ldg(xp + (int64_t)j * K + c); });
-        TZ zo = (TZ)(ldg(xp + g_) + ldg(dinv + i) * (ldg(b + g_) - acc));
-        z[g_] = zo;
-        if (DOT) {
-            rz += ldg(r64 + g_) * (double)zo;
-            if (FCG) zq += (double)zo * ldg(qold + g_);
+        T acc[V];
+        sell_row_vec<U, STREAM, V>(col + base + lane, val + base + lane, w, i,
+                                   [&](int j, T (&x)[V]) { ld_vec<T, V>(xp + (int64_t)j * K + c0, x); }, acc);
+        T xv[V], bv[V];
+        ld_vec<T, V>(xp + e0, xv);
+        ld_vec<T, V>(b + e0, bv);
+        T d = ldg(dinv + i);
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            TZ zo = (TZ)(xv[v] + d * (bv[v] - acc[v]));
+            z[e0 + v] = zo;
+            if (DOT) {
+                rz[v] += ldg(r64 + e0 + v) * (double)zo;
+                if (FCG) zq[v] += (double)zo * ldg(qold + e0 + v);
+            }
         }
     }
     if (DOT) {
         __shared__ double res[2 * kMaxK];
-        if (publish_cols<K>(rz, zq, partials, &ctl->counter[0])) {
+        if (publish_cols<K, V>(rz, zq, partials, &ctl->counter[0])) {
             final_cols<K>(partials, res);
             if (threadIdx.x == 0) ctl->counter[0] = 0;
             int c = threadIdx.x;
@@ -221,10 +364,16 @@ __global__ void __launch_bounds__(kMB) k_post_m(int n, const int32_t *__restrict
 template <int K>
 __global__ void __launch_bounds__(kMB) k_axpy_m(int n, const double *__restrict__ z, double *__restrict__ p,
                                                const CtlM *__restrict__ ctl) {
+    constexpr int V = 2;
     if (ctl->done) return;
-    MK_FOR(n) {
-        int c = (int)(g_ % K);
-        p[g_] = ctl->active[c] ? z[g_] + ctl->beta[c] * p[g_] : 0.0;
+    MK_FOR(n, V) {
+        MK_IDX(V)
+        double zv[V], pv[V], o[V];
+        ld_vec<double, V>(z + e0, zv);
+        ld_vec_cg<double, V>(p + e0, pv);
+#pragma unroll
+        for (int v = 0; v < V; v++) o[v] = ctl->active[c0 + v] ? zv[v] + ctl->beta[c0 + v] * pv[v] : 0.0;
+        st_vec<double, V>(p + e0, o);
     }
 }
 
@@ -233,20 +382,26 @@ __global__ void __launch_bounds__(kMB) k_spmm_m(int n, const int32_t *__restrict
                                                const IDX *__restrict__ col, const double *__restrict__ val,
                                                const double *__restrict__ p, double *__restrict__ q,
                                                double *partials, CtlM *ctl) {
+    constexpr int V = 2;
     if (ctl->done) return;
-    double pq = 0.0;
-    MK_FOR(n) {
-        int i = (int)(g_ / K), c = (int)(g_ % K);
+    double pq[V] = {0.0, 0.0}, unused[V] = {0.0, 0.0};
+    MK_FOR(n, V) {
+        MK_IDX(V)
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
         int w = (ldg(sptr + s + 1) - base) >> 5;
-        double acc = sell_row<kUnroll, true>(col + base + lane, val + base + lane, w, i,
-                                             [&](int j) { return ldg(p + (int64_t)j * K + c); });
-        q[g_] = acc;
-        pq += ldg(p + g_) * acc;
+        double acc[V];
+        sell_row_vec<kUnroll, true, V>(col + base + lane, val + base + lane, w, i,
+                                       [&](int j, double (&x)[V]) { ld_vec<double, V>(p + (int64_t)j * K + c0, x); },
+                                       acc);
+        st_vec<double, V>(q + e0, acc);
+        double pv[V];
+        ld_vec<double, V>(p + e0, pv);
+#pragma unroll
+        for (int v = 0; v < V; v++) pq[v] += pv[v] * acc[v];
     }
     __shared__ double res[2 * kMaxK];
-    if (publish_cols<K>(pq, 0.0, partials, &ctl->counter[1])) {
+    if (publish_cols<K, V>(pq, unused, partials, &ctl->counter[1])) {
         final_cols<K>(partials, res);
         if (threadIdx.x == 0) ctl->counter[1] = 0;
         int c = threadIdx.x;
@@ -267,15 +422,18 @@ __global__ void __launch_bounds__(kMB) k_spmm_m(int n, const int32_t *__restrict
     }
 }
 
-template <int MODE, int K>
-__device__ __forceinline__ void emit_r_m(int64_t g, int i, double ri, float *r32, const float *dinv32,
+// The mode's copy of r for the V-cycle, two columns at a time.
+template <int MODE>
+__device__ __forceinline__ void emit_r_m(int64_t e, int i, const double (&ri)[2], float *r32, const float *dinv32,
                                          float *xpre32, const double *dinv64, double *xpre64) {
     if (MODE == AMG_MODE_FCG32) {
-        float r = (float)ri;
-        r32[g] = r;
-        xpre32[g] = __ldg(dinv32 + i) * r;
+        float d = __ldg(dinv32 + i);
+        float a = (float)ri[0], b = (float)ri[1];
+        *reinterpret_cast<float2 *>(r32 + e) = make_float2(a, b);
+        *reinterpret_cast<float2 *>(xpre32 + e) = make_float2(d * a, d * b);
     } else {
-        xpre64[g] = __ldg(dinv64 + i) * ri;
+        double d = __ldg(dinv64 + i);
+        *reinterpret_cast<double2 *>(xpre64 + e) = make_double2(d * ri[0], d * ri[1]);
     }
 }
 
@@ -286,22 +444,31 @@ __global__ void __launch_bounds__(kMB) k_update_m(int n, const double *__restric
                                                  const float *__restrict__ dinv32, float *__restrict__ xpre32,
                                                  const double *__restrict__ dinv64, double *__restrict__ xpre64,
                                                  double *partials, CtlM *ctl, double *hist, int hstride) {
+    constexpr int V = 2;
     if (ctl->done) return;
-    double rr = 0.0;
-    MK_FOR(n) {
-        int i = (int)(g_ / K), c = (int)(g_ % K);
-        double ri = r[g_];
-        if (ctl->active[c]) {
-            double al = ctl->alpha[c];
-            x[g_] = x[g_] + al * p[g_];
-            ri = ri - al * q[g_];
-            r[g_] = ri;
-            rr += ri * ri;
+    double rr[V] = {0.0, 0.0}, unused[V] = {0.0, 0.0};
+    MK_FOR(n, V) {
+        MK_IDX(V)
+        double rv[V], xv[V], pv[V], qv[V];
+        ld_vec_cg<double, V>(r + e0, rv);
+        ld_vec_cg<double, V>(x + e0, xv);
+        ld_vec<double, V>(p + e0, pv);
+        ld_vec<double, V>(q + e0, qv);
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            if (ctl->active[c0 + v]) {
+                double al = ctl->alpha[c0 + v];
+                xv[v] = xv[v] + al * pv[v];
+                rv[v] = rv[v] - al * qv[v];
+                rr[v] += rv[v] * rv[v];
+            }
         }
-        emit_r_m<MODE, K>(g_, i, ri, r32, dinv32, xpre32, dinv64, xpre64);
+        st_vec<double, V>(x + e0, xv);
+        st_vec<double, V>(r + e0, rv);
+        emit_r_m<MODE>(e0, i, rv, r32, dinv32, xpre32, dinv64, xpre64);
     }
     __shared__ double res[2 * kMaxK];
-    if (publish_cols<K>(rr, 0.0, partials, &ctl->counter[2])) {
+    if (publish_cols<K, V>(rr, unused, partials, &ctl->counter[2])) {
         final_cols<K>(partials, res);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -338,26 +505,37 @@ __global__ void __launch_bounds__(kMB) k_residual_m(int n, const int32_t *__rest
                                                    const float *__restrict__ dinv32, float *__restrict__ xpre32,
                                                    const double *__restrict__ dinv64, double *__restrict__ xpre64,
                                                    double *partials, CtlM *ctl, double *hist, int hstride) {
+    constexpr int V = 2;
     if (ctl->done) return;
     if (!INIT && !ctl->any_check) return;
-    double rr = 0.0, bb = 0.0;
-    MK_FOR(n) {
-        int i = (int)(g_ / K), c = (int)(g_ % K);
-        if (!INIT && !ctl->check[c]) continue;
+    double rr[V] = {0.0, 0.0}, bb[V] = {0.0, 0.0};
+    MK_FOR(n, V) {
+        MK_IDX(V)
+        bool use0 = INIT || ctl->check[c0], use1 = INIT || ctl->check[c0 + 1];
+        if (!use0 && !use1) continue;
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
         int w = (ldg(sptr + s + 1) - base) >> 5;
-        double acc = sell_row<kUnroll, true>(col + base + lane, val + base + lane, w, i,
-                                             [&](int j) { return ldg(x + (int64_t)j * K + c); });
-        double bi = ldg(b + g_);
-        double ri = bi - acc;
-        r[g_] = ri;
-        emit_r_m<MODE, K>(g_, i, ri, r32, dinv32, xpre32, dinv64, xpre64);
-        rr += ri * ri;
-        if (INIT) bb += bi * bi;
+        double acc[V];
+        sell_row_vec<kUnroll, true, V>(col + base + lane, val + base + lane, w, i,
+                                       [&](int j, double (&xx)[V]) { ld_vec<double, V>(x + (int64_t)j * K + c0, xx); },
+                                       acc);
+        double bv[V], rv[V];
+        ld_vec<double, V>(b + e0, bv);
+        ld_vec_cg<double, V>(r + e0, rv);
+        if (use0) rv[0] = bv[0] - acc[0];
+        if (use1) rv[1] = bv[1] - acc[1];
+        st_vec<double, V>(r + e0, rv);
+        emit_r_m<MODE>(e0, i, rv, r32, dinv32, xpre32, dinv64, xpre64);
+        if (use0) rr[0] += rv[0] * rv[0];
+        if (use1) rr[1] += rv[1] * rv[1];
+        if (INIT) {
+            bb[0] += bv[0] * bv[0];
+            bb[1] += bv[1] * bv[1];
+        }
     }
     __shared__ double res[2 * kMaxK];
-    if (publish_cols<K>(rr, bb, partials, &ctl->counter[3])) {
+    if (publish_cols<K, V>(rr, bb, partials, &ctl->counter[3])) {
         final_cols<K>(partials, res);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -478,6 +656,8 @@ struct MP<double> {
 template <typename T, bool FCG, int K>
 int launch_vcycle_m(amg_hier *h, MultiWS &W, cudaStream_t s) {
     using P = MP<T>;
+    constexpr int V = VW<T>::V;
+    auto gv = [](int64_t rows) { return grid_of(rows * (K / V)); };
     auto &lev = h->lev;
     int L = (int)lev.size() - 1;
     CtlM *ctl = W.ctl;
@@ -499,25 +679,25 @@ int launch_vcycle_m(amg_hier *h, MultiWS &W, cudaStream_t s) {
         MultiLevel &mv = W.lev[l];
         int n = lv.A.n;
         if (l > 0)
-            WITH_COLS_M(lv.S, (k_down_m<T, IDX, K, kUnroll, false><<<grid_of((int64_t)n * K), kMB, 0, s>>>(
+            WITH_COLS_M(lv.S, (k_down_m<T, IDX, K, kUnroll, false><<<gv(n), kMB, 0, s>>>(
                                   n, lv.S.sptr, cols, P::val(lv), P::xpre(mv), P::b(mv), P::p(lv), P::t(mv), ctl)));
         if (l + 1 == L)
-            k_restrict_m<T, double, false, K><<<grid_of((int64_t)lv.nc * K), kMB, 0, s>>>(
+            k_restrict_m<T, double, false, K><<<gv(lv.nc), kMB, 0, s>>>(
                 lv.nc, lv.rptr, lv.ridx, P::t(mv), W.bL, nullptr, nullptr, ctl);
         else
-            k_restrict_m<T, T, true, K><<<grid_of((int64_t)lv.nc * K), kMB, 0, s>>>(
+            k_restrict_m<T, T, true, K><<<gv(lv.nc), kMB, 0, s>>>(
                 lv.nc, lv.rptr, lv.ridx, P::t(mv), P::b(W.lev[l + 1]), P::dinv(lev[l + 1]), P::xpre(W.lev[l + 1]),
                 ctl);
     }
-    k_coarse_m<T, K><<<grid_of((int64_t)h->nL * K), kMB, 0, s>>>(h->nL, h->Ainv, W.bL, P::x(W.lev[L]), ctl);
+    k_coarse_m<T, K><<<grid_of((int64_t)h->nL * (K / 2)), kMB, 0, s>>>(h->nL, h->Ainv, W.bL, P::x(W.lev[L]), ctl);
     for (int l = L - 1; l >= 1; l--) {
         Level &lv = lev[l];
         MultiLevel &mv = W.lev[l];
         int n = lv.A.n;
-        k_prolong_m<T, K><<<grid_of((int64_t)n * K), kMB, 0, s>>>(n, P::xpre(mv), P::p(lv), lv.agg,
+        k_prolong_m<T, K><<<gv(n), kMB, 0, s>>>(n, P::xpre(mv), P::p(lv), lv.agg,
                                                                   P::x(W.lev[l + 1]), P::xp(mv), ctl);
         WITH_COLS_M(lv.S, (k_post_m<T, T, false, false, IDX, K, kUnroll, false>
-                           <<<grid_of((int64_t)n * K), kMB, 0, s>>>(n, lv.S.sptr, cols, P::val(lv), P::xp(mv),
+                           <<<gv(n), kMB, 0, s>>>(n, lv.S.sptr, cols, P::val(lv), P::xp(mv),
                                                                     P::b(mv), P::dinv(lv), P::x(mv), nullptr,
                                                                     nullptr, nullptr, ctl)));
     }
