@@ -51,6 +51,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--multi-k", type=int, default=32, help="right-hand sides of the multi-column form (0: skip)")
     ap.add_argument("--multi-reps", type=int, default=3)
+    ap.add_argument("--batch-count", type=int, default=48, help="independent systems of the batched form (0: skip)")
     return ap.parse_args(argv)
 
 
@@ -378,6 +379,48 @@ def run_ours(args):
                            "max_true_rel": float(np.max(tr))}
         amg.set_mode("fcg32")
 
+    # batched form: independent graded systems of uneven size, one launch
+    batch = {}
+    if args.batch_count > 0:
+        sizes = W.batch_sizes(args.batch_count, 24, 112, seed=3)
+        bprobs = [W.make_problem(Nn, args.ratio, seed=3000 + k) for k, Nn in enumerate(sizes)]
+        bamgs = [B.AMG.from_csr(p.A, mode="fcg32", stream=stream) for p in bprobs]
+        bb = [torch.from_numpy(p.b).to(device) for p in bprobs]
+        bx = [torch.zeros_like(v) for v in bb]
+        bt = B.Batch(bamgs)
+        for _ in range(2):
+            for v in bx:
+                v.zero_()
+            bt.solve(bb, bx, rtol=args.rtol, maxit=args.maxit, stream=stream)
+        torch.cuda.synchronize()
+        reps = args.multi_reps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            for v in bx:
+                v.zero_()
+            st, bit, bsts = bt.solve(bb, bx, rtol=args.rtol, maxit=args.maxit, stream=stream)
+            if st != 0:
+                raise RuntimeError(f"batch solve failed: {bsts}")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_batch = e0.elapsed_time(e1) / reps
+        # the same systems one after another (each its own whole-solve graph)
+        e0.record(stream)
+        for k in range(len(bamgs)):
+            bx[k].zero_()
+            bamgs[k].solve(bb[k], bx[k], rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_seq = e0.elapsed_time(e1)
+        batch = {"systems": len(sizes), "dofs": int(sum(Nn ** 3 for Nn in sizes)), "mode": "fcg32",
+                 "ms_per_batch": ms_batch, "solves_per_s": len(sizes) / (ms_batch / 1e3),
+                 "sequential_ms": ms_seq, "sequential_solves_per_s": len(sizes) / (ms_seq / 1e3),
+                 "max_iters": int(bit.max())}
+        bt.close()
+        for a in bamgs:
+            a.close()
+
     # end to end through the C ABI with host buffers (pinned), copies inside the call
     pin_b = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
     pin_x = torch.zeros(prob.A.n, dtype=torch.float64).pin_memory().numpy()
@@ -471,6 +514,7 @@ def run_ours(args):
             "latency_ms": {"p50": pct(m["lat_ms"], 50), "p99": pct(m["lat_ms"], 99)},
             "true_rel": m["true_rel"],
             "multi_rhs": multi,
+            "batch": batch,
             "fp64": {"value": solves / (f64_ms / 1e3), "unit": UNIT, "ms_per_step": f64_ms / args.steps,
                      "latency_ms": {"p50": pct(f64["lat_ms"], 50), "p99": pct(f64["lat_ms"], 99)},
                      "iters": statistics.median(f64["iters"]), "gpu_launches": f64["launches"]},

@@ -140,6 +140,22 @@ int pcg_solve_multi(amg_handle h, int k, const double *B, double *X, double rtol
  * (host) or NULL. */
 int amg_multi_info(amg_handle h, int *k, int *status, double *true_rel);
 
+/* Batched solve of independent systems, each with its own hierarchy (own
+ * handle; handles may differ in size and mode). amg_batch_create fixes the
+ * list of handles; pcg_solve_batch then solves system i: A_i x_i = B[i]
+ * (x_i: initial guess in X[i], solution on exit) for all i in one CUDA-graph
+ * launch whose branches run concurrently on the GPU, each with its own
+ * device-side iteration loop. Each system's result equals that handle's own
+ * pcg_solve bit for bit. B[i], X[i]: host or device, n_i values each.
+ * iters, status: m values each (host, may be NULL). Returns AMG_OK when all
+ * systems converged, else the first failing status. A handle must not be
+ * destroyed while a batch holding it exists, nor used by two calls at once. */
+typedef struct amg_batch_s *amg_batch;
+int amg_batch_create(int m, const amg_handle *hs, amg_batch *out);
+int pcg_solve_batch(amg_batch b, const double *const *B, double *const *X, double rtol, int maxit, int *iters,
+                    int *status, void *stream);
+void amg_batch_destroy(amg_batch b);
+
 /* True relative residual ||b - A x|| / ||b|| at the end of the last solve on h. */
 double amg_last_true_residual(amg_handle h);
 

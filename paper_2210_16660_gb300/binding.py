@@ -24,7 +24,8 @@ _MODES = {"pcg64": MODE_PCG64, "fcg32": MODE_FCG32}
 EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode", "pcg_solve",
            "amg_last_true_residual", "amg_info", "amg_level_agg", "amg_level_csr", "amg_setup_times",
            "amg_destroy", "amg_last_error", "amg_profile", "amg_profile_read", "amg_launch_count",
-           "amg_level_layout", "amg_residual_noalloc", "pcg_solve_multi", "amg_multi_info")
+           "amg_level_layout", "amg_residual_noalloc", "pcg_solve_multi", "amg_multi_info",
+           "amg_batch_create", "pcg_solve_batch", "amg_batch_destroy")
 
 
 class AmgCsr(C.Structure):
@@ -89,6 +90,12 @@ def load(build_if_missing: bool = True):
     lib.pcg_solve_multi.restype = I
     lib.amg_multi_info.argtypes = [P, C.POINTER(I), P, P]
     lib.amg_multi_info.restype = I
+    lib.amg_batch_create.argtypes = [I, P, C.POINTER(P)]
+    lib.amg_batch_create.restype = I
+    lib.pcg_solve_batch.argtypes = [P, P, P, D, I, P, P, P]
+    lib.pcg_solve_batch.restype = I
+    lib.amg_batch_destroy.argtypes = [P]
+    lib.amg_batch_destroy.restype = None
     lib.amg_destroy.argtypes = [P]
     lib.amg_destroy.restype = None
     lib.amg_last_error.argtypes = []
@@ -328,3 +335,39 @@ class AMG:
         ms = np.zeros(4)
         load().amg_setup_times(self._h, ms.ctypes.data)
         return {"total_ms": ms[0], "matching_ms": ms[1], "galerkin_ms": ms[2], "other_ms": ms[3]}
+
+
+class Batch:
+    """``amg_batch_create`` / ``pcg_solve_batch``: independent systems in one launch."""
+
+    def __init__(self, amgs):
+        lib = load()
+        self.amgs = list(amgs)           # keeps the handles alive
+        arr = (C.c_void_p * len(self.amgs))(*[a._h.value for a in self.amgs])
+        b = C.c_void_p()
+        st = lib.amg_batch_create(len(self.amgs), arr, C.byref(b))
+        if st:
+            raise AmgError(st, last_error())
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().amg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, bs, xs, rtol: float = 1e-8, maxit: int = 1000, stream=None):
+        """Solve every system; xs updated in place. Returns (status, iters[m], statuses[m])."""
+        m = len(self.amgs)
+        bp = (C.c_void_p * m)(*[_ptr(b, np.float64)[0] for b in bs])
+        xp = (C.c_void_p * m)(*[_ptr(x, np.float64)[0] for x in xs])
+        it = np.zeros(m, np.int32)
+        sts = np.zeros(m, np.int32)
+        st = load().pcg_solve_batch(self._b, bp, xp, rtol, maxit, it.ctypes.data, sts.ctypes.data,
+                                    _stream_ptr(stream))
+        return st, it, sts

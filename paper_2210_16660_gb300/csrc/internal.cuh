@@ -160,6 +160,14 @@ struct MultiWS {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
 };
 
+// A whole-solve while node whose body is captured after the outer capture.
+struct PendingBody {
+    struct ::amg_hier *h = nullptr;
+    int mode = 0;
+    cudaGraph_t body = nullptr;
+    cudaGraphConditionalHandle hc = 0;
+};
+
 }  // namespace pcgamg
 
 struct amg_hier {
@@ -200,6 +208,7 @@ struct amg_hier {
     int graph_body_kernels[2] = {0, 0};
     int use_graph = 1;
     int no_col16 = 0;
+    int graph_gen = 0;       // bumped whenever captured graphs go stale
     // fused tail: levels tail_first..L run in one cooperative kernel
     int tail_first = 0;      // 0 = no tail (every level launched separately)
     int tail_grid = 0;
@@ -223,4 +232,7 @@ void free_profile(amg_hier *h);
 int solve_multi_impl(amg_hier *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
                      double *res_hist, cudaStream_t s);
 void free_multi(amg_hier *h);
+int capture_solve_prefix(amg_hier *h, int mode, cudaStream_t cs, PendingBody *pb, int *prefix_k);
+int capture_solve_body(const PendingBody &pb, cudaStream_t s, int *body_k);
+int ensure_hist(amg_hier *h, int maxit);
 }  // namespace pcgamg

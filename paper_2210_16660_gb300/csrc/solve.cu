@@ -769,15 +769,16 @@ int launch_prefix(amg_hier *h, cudaStream_t s) {
     return AMG_OK;
 }
 
-// Whole solve as one graph: prefix (zero p/q, first residual, condition),
-// then a while node whose body is two iterations plus the condition kernel.
-int build_graph(amg_hier *h, int mode) {
-    if (!h->cap_stream) PCG_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    cudaStream_t cs = h->cap_stream;
+}  // namespace
+
+// Captures the prefix of one whole solve of h in `mode` onto cs, which must
+// be capturing (possibly as a forked branch of a larger capture): zero p/q,
+// first residual, the loop-condition kernel, and a while node whose body is
+// filled later by capture_solve_body. Kernel counts go to *prefix_k.
+int capture_solve_prefix(amg_hier *h, int mode, cudaStream_t cs, PendingBody *pb, int *prefix_k) {
     int saved_mode = h->mode;
     h->mode = mode;
     int64_t l0 = h->launches;
-    PCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int st = launch_prefix(h, cs);
     cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle hc = 0;
@@ -803,33 +804,61 @@ int build_graph(amg_hier *h, int mode) {
     }
     if (!st && e == cudaSuccess)
         e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-    cudaGraph_t full = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &full);
-    int prefix = (int)(h->launches - l0) + 1;
-    if (st || e != cudaSuccess || e2 != cudaSuccess) {
-        if (full) cudaGraphDestroy(full);
-        h->mode = saved_mode;
-        h->launches = l0;
-        if (!st) st = cuda_fail(e != cudaSuccess ? e : e2, "solve graph capture", __FILE__, __LINE__);
-        return st;
-    }
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    int64_t l1 = h->launches;
-    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        st = launch_iteration(h, cs);
-        if (!st) st = launch_iteration(h, cs);
-        if (!st) k_set_cond<<<1, 32, 0, cs>>>(hc, h->ctl, 1);
-        cudaGraph_t bout = body;
-        e = cudaStreamEndCapture(cs, &bout);
-        if (e == cudaSuccess) e = cudaGetLastError();
-    }
-    int body_k = (int)(h->launches - l1) + 1;
+    *prefix_k = (int)(h->launches - l0) + 1;
     h->launches = l0;
     h->mode = saved_mode;
-    if (st || e != cudaSuccess) {
-        cudaGraphDestroy(full);
-        if (!st) st = cuda_fail(e, "solve graph body capture", __FILE__, __LINE__);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "solve graph capture", __FILE__, __LINE__);
+    pb->h = h;
+    pb->mode = mode;
+    pb->body = cp.conditional.phGraph_out[0];
+    pb->hc = hc;
+    return AMG_OK;
+}
+
+// Fills the while node's body: two iterations and the condition kernel,
+// captured on s (not capturing). Kernel count of one body to *body_k.
+int capture_solve_body(const PendingBody &pb, cudaStream_t s, int *body_k) {
+    amg_hier *h = pb.h;
+    int saved_mode = h->mode;
+    h->mode = pb.mode;
+    int64_t l1 = h->launches;
+    int st = AMG_OK;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(s, pb.body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = launch_iteration(h, s);
+        if (!st) st = launch_iteration(h, s);
+        if (!st) k_set_cond<<<1, 32, 0, s>>>(pb.hc, h->ctl, 1);
+        cudaGraph_t bout = pb.body;
+        cudaError_t e2 = cudaStreamEndCapture(s, &bout);
+        if (e2 != cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    *body_k = (int)(h->launches - l1) + 1;
+    h->launches = l1;
+    h->mode = saved_mode;
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "solve graph body capture", __FILE__, __LINE__);
+    return AMG_OK;
+}
+
+namespace {
+
+// Whole solve as one graph: prefix (zero p/q, first residual, condition),
+// then a while node whose body is two iterations plus the condition kernel.
+int build_graph(amg_hier *h, int mode) {
+    if (!h->cap_stream) PCG_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = h->cap_stream;
+    PendingBody pb;
+    int prefix = 0, body_k = 0;
+    PCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int st = capture_solve_prefix(h, mode, cs, &pb, &prefix);
+    cudaGraph_t full = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &full);
+    if (!st && e != cudaSuccess) st = cuda_fail(e, "solve graph capture", __FILE__, __LINE__);
+    if (!st) st = capture_solve_body(pb, cs, &body_k);
+    if (st) {
+        if (full) cudaGraphDestroy(full);
         return st;
     }
     e = cudaGraphInstantiate(&h->gexec[mode], full, 0);
@@ -973,6 +1002,20 @@ int alloc_solve_workspace(amg_hier *h) {
     return AMG_OK;
 }
 
+// Makes room for maxit+1 history values (invalidates captured graphs).
+int ensure_hist(amg_hier *h, int maxit) {
+    if (maxit + 1 <= h->hist_cap) return AMG_OK;
+    release(h->mem, h->hist);
+    h->hist_cap = maxit + 1;
+    PCG_TRY(alloc(h->mem, &h->hist, h->hist_cap));
+    for (auto &g : h->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    h->graph_gen++;
+    return AMG_OK;
+}
+
 int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, int *iters, double *res_hist,
                cudaStream_t s) {
     if (!b || !x || !(rtol >= 0.0) || maxit < 0) {
@@ -990,6 +1033,7 @@ int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, 
             if (g) cudaGraphExecDestroy(g);
             g = nullptr;
         }
+        h->graph_gen++;
     }
     bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
     PCG_CK(cudaMemcpyAsync(h->b, b, sizeof(double) * n, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
