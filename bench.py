@@ -18,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -52,6 +53,12 @@ def parse_args(argv=None):
     ap.add_argument("--multi-k", type=int, default=32, help="right-hand sides of the multi-column form (0: skip)")
     ap.add_argument("--multi-reps", type=int, default=3)
     ap.add_argument("--batch-count", type=int, default=48, help="independent systems of the batched form (0: skip)")
+    ap.add_argument("--serve-count", type=int, default=160,
+                    help="requests per serving run over resident 64^3/128^3/192^3 meshes (0: skip)")
+    ap.add_argument("--serve-sizes", type=int, nargs="+", default=[64, 128, 192])
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-engines", type=int, default=2)
+    ap.add_argument("--serve-chunk", type=int, default=4)
     return ap.parse_args(argv)
 
 
@@ -178,25 +185,35 @@ def algorithmic_bytes(kind: str, mode: str, n0: int, nnz0: int, n1: int, ib: int
     raise KeyError(kind)
 
 
-def source_sha() -> str:
-    h = hashlib.sha256()
-    for f in ("solve.cu", "internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2210_16660_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+def kernel_source(kernel: str) -> str:
+    """Text of a kernel's definition in solve.cu (template line to closing brace)."""
+    src = open(os.path.join(ROOT, "paper_2210_16660_gb300", "csrc", "solve.cu")).read()
+    m = re.search(r"(^template <[^\n]*\n)?^__global__[^\n]*?\b" + re.escape(kernel) + r"\(", src, flags=re.M)
+    if not m:
+        return ""
+    end = src.find("\n}\n", m.start())
+    return src[m.start(): end + 3]
+
+
+def kernel_sha(kernel: str) -> str:
+    """Hash of what decides a kernel's memory traffic: its own source and the
+    sliced-ELL row helper it inlines."""
+    h = hashlib.sha256(kernel_source(kernel).encode())
+    with open(os.path.join(ROOT, "paper_2210_16660_gb300", "csrc", "sell_row.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def committed_traffic(kernel: str, mode: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is still the one the counters were taken on."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         data = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if data.get("source_sha") != source_sha():
-        return None
     ent = data.get("kernels", {}).get(f"{kernel}:{mode}")
-    if not ent:
+    if not ent or ent.get("kernel_sha") != kernel_sha(kernel):
         return None
     return ent.get("dram_bytes_per_launch_full_size")
 
@@ -421,6 +438,27 @@ def run_ours(args):
         for a in bamgs:
             a.close()
 
+    # serving: Poisson streams of warm-started solves over resident meshes,
+    # continuous batching; saturated throughput, then p50/p99 at 70% of it
+    serving = {}
+    if args.serve_count > 0:
+        from paper_2210_16660_gb300 import serving as SV
+        meshes = SV.prepare_meshes(tuple(args.serve_sizes), ratio=args.ratio, seed=5, pool=4, device=device)
+        kw = dict(slots=args.serve_slots, max_engines=args.serve_engines, chunk=args.serve_chunk,
+                  rtol=args.rtol, maxit=args.maxit)
+        srv = SV.make_server(meshes, "fcg32", **kw)
+        plan = [dict(zip(("engines", "slots", "engine_bytes", "resident_bytes"), srv.mesh_info(i)))
+                for i in range(len(meshes))]
+        srv.close()
+        res = SV.serve_modes(meshes, args.serve_count, load_fraction=0.7, seed=5, **kw)
+        serving = {"meshes": [{"name": mm.name, "n": mm.problem.A.n, **pl} for mm, pl in zip(meshes, plan)],
+                   "requests_per_run": args.serve_count, "arrivals": "Poisson, mesh uniform, seed 5",
+                   "warm_start": "x0 = previous step's x*, x*_t = x*_{t-1} + 0.01 rms(x*_{t-1}) xi_t",
+                   "mixed": res["fcg32"], "fp64": res["pcg64"]}
+        for mm in meshes:
+            mm.amg.close()
+        del meshes
+
     # end to end through the C ABI with host buffers (pinned), copies inside the call
     pin_b = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
     pin_x = torch.zeros(prob.A.n, dtype=torch.float64).pin_memory().numpy()
@@ -515,6 +553,7 @@ def run_ours(args):
             "true_rel": m["true_rel"],
             "multi_rhs": multi,
             "batch": batch,
+            "serving": serving,
             "fp64": {"value": solves / (f64_ms / 1e3), "unit": UNIT, "ms_per_step": f64_ms / args.steps,
                      "latency_ms": {"p50": pct(f64["lat_ms"], 50), "p99": pct(f64["lat_ms"], 99)},
                      "iters": statistics.median(f64["iters"]), "gpu_launches": f64["launches"]},

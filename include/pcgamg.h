@@ -51,6 +51,7 @@ extern "C" {
 #define AMG_ERR_CUDA 6      /* a CUDA runtime call failed */
 #define AMG_ERR_TIMEOUT 7   /* a bounded device-side wait expired */
 #define AMG_ERR_COARSE 8    /* coarsening stalled with more than 4096 rows left */
+#define AMG_ERR_BUSY 9      /* serving: the request queue is full */
 
 /* Precision of the V-cycle (Sec. 5 uses flexible CG around the preconditioner). */
 #define AMG_MODE_PCG64 0    /* float64 V-cycle, plain PCG */
@@ -155,6 +156,109 @@ int amg_batch_create(int m, const amg_handle *hs, amg_batch *out);
 int pcg_solve_batch(amg_batch b, const double *const *B, double *const *X, double rtol, int maxit, int *iters,
                     int *status, void *stream);
 void amg_batch_destroy(amg_batch b);
+
+/* ---------------------------------------------------------------------------
+ * Serving: pressure solves of many time steps over meshes whose hierarchies
+ * stay resident on the device. The paper builds the hierarchy of a fixed
+ * mesh once and reuses it for every time step's solve (Sec. 1, Sec. 4), each
+ * solve starting from the previous step's pressure (Sec. 5); it has no
+ * serving layer of its own, this is the way to run many such solves at once
+ * on one GPU.
+ *
+ * A request is (mesh, b, x0): solve A_mesh x = b from x0 to
+ * ||b - A x|| / ||b|| <= rtol with the server's mode. Every mesh gets engines
+ * of `slots` right-hand-side slots (the kernels of pcg_solve_multi). A
+ * request takes a free slot of its mesh; between chunks of `chunk`
+ * iterations the host hands finished requests back and starts queued ones in
+ * the freed slots, while the other slots carry on where they were
+ * (continuous batching). Engines run on their own streams and overlap on the
+ * device. A request's result depends only on its own (mesh, b, x0) and the
+ * server parameters, not on what else is running: for a given `slots` it is
+ * the same bit for bit alone or in any mix, and it equals column c of
+ * pcg_solve_multi with the same K in the same mode.
+ *
+ * Memory: the resident hierarchies (all device bytes each handle holds) plus
+ * every engine fit in hbm_budget bytes (0: the hierarchies' bytes plus the
+ * free device memory less 1 GiB). amg_serve_plan decides the engines per
+ * mesh; a mesh whose hierarchy and one engine do not fit gets no engine and
+ * its requests are refused with AMG_ERR_OOM.
+ *
+ * The server is driven by one host thread (submit / progress / result); a
+ * mesh's handle must stay alive and must not be used by other calls while
+ * the server exists.
+ * ------------------------------------------------------------------------- */
+typedef struct amg_server_s *amg_server;
+
+typedef struct {
+    int mode;          /* AMG_MODE_FCG32 or AMG_MODE_PCG64, for every request */
+    int slots;         /* right-hand sides per engine: 4, 8, 16 or 32 */
+    int max_engines;   /* engines per mesh, at most (>= 1) */
+    int chunk;         /* iterations per device step between host visits (>= 1) */
+    int queue_cap;     /* requests waiting for a slot, at most (>= 0) */
+    int maxit;         /* iterations per request, at most */
+    double rtol;       /* relative residual target per request */
+    size_t hbm_budget; /* device bytes for hierarchies plus engines; 0: see above */
+} amg_server_params;
+
+/* FCG32, 8 slots, 2 engines per mesh, chunk 4, queue 4096, maxit 1000,
+ * rtol 1e-8, budget 0. */
+void amg_server_default_params(amg_server_params *p);
+
+/* Engine plan (host only, no device call). Mesh i needs resident[i] bytes for
+ * its hierarchy and engine_bytes[i] per engine. In mesh order, a mesh is
+ * admitted with one engine if its hierarchy and one engine fit in what is
+ * left of budget; then engines are added one at a time to the admitted mesh
+ * with the largest load[i] / engines[i] (ties: lowest i; load NULL: all 1)
+ * that still fits and has fewer than max_engines. engines: m values out
+ * (0 = not admitted); *total (may be NULL): bytes planned. Returns AMG_OK if
+ * at least one mesh was admitted, AMG_ERR_OOM if none, AMG_ERR_ARG on bad
+ * arguments. */
+int amg_serve_plan(int m, const size_t *resident, const size_t *engine_bytes, const double *load, size_t budget,
+                   int max_engines, int *engines, size_t *total);
+
+/* Creates a server over m resident hierarchies (distinct handles with at
+ * least two levels). load: m relative request loads for the plan (NULL: all
+ * equal). Allocates every engine up front. Errors: AMG_ERR_ARG, AMG_ERR_OOM
+ * (nothing fits, or an allocation failed), AMG_ERR_CUDA. */
+int amg_server_create(const amg_server_params *p, int m, const amg_handle *meshes, const double *load,
+                      amg_server *out);
+
+/* Plan of one mesh: engines, slots per engine, bytes per engine, resident
+ * hierarchy bytes (each pointer may be NULL). */
+int amg_server_mesh_info(amg_server s, int mesh, int *engines, int *slots, size_t *engine_bytes,
+                         size_t *resident_bytes);
+
+/* Budget in use and state: budget, planned bytes, requests waiting, requests
+ * in slots, kernels launched so far (each may be NULL). */
+int amg_server_info(amg_server s, size_t *budget, size_t *used, int *queued, int *running, int64_t *launches);
+
+/* Queues a request. b, x0 (n values, host or device) must stay valid until
+ * the request has started (its first progress call that admits it); x (n
+ * values, host or device) receives the solution when it finishes and must
+ * stay valid until then. *ticket names it in amg_server_result. Errors:
+ * AMG_ERR_ARG, AMG_ERR_OOM (mesh not admitted), AMG_ERR_BUSY (queue full;
+ * nothing queued). */
+int amg_server_submit(amg_server s, int mesh, const double *b, const double *x0, double *x, int64_t *ticket);
+
+/* One visit of every engine: engines whose chunk has finished hand back their
+ * finished requests (x written, result recorded), then every idle engine
+ * starts queued requests in its free slots and launches its next chunk if a
+ * slot is in use. wait != 0: first wait until some running chunk finishes
+ * (returns at once if none is running). *finished (may be NULL): requests
+ * finished by this call. */
+int amg_server_progress(amg_server s, int wait, int *finished);
+
+/* Outcome of a request. *done = 0 while it is queued or running; once it is
+ * 1 the record is released and the ticket is no longer known. status: the
+ * request's AMG_* code (AMG_ERR_NOCONV with x = last iterate, as pcg_solve);
+ * iters; true_rel = ||b - A x|| / ||b||; times (3 doubles, may be NULL):
+ * ms waiting in the queue, ms in a slot, ms from submit to finish. Returns
+ * AMG_ERR_ARG for an unknown ticket. */
+int amg_server_result(amg_server s, int64_t ticket, int *done, int *status, int *iters, double *true_rel,
+                      double *times);
+
+/* Waits for running chunks and frees every engine (not the hierarchies). */
+void amg_server_destroy(amg_server s);
 
 /* True relative residual ||b - A x|| / ||b|| at the end of the last solve on h. */
 double amg_last_true_residual(amg_handle h);

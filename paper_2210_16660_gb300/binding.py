@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_NAN, ERR_CUDA, ERR_TIMEOUT, ERR_COARSE = range(9)
+OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_NAN, ERR_CUDA, ERR_TIMEOUT, ERR_COARSE, ERR_BUSY = range(10)
 MODE_PCG64, MODE_FCG32 = 0, 1
 _MODES = {"pcg64": MODE_PCG64, "fcg32": MODE_FCG32}
 
@@ -25,7 +25,9 @@ EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode
            "amg_last_true_residual", "amg_info", "amg_level_agg", "amg_level_csr", "amg_setup_times",
            "amg_destroy", "amg_last_error", "amg_profile", "amg_profile_read", "amg_launch_count",
            "amg_level_layout", "amg_residual_noalloc", "pcg_solve_multi", "amg_multi_info",
-           "amg_batch_create", "pcg_solve_batch", "amg_batch_destroy")
+           "amg_batch_create", "pcg_solve_batch", "amg_batch_destroy", "amg_server_default_params",
+           "amg_serve_plan", "amg_server_create", "amg_server_mesh_info", "amg_server_info", "amg_server_submit",
+           "amg_server_progress", "amg_server_result", "amg_server_destroy")
 
 
 class AmgCsr(C.Structure):
@@ -36,6 +38,11 @@ class AmgCsr(C.Structure):
 class AmgParams(C.Structure):
     _fields_ = [("coarse_max", C.c_int), ("n_pass", C.c_int), ("max_levels", C.c_int), ("mode", C.c_int),
                 ("hbm_budget", C.c_size_t)]
+
+
+class ServerParams(C.Structure):
+    _fields_ = [("mode", C.c_int), ("slots", C.c_int), ("max_engines", C.c_int), ("chunk", C.c_int),
+                ("queue_cap", C.c_int), ("maxit", C.c_int), ("rtol", C.c_double), ("hbm_budget", C.c_size_t)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -96,6 +103,25 @@ def load(build_if_missing: bool = True):
     lib.pcg_solve_batch.restype = I
     lib.amg_batch_destroy.argtypes = [P]
     lib.amg_batch_destroy.restype = None
+    SZ, I64 = C.c_size_t, C.c_int64
+    lib.amg_server_default_params.argtypes = [C.POINTER(ServerParams)]
+    lib.amg_server_default_params.restype = None
+    lib.amg_serve_plan.argtypes = [I, P, P, P, SZ, I, P, C.POINTER(SZ)]
+    lib.amg_serve_plan.restype = I
+    lib.amg_server_create.argtypes = [C.POINTER(ServerParams), I, P, P, C.POINTER(P)]
+    lib.amg_server_create.restype = I
+    lib.amg_server_mesh_info.argtypes = [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(SZ), C.POINTER(SZ)]
+    lib.amg_server_mesh_info.restype = I
+    lib.amg_server_info.argtypes = [P, C.POINTER(SZ), C.POINTER(SZ), C.POINTER(I), C.POINTER(I), C.POINTER(I64)]
+    lib.amg_server_info.restype = I
+    lib.amg_server_submit.argtypes = [P, I, P, P, P, C.POINTER(I64)]
+    lib.amg_server_submit.restype = I
+    lib.amg_server_progress.argtypes = [P, I, C.POINTER(I)]
+    lib.amg_server_progress.restype = I
+    lib.amg_server_result.argtypes = [P, I64, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(D), P]
+    lib.amg_server_result.restype = I
+    lib.amg_server_destroy.argtypes = [P]
+    lib.amg_server_destroy.restype = None
     lib.amg_destroy.argtypes = [P]
     lib.amg_destroy.restype = None
     lib.amg_last_error.argtypes = []
@@ -371,3 +397,133 @@ class Batch:
         st = load().pcg_solve_batch(self._b, bp, xp, rtol, maxit, it.ctypes.data, sts.ctypes.data,
                                     _stream_ptr(stream))
         return st, it, sts
+
+
+def serve_plan(resident, engine_bytes, budget: int, max_engines: int, loads=None):
+    """``amg_serve_plan`` (host only): engines per mesh under a byte budget.
+
+    Returns (status, engines[m], planned bytes)."""
+    m = len(resident)
+    res = np.ascontiguousarray(resident, dtype=np.uint64)
+    eb = np.ascontiguousarray(engine_bytes, dtype=np.uint64)
+    ld = None if loads is None else np.ascontiguousarray(loads, dtype=np.float64)
+    eng = np.zeros(m, np.int32)
+    tot = C.c_size_t(0)
+    st = load().amg_serve_plan(m, res.ctypes.data, eb.ctypes.data, None if ld is None else ld.ctypes.data,
+                               int(budget), int(max_engines), eng.ctypes.data, C.byref(tot))
+    return st, eng, int(tot.value)
+
+
+@dataclasses.dataclass
+class ServeResult:
+    status: int
+    iters: int
+    true_rel: float
+    queue_ms: float
+    run_ms: float
+    total_ms: float
+
+
+class Server:
+    """``amg_server_*``: continuous-batching request loop over resident hierarchies.
+
+    ``submit`` queues (mesh, b, x0, x) and returns a ticket; ``progress`` visits
+    the engines; ``result`` returns a ServeResult once the request finished
+    (None before). Buffers passed to ``submit`` are kept referenced here until
+    the request's result has been read."""
+
+    def __init__(self, amgs, mode: str = "fcg32", slots: int = 8, max_engines: int = 2, chunk: int = 4,
+                 queue_cap: int = 4096, rtol: float = 1e-8, maxit: int = 1000, hbm_budget: int = 0, loads=None):
+        lib = load()
+        self.amgs = list(amgs)
+        p = ServerParams()
+        lib.amg_server_default_params(C.byref(p))
+        p.mode = _MODES[mode] if isinstance(mode, str) else int(mode)
+        p.slots, p.max_engines, p.chunk, p.queue_cap = slots, max_engines, chunk, queue_cap
+        p.rtol, p.maxit, p.hbm_budget = rtol, maxit, int(hbm_budget)
+        arr = (C.c_void_p * len(self.amgs))(*[a._h.value for a in self.amgs])
+        ld = None if loads is None else np.ascontiguousarray(loads, dtype=np.float64)
+        srv = C.c_void_p()
+        st = lib.amg_server_create(C.byref(p), len(self.amgs), arr, None if ld is None else ld.ctypes.data,
+                                   C.byref(srv))
+        if st:
+            raise AmgError(st, last_error())
+        self._s = srv
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            load().amg_server_destroy(self._s)
+            self._s = None
+            self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def mesh_info(self, mesh: int):
+        """(engines, slots, engine bytes, resident bytes) of one mesh."""
+        e, k = C.c_int(), C.c_int()
+        eb, rb = C.c_size_t(), C.c_size_t()
+        st = load().amg_server_mesh_info(self._s, mesh, C.byref(e), C.byref(k), C.byref(eb), C.byref(rb))
+        if st:
+            raise AmgError(st, last_error())
+        return e.value, k.value, eb.value, rb.value
+
+    def info(self):
+        """dict: budget, used (planned bytes), queued, running, launches."""
+        b, u = C.c_size_t(), C.c_size_t()
+        q, r = C.c_int(), C.c_int()
+        n = C.c_int64()
+        st = load().amg_server_info(self._s, C.byref(b), C.byref(u), C.byref(q), C.byref(r), C.byref(n))
+        if st:
+            raise AmgError(st, last_error())
+        return {"budget": b.value, "used": u.value, "queued": q.value, "running": r.value, "launches": n.value}
+
+    def submit(self, mesh: int, b, x0, x):
+        """Queue a request; returns (status, ticket)."""
+        t = C.c_int64(0)
+        st = load().amg_server_submit(self._s, mesh, _ptr(b, np.float64)[0], _ptr(x0, np.float64)[0],
+                                          _ptr(x, np.float64)[0], C.byref(t))
+        if st == OK:
+            self._keep[t.value] = (b, x0, x)
+        return st, t.value
+
+    def progress(self, wait: bool = False) -> int:
+        """One visit of every engine; returns the number of requests finished."""
+        f = C.c_int(0)
+        st = load().amg_server_progress(self._s, int(bool(wait)), C.byref(f))
+        if st:
+            raise AmgError(st, last_error())
+        return f.value
+
+    def result(self, ticket: int):
+        done, sts, it = C.c_int(), C.c_int(), C.c_int()
+        tr = C.c_double()
+        tm = np.zeros(3)
+        st = load().amg_server_result(self._s, ticket, C.byref(done), C.byref(sts), C.byref(it), C.byref(tr),
+                                          tm.ctypes.data)
+        if st:
+            raise AmgError(st, last_error())
+        if not done.value:
+            return None
+        self._keep.pop(ticket, None)
+        return ServeResult(sts.value, it.value, tr.value, float(tm[0]), float(tm[1]), float(tm[2]))
+
+    def drain(self, tickets):
+        """Run until every ticket has finished; returns {ticket: ServeResult}."""
+        out = {}
+        pending = list(tickets)
+        while pending:
+            self.progress(wait=True)
+            rest = []
+            for t in pending:
+                r = self.result(t)
+                if r is None:
+                    rest.append(t)
+                else:
+                    out[t] = r
+            pending = rest
+        return out

@@ -35,6 +35,13 @@ int Mem::alloc_bytes(void **p, size_t n) {
         set_error("device memory budget exceeded (%zu + %zu > %zu bytes)", bytes, n, budget);
         return AMG_ERR_OOM;
     }
+    if (dry) {
+        // Counting only: a distinct, never dereferenced address per call.
+        bytes += n;
+        if (bytes > peak) peak = bytes;
+        *p = reinterpret_cast<void *>(bytes);
+        return AMG_OK;
+    }
     void *q = nullptr;
     if (g_alloc) {
         q = g_alloc(n, (void *)stream, g_alloc_ctx);

@@ -40,6 +40,7 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 struct Mem {
     cudaStream_t stream = nullptr;
     size_t bytes = 0, peak = 0, budget = 0;
+    bool dry = false;  // count requests (rounded as real ones) without allocating
     std::unordered_map<void *, size_t> live;
     int alloc_bytes(void **p, size_t bytes);
     void release(void *p);
@@ -137,6 +138,7 @@ struct CtlM {
     double bnorm[32], rho[32], rho_old[32], pq[32], pq_old[32], alpha[32], beta[32], rel[32], true_rel[32];
     double rtol;
     int iter[32], active[32], restart[32], check[32], status[32];
+    int pending[32];     // column awaits its first residual (new right-hand side)
     int k, K, maxit, mode, iter_all, any_check, done, bodies;
     unsigned int counter[8];
 };
@@ -158,6 +160,9 @@ struct MultiWS {
     CtlM *ctl_host = nullptr;
     double *hist = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraph_t step_graph = nullptr;     // fixed chunk of iterations (serving)
+    cudaGraphExec_t step_exec = nullptr;
+    int step_iters = 0, step_mode = -1;
 };
 
 // A whole-solve while node whose body is captured after the outer capture.
@@ -232,6 +237,13 @@ void free_profile(amg_hier *h);
 int solve_multi_impl(amg_hier *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
                      double *res_hist, cudaStream_t s);
 void free_multi(amg_hier *h);
+int mws_alloc(amg_hier *h, Mem &M, MultiWS &W, int K, int hist_cap, int which);
+void mws_free(Mem &M, MultiWS &W);
+size_t mws_bytes(amg_hier *h, int K, int hist_cap, int which);
+int mws_reset(MultiWS &W, int mode, double rtol, int maxit, cudaStream_t s);
+int mws_put_column(MultiWS &W, int c, const double *b_dev, const double *x_dev, int n, cudaStream_t s);
+int mws_admit(amg_hier *h, MultiWS &W, int mode, unsigned mask, cudaStream_t s);
+int mws_iterate(amg_hier *h, MultiWS &W, int mode, int iterations, cudaStream_t s, int launch);
 int capture_solve_prefix(amg_hier *h, int mode, cudaStream_t cs, PendingBody *pb, int *prefix_k);
 int capture_solve_body(const PendingBody &pb, cudaStream_t s, int *body_k);
 int ensure_hist(amg_hier *h, int maxit);

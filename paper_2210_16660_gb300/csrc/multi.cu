@@ -113,6 +113,23 @@ __device__ __forceinline__ void sell_row_vec(const IDX *__restrict__ c, const T 
     int c0 = (int)(g_ % (K / (V))) * (V);                                                     \
     int64_t e0 = (int64_t)i * K + c0;
 
+// Whether any of the V columns from c0 is still iterating.
+template <int V>
+__device__ __forceinline__ bool group_live(const CtlM *ctl, int c0) {
+    int a = 0;
+#pragma unroll
+    for (int v = 0; v < V; v++) a |= ctl->active[c0 + v];
+    return a != 0;
+}
+
+// A thread's column group is fixed over its grid-stride loop (the stride is a
+// multiple of K / V); a group whose columns have all stopped skips its rows,
+// so a block with few live columns moves only their vectors. The arithmetic
+// of a live column does not depend on which other columns are live.
+#define MK_LIVE(V)                                                                            \
+    const bool live_ = group_live<V>(                                                         \
+        ctl, (int)((((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % (K / (V))) * (V)));
+
 // Per-column block sums: a thread holds a[V] and b[V] for columns c0..c0+V-1
 // (c0 fixed per thread). Result: threads 0..K-1 hold the block's sums for
 // columns 0..K-1.
@@ -211,7 +228,8 @@ __global__ void __launch_bounds__(kMB) k_down_m(int n, const int32_t *__restrict
                                                const CtlM *__restrict__ ctl) {
     constexpr int V = VW<T>::V;
     if (ctl->done) return;
-    MK_FOR(n, V) {
+    MK_LIVE(V)
+    MK_FOR(live_ ? n : 0, V) {
         MK_IDX(V)
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
@@ -235,7 +253,8 @@ __global__ void __launch_bounds__(kMB) k_restrict_m(int nc, const int32_t *__res
                                                    T *__restrict__ xprec, const CtlM *__restrict__ ctl) {
     constexpr int V = VW<T>::V;
     if (ctl->done) return;
-    MK_FOR(nc, V) {
+    MK_LIVE(V)
+    MK_FOR(live_ ? nc : 0, V) {
         MK_IDX(V)
         T s[V];
 #pragma unroll
@@ -264,7 +283,8 @@ __global__ void __launch_bounds__(kMB) k_coarse_m(int nL, const double *__restri
                                                  const CtlM *__restrict__ ctl) {
     constexpr int V = 2;
     if (ctl->done) return;
-    MK_FOR(nL, V) {
+    MK_LIVE(V)
+    MK_FOR(live_ ? nL : 0, V) {
         MK_IDX(V)
         const double *a = ainv + (int64_t)i * nL;
         double s0 = 0.0, s1 = 0.0;
@@ -285,7 +305,8 @@ __global__ void __launch_bounds__(kMB) k_prolong_m(int n, const T *__restrict__ 
                                                   T *__restrict__ xp, const CtlM *__restrict__ ctl) {
     constexpr int V = VW<T>::V;
     if (ctl->done) return;
-    MK_FOR(n, V) {
+    MK_LIVE(V)
+    MK_FOR(live_ ? n : 0, V) {
         MK_IDX(V)
         T x[V];
         ld_vec<T, V>(xpre + e0, x);
@@ -314,7 +335,8 @@ __global__ void __launch_bounds__(kMB) k_post_m(int n, const int32_t *__restrict
     double rz[V], zq[V];
 #pragma unroll
     for (int v = 0; v < V; v++) rz[v] = zq[v] = 0.0;
-    MK_FOR(n, V) {
+    MK_LIVE(V)
+    MK_FOR(live_ ? n : 0, V) {
         MK_IDX(V)
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
@@ -366,7 +388,8 @@ __global__ void __launch_bounds__(kMB) k_axpy_m(int n, const double *__restrict_
                                                const CtlM *__restrict__ ctl) {
     constexpr int V = 2;
     if (ctl->done) return;
-    MK_FOR(n, V) {
+    MK_LIVE(V)
+    MK_FOR(live_ ? n : 0, V) {
         MK_IDX(V)
         double zv[V], pv[V], o[V];
         ld_vec<double, V>(z + e0, zv);
@@ -385,7 +408,8 @@ __global__ void __launch_bounds__(kMB) k_spmm_m(int n, const int32_t *__restrict
     constexpr int V = 2;
     if (ctl->done) return;
     double pq[V] = {0.0, 0.0}, unused[V] = {0.0, 0.0};
-    MK_FOR(n, V) {
+    MK_LIVE(V)
+    MK_FOR(live_ ? n : 0, V) {
         MK_IDX(V)
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
@@ -447,7 +471,8 @@ __global__ void __launch_bounds__(kMB) k_update_m(int n, const double *__restric
     constexpr int V = 2;
     if (ctl->done) return;
     double rr[V] = {0.0, 0.0}, unused[V] = {0.0, 0.0};
-    MK_FOR(n, V) {
+    MK_LIVE(V)
+    MK_FOR(live_ ? n : 0, V) {
         MK_IDX(V)
         double rv[V], xv[V], pv[V], qv[V];
         ld_vec_cg<double, V>(r + e0, rv);
@@ -495,8 +520,9 @@ __global__ void __launch_bounds__(kMB) k_update_m(int n, const double *__restric
     }
 }
 
-// r = b - A x. INIT: every column, plus ||b||; otherwise only the columns
-// whose recursive residual met rtol (the others keep their r).
+// r = b - A x. INIT: the columns marked pending (a new right-hand side),
+// plus ||b||; otherwise only the columns whose recursive residual met rtol.
+// The other columns keep their r.
 template <bool INIT, int MODE, typename IDX, int K>
 __global__ void __launch_bounds__(kMB) k_residual_m(int n, const int32_t *__restrict__ sptr,
                                                    const IDX *__restrict__ col, const double *__restrict__ val,
@@ -511,7 +537,8 @@ __global__ void __launch_bounds__(kMB) k_residual_m(int n, const int32_t *__rest
     double rr[V] = {0.0, 0.0}, bb[V] = {0.0, 0.0};
     MK_FOR(n, V) {
         MK_IDX(V)
-        bool use0 = INIT || ctl->check[c0], use1 = INIT || ctl->check[c0 + 1];
+        bool use0 = INIT ? ctl->pending[c0] != 0 : ctl->check[c0] != 0;
+        bool use1 = INIT ? ctl->pending[c0 + 1] != 0 : ctl->check[c0 + 1] != 0;
         if (!use0 && !use1) continue;
         int s = i >> 5, lane = i & 31;
         int32_t base = ldg(sptr + s);
@@ -530,8 +557,8 @@ __global__ void __launch_bounds__(kMB) k_residual_m(int n, const int32_t *__rest
         if (use0) rr[0] += rv[0] * rv[0];
         if (use1) rr[1] += rv[1] * rv[1];
         if (INIT) {
-            bb[0] += bv[0] * bv[0];
-            bb[1] += bv[1] * bv[1];
+            if (use0) bb[0] += bv[0] * bv[0];
+            if (use1) bb[1] += bv[1] * bv[1];
         }
     }
     __shared__ double res[2 * kMaxK];
@@ -542,10 +569,14 @@ __global__ void __launch_bounds__(kMB) k_residual_m(int n, const int32_t *__rest
             ctl->counter[3] = 0;
             for (int c = 0; c < K; c++) {
                 if (INIT) {
+                    if (!ctl->pending[c]) continue;
+                    ctl->pending[c] = 0;
                     double bn = sqrt(res[K + c]);
                     ctl->bnorm[c] = bn;
                     ctl->active[c] = 0;
                     ctl->status[c] = AMG_OK;
+                    ctl->iter[c] = 0;
+                    ctl->check[c] = 0;
                     if (c >= ctl->k) continue;
                     if (!isfinite(bn) || !isfinite(res[c])) { col_fail(ctl, c, AMG_ERR_NAN); continue; }
                     if (bn == 0.0) { ctl->true_rel[c] = 0.0; hist[(int64_t)c * hstride] = 0.0; continue; }
@@ -737,14 +768,12 @@ int launch_iteration_m(amg_hier *h, MultiWS &W, int mode, cudaStream_t s) {
     return AMG_OK;
 }
 
+// First residual, ||b|| and state of the pending columns only.
 template <int K>
-int launch_prefix_m(amg_hier *h, MultiWS &W, int mode, cudaStream_t s) {
+int launch_init_residual_m(amg_hier *h, MultiWS &W, int mode, cudaStream_t s) {
     Level &l0 = h->lev[0];
     MultiLevel &m0 = W.lev[0];
     int n = l0.A.n;
-    int64_t nk = (int64_t)n * K;
-    k_zero_m<<<grid_of(nk), kMB, 0, s>>>(W.p, nk);
-    k_zero_m<<<grid_of(nk), kMB, 0, s>>>(W.q, nk);
     int hs = W.hist_cap;
     if (mode == AMG_MODE_FCG32)
         WITH_COLS_M(l0.S, (k_residual_m<true, AMG_MODE_FCG32, IDX, K><<<W.grid, kMB, 0, s>>>(
@@ -756,6 +785,15 @@ int launch_prefix_m(amg_hier *h, MultiWS &W, int mode, cudaStream_t s) {
                               m0.xpre64, W.partials, W.ctl, W.hist, hs)));
     PCG_LAUNCH_CK();
     return AMG_OK;
+}
+
+template <int K>
+int launch_prefix_m(amg_hier *h, MultiWS &W, int mode, cudaStream_t s) {
+    int64_t nk = (int64_t)h->lev[0].A.n * K;
+    k_zero_m<<<grid_of(nk), kMB, 0, s>>>(W.p, nk);
+    k_zero_m<<<grid_of(nk), kMB, 0, s>>>(W.q, nk);
+    PCG_LAUNCH_CK();
+    return launch_init_residual_m<K>(h, W, mode, s);
 }
 
 // Whole multi-column solve as one graph (prefix, then a device-side while
@@ -834,48 +872,8 @@ bool is_dev(const void *p) {
 int ensure_ws(amg_hier *h, int K, int maxit) {
     MultiWS &W = h->multi;
     if (W.K == K && W.hist_cap >= maxit + 1) return AMG_OK;
-    free_multi(h);
-    Mem &M = h->mem;
-    int L = (int)h->lev.size() - 1;
-    int n0 = h->lev[0].A.n;
-    int64_t nk = (int64_t)n0 * K;
-    W.K = K;
-    W.hist_cap = maxit + 1 > 1001 ? maxit + 1 : 1001;
-    PCG_TRY(alloc(M, &W.b, nk));
-    PCG_TRY(alloc(M, &W.x, nk));
-    PCG_TRY(alloc(M, &W.r, nk));
-    PCG_TRY(alloc(M, &W.z, nk));
-    PCG_TRY(alloc(M, &W.p, nk));
-    PCG_TRY(alloc(M, &W.q, nk));
-    PCG_TRY(alloc(M, &W.r32, nk));
-    W.lev.assign(L + 1, MultiLevel{});
-    for (int l = 0; l <= L; l++) {
-        int64_t m = (int64_t)h->lev[l].A.n * K;
-        MultiLevel &v = W.lev[l];
-        PCG_TRY(alloc(M, &v.b32, m));
-        PCG_TRY(alloc(M, &v.x32, m));
-        PCG_TRY(alloc(M, &v.t32, m));
-        PCG_TRY(alloc(M, &v.xpre32, m));
-        PCG_TRY(alloc(M, &v.xp32, m));
-        PCG_TRY(alloc(M, &v.b64, m));
-        PCG_TRY(alloc(M, &v.x64, m));
-        PCG_TRY(alloc(M, &v.t64, m));
-        PCG_TRY(alloc(M, &v.xpre64, m));
-        PCG_TRY(alloc(M, &v.xp64, m));
-    }
-    PCG_TRY(alloc(M, &W.bL, (int64_t)h->nL * K));
-    int sms = 0;
-    PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    int64_t want = (nk + kMB - 1) / kMB;
-    int64_t cap = (int64_t)sms * 8;
-    W.grid = (int)(want < cap ? want : cap);
-    if (W.grid < 1) W.grid = 1;
-    PCG_TRY(alloc(M, &W.partials, (size_t)2 * K * W.grid));
-    PCG_TRY(alloc(M, &W.ctl, 1));
-    PCG_CK(cudaMemsetAsync(W.ctl, 0, sizeof(CtlM), M.stream));
-    PCG_CK(cudaMallocHost(&W.ctl_host, sizeof(CtlM)));
-    PCG_TRY(alloc(M, &W.hist, (size_t)K * W.hist_cap));
-    return AMG_OK;
+    mws_free(h->mem, W);
+    return mws_alloc(h, h->mem, W, K, maxit + 1 > 1001 ? maxit + 1 : 1001, 3);
 }
 
 template <int K>
@@ -911,6 +909,7 @@ int solve_multi_k(amg_hier *h, int k, const double *B, double *X, double rtol, i
     c0.mode = h->mode;
     c0.k = k;
     c0.K = K;
+    for (int q = 0; q < K; q++) c0.pending[q] = 1;
     *W.ctl_host = c0;
     PCG_CK(cudaMemcpyAsync(W.ctl, W.ctl_host, sizeof(CtlM), cudaMemcpyHostToDevice, s));
     int mode = h->mode;
@@ -959,13 +958,77 @@ int solve_multi_k(amg_hier *h, int k, const double *B, double *X, double rtol, i
 
 }  // namespace
 
-void free_multi(amg_hier *h) {
-    MultiWS &W = h->multi;
-    Mem &M = h->mem;
+// Allocates a K-column workspace; which: 1 float32 V-cycle vectors,
+// 2 float64 V-cycle vectors, 3 both.
+int mws_alloc(amg_hier *h, Mem &M, MultiWS &W, int K, int hist_cap, int which) {
+    int L = (int)h->lev.size() - 1;
+    int n0 = h->lev[0].A.n;
+    int64_t nk = (int64_t)n0 * K;
+    W.K = K;
+    W.hist_cap = hist_cap;
+    PCG_TRY(alloc(M, &W.b, nk));
+    PCG_TRY(alloc(M, &W.x, nk));
+    PCG_TRY(alloc(M, &W.r, nk));
+    PCG_TRY(alloc(M, &W.z, nk));
+    PCG_TRY(alloc(M, &W.p, nk));
+    PCG_TRY(alloc(M, &W.q, nk));
+    PCG_TRY(alloc(M, &W.r32, nk));
+    W.lev.assign(L + 1, MultiLevel{});
+    for (int l = 0; l <= L; l++) {
+        int64_t m = (int64_t)h->lev[l].A.n * K;
+        MultiLevel &v = W.lev[l];
+        if (which & 1) {
+            PCG_TRY(alloc(M, &v.b32, m));
+            PCG_TRY(alloc(M, &v.x32, m));
+            PCG_TRY(alloc(M, &v.t32, m));
+            PCG_TRY(alloc(M, &v.xpre32, m));
+            PCG_TRY(alloc(M, &v.xp32, m));
+        }
+        if (which & 2) {
+            PCG_TRY(alloc(M, &v.b64, m));
+            PCG_TRY(alloc(M, &v.x64, m));
+            PCG_TRY(alloc(M, &v.t64, m));
+            PCG_TRY(alloc(M, &v.xpre64, m));
+            PCG_TRY(alloc(M, &v.xp64, m));
+        }
+    }
+    PCG_TRY(alloc(M, &W.bL, (int64_t)h->nL * K));
+    int sms = 0;
+    PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    int64_t want = (nk + kMB - 1) / kMB;
+    int64_t cap = (int64_t)sms * 8;
+    W.grid = (int)(want < cap ? want : cap);
+    if (W.grid < 1) W.grid = 1;
+    PCG_TRY(alloc(M, &W.partials, (size_t)2 * K * W.grid));
+    PCG_TRY(alloc(M, &W.ctl, 1));
+    PCG_TRY(alloc(M, &W.hist, (size_t)K * W.hist_cap));
+    if (M.dry) return AMG_OK;
+    PCG_CK(cudaMemsetAsync(W.ctl, 0, sizeof(CtlM), M.stream));
+    PCG_CK(cudaMallocHost(&W.ctl_host, sizeof(CtlM)));
+    return AMG_OK;
+}
+
+// Device bytes that mws_alloc takes for this workspace shape (exact: the
+// same requests, counted by a dry-run pool).
+size_t mws_bytes(amg_hier *h, int K, int hist_cap, int which) {
+    Mem M;
+    M.dry = true;
+    MultiWS W;
+    if (mws_alloc(h, M, W, K, hist_cap, which)) return (size_t)-1;
+    return M.bytes;
+}
+
+void mws_free(Mem &M, MultiWS &W) {
     for (auto &g : W.gexec) {
         if (g) cudaGraphExecDestroy(g);
         g = nullptr;
     }
+    if (W.step_exec) cudaGraphExecDestroy(W.step_exec);
+    if (W.step_graph) cudaGraphDestroy(W.step_graph);
+    W.step_exec = nullptr;
+    W.step_graph = nullptr;
+    W.step_iters = 0;
+    W.step_mode = -1;
     release(M, W.b);
     release(M, W.x);
     release(M, W.r);
@@ -986,6 +1049,125 @@ void free_multi(amg_hier *h) {
     W.ctl_host = nullptr;
     W.K = 0;
     W.hist_cap = 0;
+}
+
+void free_multi(amg_hier *h) { mws_free(h->mem, h->multi); }
+
+namespace {
+
+// Column c of a new request: b and x0 in, and p = q = 0 (the first
+// iteration's p = z + 0 p and FCG's z.q_old must not see an earlier
+// occupant's values).
+__global__ void k_col_put(const double *__restrict__ b, const double *__restrict__ x0, double *__restrict__ B,
+                          double *__restrict__ X, double *__restrict__ P, double *__restrict__ Q, int K, int c,
+                          int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t e = (int64_t)i * K + c;
+    B[e] = b[i];
+    X[e] = x0[i];
+    P[e] = 0.0;
+    Q[e] = 0.0;
+}
+
+// Marks new columns for initialisation and wakes the solve up.
+__global__ void k_admit(CtlM *ctl, unsigned mask) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int c = 0; c < ctl->K; c++)
+        if (mask & (1u << c)) {
+            ctl->pending[c] = 1;
+            ctl->active[c] = 0;
+            ctl->status[c] = AMG_OK;
+        }
+    ctl->done = 0;
+}
+
+// Only the new columns' p and q were cleared (by their put): the running
+// columns keep their search directions.
+template <int K>
+int mws_init_pending(amg_hier *h, MultiWS &W, int mode, cudaStream_t s) {
+    return launch_init_residual_m<K>(h, W, mode, s);
+}
+
+}  // namespace
+
+// Resets a workspace's state: no column in use, solve idle.
+int mws_reset(MultiWS &W, int mode, double rtol, int maxit, cudaStream_t s) {
+    CtlM c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.rtol = rtol;
+    c0.maxit = maxit;
+    c0.mode = mode;
+    c0.k = W.K;
+    c0.K = W.K;
+    c0.done = 1;
+    *W.ctl_host = c0;
+    PCG_CK(cudaMemcpyAsync(W.ctl, W.ctl_host, sizeof(CtlM), cudaMemcpyHostToDevice, s));
+    PCG_CK(cudaStreamSynchronize(s));
+    return AMG_OK;
+}
+
+int mws_put_column(MultiWS &W, int c, const double *b_dev, const double *x_dev, int n, cudaStream_t s) {
+    k_col_put<<<(n + kMB - 1) / kMB, kMB, 0, s>>>(b_dev, x_dev, W.b, W.x, W.p, W.q, W.K, c, n);
+    PCG_LAUNCH_CK();
+    return AMG_OK;
+}
+
+// Starts the columns in mask: residual, ||b|| and state of each, while the
+// other columns keep their place in their own iterations.
+int mws_admit(amg_hier *h, MultiWS &W, int mode, unsigned mask, cudaStream_t s) {
+    k_admit<<<1, 32, 0, s>>>(W.ctl, mask);
+    PCG_LAUNCH_CK();
+    switch (W.K) {
+        case 4: return mws_init_pending<4>(h, W, mode, s);
+        case 8: return mws_init_pending<8>(h, W, mode, s);
+        case 16: return mws_init_pending<16>(h, W, mode, s);
+        default: return mws_init_pending<32>(h, W, mode, s);
+    }
+}
+
+// `iterations` iterations of every active column (kernels of finished
+// columns do no work), then the state is copied to the pinned host mirror.
+// The chunk is captured once as a graph (kept in W) that every later call
+// replays; launch = 0 only captures it.
+int mws_iterate(amg_hier *h, MultiWS &W, int mode, int iterations, cudaStream_t s, int launch) {
+    if (!W.step_exec || W.step_iters != iterations || W.step_mode != mode) {
+        if (W.step_exec) cudaGraphExecDestroy(W.step_exec);
+        if (W.step_graph) cudaGraphDestroy(W.step_graph);
+        W.step_exec = nullptr;
+        W.step_graph = nullptr;
+        if (!h->cap_stream) PCG_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = h->cap_stream;
+        PCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int st = AMG_OK;
+        for (int k = 0; k < iterations && !st; k++) {
+            switch (W.K) {
+                case 4: st = launch_iteration_m<4>(h, W, mode, cs); break;
+                case 8: st = launch_iteration_m<8>(h, W, mode, cs); break;
+                case 16: st = launch_iteration_m<16>(h, W, mode, cs); break;
+                default: st = launch_iteration_m<32>(h, W, mode, cs); break;
+            }
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&W.step_exec, g, 0);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            W.step_exec = nullptr;
+            return cuda_fail(e, "serving step graph", __FILE__, __LINE__);
+        }
+        W.step_graph = g;
+        W.step_iters = iterations;
+        W.step_mode = mode;
+    }
+    if (!launch) return AMG_OK;
+    PCG_CK(cudaGraphLaunch(W.step_exec, s));
+    PCG_CK(cudaMemcpyAsync(W.ctl_host, W.ctl, sizeof(CtlM), cudaMemcpyDeviceToHost, s));
+    return AMG_OK;
 }
 
 int solve_multi_impl(amg_hier *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,

@@ -1,0 +1,169 @@
+"""Request streams for the serving runtime (``amg_server_*``).
+
+Each mesh's hierarchy is built once and stays resident; a request is one
+time step's pressure solve on a mesh, warm-started from the previous step's
+solution (arxiv 2210.16660, Sec. 4 and Sec. 5). Requests arrive as a Poisson
+stream, each for a mesh drawn uniformly; the server batches whatever is in
+flight. Latency is measured from a request's scheduled arrival to the moment
+its result is read back on the host.
+
+Usage as a load generator::
+
+    python -m paper_2210_16660_gb300.serving --sizes 64 128 192 --count 400
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import time
+
+import numpy as np
+
+from . import binding as B
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class Mesh:
+    """One resident mesh: its problem, hierarchy and a pool of time steps
+    ``(b_t, x0_t)`` on the device (requests cycle through the pool). Meshes
+    finer than 128^3 keep the z-spacing range of the 128^3 mesh
+    (``workloads.capped_grading``)."""
+    name: str
+    problem: W.Problem
+    amg: B.AMG
+    steps: list
+
+
+def prepare_meshes(sizes=(64, 128, 192), ratio: float = 1.04, seed: int = 5, pool: int = 4,
+                   device: str = "cuda") -> list[Mesh]:
+    import torch
+    meshes = []
+    for idx, N in enumerate(sizes):
+        r = W.capped_grading(N, ratio)
+        prob = W.make_problem(N, r, seed=seed + idx, name=f"q1_{N}cube_r{r}")
+        _, xs0 = W.make_rhs(prob, 1, seed + 100 + idx)
+        chain = W.time_steps(prob, np.ascontiguousarray(xs0[:, 0]), pool, seed + 200 + idx)
+        amg = B.AMG.from_csr(prob.A, mode="fcg32")
+        steps = [(torch.from_numpy(b).to(device), torch.from_numpy(np.ascontiguousarray(x0)).to(device))
+                 for b, x0, _ in chain]
+        meshes.append(Mesh(prob.name, prob, amg, steps))
+    return meshes
+
+
+def make_server(meshes: list[Mesh], mode: str, slots: int = 8, max_engines: int = 2, chunk: int = 4,
+                hbm_budget: int = 0, queue_cap: int = 1 << 20, rtol: float = 1e-8, maxit: int = 1000) -> B.Server:
+    loads = [float(m.problem.A.n) for m in meshes]
+    return B.Server([m.amg for m in meshes], mode=mode, slots=slots, max_engines=max_engines, chunk=chunk,
+                    queue_cap=queue_cap, rtol=rtol, maxit=maxit, hbm_budget=hbm_budget, loads=loads)
+
+
+def run_stream(server: B.Server, meshes: list[Mesh], rate: float, count: int, seed: int = 5) -> dict:
+    """Serve ``count`` requests arriving at ``rate`` per second (inf: all at
+    once). Returns throughput, latency percentiles and per-request outcomes."""
+    import torch
+    arrivals = W.poisson_arrivals(rate, count, seed)
+    which = W.uniform_choices(count, len(meshes), seed)
+    used = [0] * len(meshes)
+    outstanding: dict[int, tuple[int, float]] = {}
+    lat, iters, rels, statuses, queue_ms = [], [], [], [], []
+    rejected = 0
+    nxt = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_first_done = None
+    t_last = t0
+    while nxt < count or outstanding:
+        now = time.perf_counter() - t0
+        while nxt < count and arrivals[nxt] <= now:
+            m = int(which[nxt])
+            b, x0 = meshes[m].steps[used[m] % len(meshes[m].steps)]
+            used[m] += 1
+            x = torch.empty_like(b)
+            st, t = server.submit(m, b, x0, x)
+            if st == B.OK:
+                outstanding[t] = (nxt, float(arrivals[nxt]))
+            else:
+                rejected += 1
+            nxt += 1
+        if server.progress(wait=False) == 0:
+            continue
+        tnow = time.perf_counter()
+        for t in list(outstanding):
+            r = server.result(t)
+            if r is None:
+                continue
+            _, arr = outstanding.pop(t)
+            lat.append(1e3 * (tnow - t0 - arr))
+            iters.append(r.iters)
+            rels.append(r.true_rel)
+            statuses.append(r.status)
+            queue_ms.append(r.queue_ms)
+            t_last = tnow
+            if t_first_done is None:
+                t_first_done = tnow
+    span = t_last - t0
+    done = len(lat)
+    lat_a = np.asarray(lat) if lat else np.zeros(1)
+    return {
+        "rate": None if not np.isfinite(rate) else rate,
+        "requests": count,
+        "completed": done,
+        "rejected": rejected,
+        "span_s": span,
+        "solves_per_s": done / span if span > 0 else 0.0,
+        "p50_ms": float(np.percentile(lat_a, 50)),
+        "p99_ms": float(np.percentile(lat_a, 99)),
+        "mean_queue_ms": float(np.mean(queue_ms)) if queue_ms else 0.0,
+        "mean_iters": float(np.mean(iters)) if iters else 0.0,
+        "max_true_rel": float(np.max(rels)) if rels else 0.0,
+        "all_ok": bool(statuses) and all(s == B.OK for s in statuses),
+    }
+
+
+def serve_modes(meshes: list[Mesh], count: int, load_fraction: float = 0.7, seed: int = 5, **server_kw) -> dict:
+    """For each mode: saturated throughput (every request queued at t = 0),
+    then latency at ``load_fraction`` of that throughput."""
+    out = {}
+    for mode in ("fcg32", "pcg64"):
+        srv = make_server(meshes, mode, **server_kw)
+        try:
+            run_stream(srv, meshes, float("inf"), max(8, count // 8), seed + 1)       # warm-up
+            sat = run_stream(srv, meshes, float("inf"), count, seed)
+            rate = load_fraction * sat["solves_per_s"]
+            lat = run_stream(srv, meshes, rate, count, seed + 2)
+        finally:
+            srv.close()
+        out[mode] = {"saturated": sat, "at_load": lat}
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--sizes", type=int, nargs="+", default=[64, 128, 192])
+    ap.add_argument("--count", type=int, default=400)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--engines", type=int, default=2)
+    ap.add_argument("--chunk", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=0.0)
+    ap.add_argument("--rates", type=float, nargs="*", default=[],
+                    help="arrival rates to sweep (per s); default: saturation and 70%% of it")
+    a = ap.parse_args(argv)
+    meshes = prepare_meshes(tuple(a.sizes))
+    kw = dict(slots=a.slots, max_engines=a.engines, chunk=a.chunk, hbm_budget=int(a.budget_gb * 2 ** 30))
+    if not a.rates:
+        print(json.dumps(serve_modes(meshes, a.count, **kw)))
+        return
+    for mode in ("fcg32", "pcg64"):
+        srv = make_server(meshes, mode, **kw)
+        try:
+            for rate in a.rates:
+                r = run_stream(srv, meshes, rate, a.count)
+                print(json.dumps({"mode": mode, **r}))
+        finally:
+            srv.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -251,3 +251,48 @@ def batch_sizes(count: int = 48, lo: int = 24, hi: int = 112, seed: int = 3) -> 
     """Node counts per side for a batch of independent systems, uniform on [lo, hi]."""
     w = splitmix64(seed, count)
     return [int(lo + int(v % np.uint64(hi - lo + 1))) for v in w]
+
+
+def capped_grading(N: int, ratio: float, ref_N: int = 128) -> float:
+    """z-grading ratio for an N^3 mesh whose largest-to-smallest z spacing
+    does not exceed that of the ref_N^3 mesh at ``ratio`` (ratio^(ref_N-2)),
+    rounded to 4 decimals. Finer meshes than ref_N keep the range, so the
+    far-field cells are not stretched further (1.04 at 192^3 would span
+    1.04^190 ~ 1700)."""
+    if N <= ref_N:
+        return ratio
+    return round(ratio ** ((ref_N - 2) / (N - 2)), 4)
+
+
+def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream of ``count`` requests at ``rate``
+    per second, starting at 0: exponential gaps ``-ln(u) / rate`` with ``u``
+    in ``(0, 1]`` from SplitMix64 words; rate = inf puts every arrival at 0."""
+    if not np.isfinite(rate):
+        return np.zeros(count)
+    w = splitmix64(seed, count)
+    u = ((w >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
+    gaps = -np.log(u) / rate
+    gaps[0] = 0.0
+    return np.cumsum(gaps)
+
+
+def uniform_choices(count: int, m: int, seed: int) -> np.ndarray:
+    """``count`` indices uniform on ``0..m-1`` (which mesh each request is for)."""
+    w = splitmix64(seed, count, offset=1 << 20)
+    return (w % np.uint64(m)).astype(np.int64)
+
+
+def time_steps(problem: Problem, x_start: np.ndarray, steps: int, seed: int,
+               scale: float = 0.01) -> list[tuple[np.ndarray, np.ndarray, np.ndarray]]:
+    """A chain of time-step-like requests on one mesh: step t has exact
+    solution ``x*_t`` (``perturb_step`` of ``x*_{t-1}``), right-hand side
+    ``b_t = A x*_t`` and warm start ``x0_t = x*_{t-1}``. Returns
+    ``[(b_t, x0_t, x*_t)]`` for t = 1..steps."""
+    out = []
+    x_prev = x_start
+    for t in range(1, steps + 1):
+        b, xs = perturb_step(problem, x_prev, seed, t, scale)
+        out.append((b, x_prev, xs))
+        x_prev = xs
+    return out

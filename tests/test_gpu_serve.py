@@ -1,0 +1,214 @@
+"""Serving runtime (amg_server_*): continuous batching over resident meshes.
+
+A request's result must not depend on what it shares the device with: the
+same request served alone and in a mix (other meshes, other slots, other
+engines, admitted while others are mid-solve) gives the same x bit for bit,
+and it equals the matching column of pcg_solve_multi with the same slot
+count. Each result also meets the single-solve bar against the oracle
+(iterations within +-1, true residual <= rtol, ||x - x_oracle|| <= 1e-6
+||x_oracle||). Budget admission, the queue cap and the special requests
+(b = 0, a converged x0, maxit exhausted, host buffers) are covered too.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2210_16660_gb300 import binding as B  # noqa: E402
+from paper_2210_16660_gb300 import serving as S  # noqa: E402
+from paper_2210_16660_gb300 import workloads as W  # noqa: E402
+
+RTOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def meshes():
+    return S.prepare_meshes((12, 16, 20), ratio=1.04, seed=31, pool=3)
+
+
+def _serve_alone(srv, m, b, x0):
+    x = torch.empty_like(b)
+    st, t = srv.submit(m, b, x0, x)
+    assert st == B.OK
+    r = srv.drain([t])[t]
+    return x, r
+
+
+@pytest.mark.parametrize("mode", ["fcg32", "pcg64"])
+def test_alone_and_in_the_mix_are_identical(meshes, mode):
+    srv = S.make_server(meshes, mode, slots=4, max_engines=2, chunk=3)
+    reqs = [(i % 3, (i // 3) % 3) for i in range(16)]
+    xs, tickets = [], []
+    for j, (m, k) in enumerate(reqs):
+        b, x0 = meshes[m].steps[k]
+        x = torch.empty_like(b)
+        st, t = srv.submit(m, b, x0, x)
+        assert st == B.OK
+        xs.append(x)
+        tickets.append(t)
+        if j % 5 == 4:                      # requests keep arriving while others run
+            srv.progress(wait=True)
+    res = srv.drain(tickets)
+    assert srv.info()["running"] == 0 and srv.info()["queued"] == 0
+    for j, (m, k) in enumerate(reqs):
+        r = res[tickets[j]]
+        assert r.status == B.OK and r.true_rel <= RTOL
+        b, x0 = meshes[m].steps[k]
+        xa, ra = _serve_alone(srv, m, b, x0)
+        assert torch.equal(xa, xs[j]), (j, m, k, float((xa - xs[j]).abs().max()))
+        assert ra.iters == r.iters
+    # against the oracle from the same warm start (one request per mesh)
+    for m in range(3):
+        b, x0 = meshes[m].steps[0]
+        j = reqs.index((m, 0))
+        h_or = O.Hierarchy(meshes[m].problem.A, n_pass=2)
+        ref = h_or.solve(b.cpu().numpy(), x0=x0.cpu().numpy(), rtol=RTOL, maxit=1000, mode=mode)
+        assert abs(res[tickets[j]].iters - ref["iters"]) <= 1
+        xh = xs[j].cpu().numpy()
+        assert np.linalg.norm(xh - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+        bh = b.cpu().numpy()
+        assert np.linalg.norm(bh - W.spmv(meshes[m].problem.A, xh)) <= RTOL * np.linalg.norm(bh)
+    srv.close()
+
+
+def test_requests_join_an_engine_mid_solve(meshes):
+    """Two requests start, two more join the same engine between chunks while
+    the first two are still iterating; all four equal their solo results."""
+    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1, chunk=2)
+    m = 2
+    xs, tickets = [], []
+    for k in (0, 1):
+        b, x0 = meshes[m].steps[k]
+        x = torch.empty_like(b)
+        tickets.append(srv.submit(m, b, x0, x)[1])
+        xs.append(x)
+    srv.progress()
+    assert srv.info()["running"] == 2
+    for k in (2, 0):
+        b, x0 = meshes[m].steps[k]
+        x = torch.empty_like(b)
+        tickets.append(srv.submit(m, b, x0, x)[1])
+        xs.append(x)
+    srv.progress(wait=True)                 # first chunk back: nobody done after 2 iterations
+    assert srv.info()["running"] == 4
+    res = srv.drain(tickets)
+    assert all(res[t].status == B.OK for t in tickets)
+    assert torch.equal(xs[0], xs[3])        # same request, started at different times
+    for j, k in enumerate((0, 1, 2, 0)):
+        b, x0 = meshes[m].steps[k]
+        xa, ra = _serve_alone(srv, m, b, x0)
+        assert torch.equal(xa, xs[j]) and ra.iters == res[tickets[j]].iters
+    srv.close()
+
+
+@pytest.mark.parametrize("mode", ["fcg32", "pcg64"])
+def test_served_equals_multi_column(meshes, mode):
+    m = 1
+    mesh = meshes[m]
+    n = mesh.problem.A.n
+    Bm = torch.stack([mesh.steps[k][0] for k in range(3)] + [mesh.steps[0][0] * 0.5], dim=1).contiguous()
+    X0 = torch.stack([mesh.steps[k][1] for k in range(3)] + [mesh.steps[0][1] * 0.5], dim=1).contiguous()
+    X = X0.clone()
+    mesh.amg.set_mode(mode)
+    st, it, _, sts, _ = mesh.amg.solve_multi(Bm, X, rtol=RTOL)
+    mesh.amg.set_mode("fcg32")
+    assert st == 0
+    srv = S.make_server(meshes, mode, slots=4, max_engines=1, chunk=5)
+    xs, tickets = [], []
+    for c in range(4):
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        tickets.append(srv.submit(m, Bm[:, c].contiguous(), X0[:, c].contiguous(), x)[1])
+        xs.append(x)
+    res = srv.drain(tickets)
+    for c in range(4):
+        assert torch.equal(xs[c], X[:, c]), c
+        assert res[tickets[c]].iters == int(it[c])
+    srv.close()
+
+
+def test_budget_admission(meshes):
+    probe = S.make_server(meshes, "fcg32", slots=4, max_engines=2)
+    info = [probe.mesh_info(m) for m in range(3)]
+    probe.close()
+    res = [i[3] for i in info]
+    eb = [i[2] for i in info]
+    assert all(r > 0 for r in res) and all(e > 0 for e in eb)
+    budget = res[0] + eb[0] + res[1] + eb[1] + eb[0] // 2     # mesh 2 cannot fit, no room for extras
+    if res[2] + eb[2] <= eb[0] // 2:
+        pytest.skip("mesh sizes too close for this budget split")
+    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=2, hbm_budget=budget)
+    st, eng, tot = B.serve_plan(res, eb, budget, 2, loads=[float(mm.problem.A.n) for mm in meshes])
+    assert [srv.mesh_info(m)[0] for m in range(3)] == list(eng) == [1, 1, 0]
+    assert srv.info()["used"] == tot <= budget
+    b, x0 = meshes[2].steps[0]
+    st, _ = srv.submit(2, b, x0, torch.empty_like(b))
+    assert st == B.ERR_OOM
+    x, r = _serve_alone(srv, 0, *meshes[0].steps[0])
+    assert r.status == B.OK and r.true_rel <= RTOL
+    srv.close()
+    with pytest.raises(B.AmgError) as e:
+        S.make_server(meshes, "fcg32", slots=4, hbm_budget=res[0] // 2)
+    assert e.value.status == B.ERR_OOM
+
+
+def test_queue_cap(meshes):
+    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1, queue_cap=2)
+    b, x0 = meshes[0].steps[0]
+    outs = [torch.empty_like(b) for _ in range(3)]
+    assert srv.submit(0, b, x0, outs[0])[0] == B.OK
+    assert srv.submit(0, b, x0, outs[1])[0] == B.OK
+    st, t = srv.submit(0, b, x0, outs[2])
+    assert st == B.ERR_BUSY and t == 0
+    srv.progress()                           # both start: the queue is empty again
+    st, t = srv.submit(0, b, x0, outs[2])
+    assert st == B.OK
+    srv.drain([1, 2, t])
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    srv.close()
+
+
+def test_special_requests_and_host_buffers(meshes):
+    m = 0
+    mesh = meshes[m]
+    A = mesh.problem.A
+    n = A.n
+    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1, chunk=3, maxit=1000)
+    b, x0 = (t.cpu().numpy() for t in mesh.steps[0])
+    zero_b = np.zeros(n)
+    x_exact = np.linalg.solve(A.to_dense(), b)
+    outs = [np.full(n, 7.0) for _ in range(4)]
+    t0 = srv.submit(m, zero_b, x0.copy(), outs[0])[1]          # b = 0 -> x = 0
+    t1 = srv.submit(m, b, x_exact, outs[1])[1]                 # converged start
+    t2 = srv.submit(m, b, x0.copy(), outs[2])[1]               # ordinary, host buffers
+    t3 = srv.submit(m, b, np.zeros(n), outs[3])[1]
+    res = srv.drain([t0, t1, t2, t3])
+    assert res[t0].status == B.OK and res[t0].iters == 0 and not outs[0].any()
+    assert res[t1].status == B.OK and res[t1].iters == 0 and np.array_equal(outs[1], x_exact)
+    for t, x in ((t2, outs[2]), (t3, outs[3])):
+        assert res[t].status == B.OK and res[t].iters > 0
+        assert np.linalg.norm(b - W.spmv(A, x)) <= RTOL * np.linalg.norm(b)
+    assert res[t3].iters >= res[t2].iters       # the warm start helps
+    srv.close()
+    # maxit exhausted for one request does not disturb the others
+    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1, chunk=2, maxit=2)
+    out = np.zeros(n)
+    t = srv.submit(m, b, np.zeros(n), out)[1]
+    r = srv.drain([t])[t]
+    assert r.status == B.ERR_NOCONV and r.iters == 2
+    srv.close()
+
+
+def test_bad_server_arguments(meshes):
+    with pytest.raises(B.AmgError) as e:
+        S.make_server(meshes, "fcg32", slots=6)
+    assert e.value.status == B.ERR_ARG
+    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1)
+    b, x0 = meshes[0].steps[0]
+    assert srv.submit(5, b, x0, torch.empty_like(b))[0] == B.ERR_ARG
+    with pytest.raises(B.AmgError):
+        srv.result(12345)
+    assert srv.progress() == 0                # nothing to do
+    srv.close()
