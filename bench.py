@@ -56,9 +56,11 @@ def parse_args(argv=None):
     ap.add_argument("--serve-count", type=int, default=160,
                     help="requests per serving run over resident 64^3/128^3/192^3 meshes (0: skip)")
     ap.add_argument("--serve-sizes", type=int, nargs="+", default=[64, 128, 192])
-    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-engines", type=int, default=2)
     ap.add_argument("--serve-chunk", type=int, default=4)
+    ap.add_argument("--serve-batch-min", type=int, default=3)
+    ap.add_argument("--serve-no-solo", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -438,14 +440,15 @@ def run_ours(args):
         for a in bamgs:
             a.close()
 
-    # serving: Poisson streams of warm-started solves over resident meshes,
-    # continuous batching; saturated throughput, then p50/p99 at 70% of it
+    # serving: Poisson streams of warm-started solves over resident meshes;
+    # the batching server (mixed and float64) against the plain float64
+    # solver serving one request at a time, saturated and at a common rate
     serving = {}
     if args.serve_count > 0:
         from paper_2210_16660_gb300 import serving as SV
         meshes = SV.prepare_meshes(tuple(args.serve_sizes), ratio=args.ratio, seed=5, pool=4, device=device)
         kw = dict(slots=args.serve_slots, max_engines=args.serve_engines, chunk=args.serve_chunk,
-                  rtol=args.rtol, maxit=args.maxit)
+                  rtol=args.rtol, maxit=args.maxit, solo=not args.serve_no_solo, batch_min=args.serve_batch_min)
         srv = SV.make_server(meshes, "fcg32", **kw)
         plan = [dict(zip(("engines", "slots", "engine_bytes", "resident_bytes"), srv.mesh_info(i)))
                 for i in range(len(meshes))]
@@ -454,7 +457,9 @@ def run_ours(args):
         serving = {"meshes": [{"name": mm.name, "n": mm.problem.A.n, **pl} for mm, pl in zip(meshes, plan)],
                    "requests_per_run": args.serve_count, "arrivals": "Poisson, mesh uniform, seed 5",
                    "warm_start": "x0 = previous step's x*, x*_t = x*_{t-1} + 0.01 rms(x*_{t-1}) xi_t",
-                   "mixed": res["fcg32"], "fp64": res["pcg64"]}
+                   "server": {"slots": args.serve_slots, "max_engines": args.serve_engines,
+                              "chunk": args.serve_chunk, "solo": not args.serve_no_solo,
+                              "batch_min": args.serve_batch_min}, **res}
         for mm in meshes:
             mm.amg.close()
         del meshes

@@ -167,15 +167,19 @@ void amg_batch_destroy(amg_batch b);
  *
  * A request is (mesh, b, x0): solve A_mesh x = b from x0 to
  * ||b - A x|| / ||b|| <= rtol with the server's mode. Every mesh gets engines
- * of `slots` right-hand-side slots (the kernels of pcg_solve_multi). A
- * request takes a free slot of its mesh; between chunks of `chunk`
- * iterations the host hands finished requests back and starts queued ones in
- * the freed slots, while the other slots carry on where they were
- * (continuous batching). Engines run on their own streams and overlap on the
- * device. A request's result depends only on its own (mesh, b, x0) and the
- * server parameters, not on what else is running: for a given `slots` it is
- * the same bit for bit alone or in any mix, and it equals column c of
- * pcg_solve_multi with the same K in the same mode.
+ * of `slots` right-hand-side slots (the kernels of pcg_solve_multi) and, with
+ * `solo`, a whole-solve lane (the kernels of pcg_solve, one graph launch per
+ * solve, on the hierarchy's own vectors). A queued request goes to its
+ * mesh's lane when the lane is idle, else to a free engine slot; between
+ * chunks of `chunk` iterations the host hands finished requests back and
+ * starts queued ones in the freed slots, while the other slots carry on
+ * where they were (continuous batching). Lanes and engines run on their own
+ * streams and overlap on the device. A request's result depends only on its
+ * own (mesh, b, x0), the server parameters and the kind of place it ran in
+ * (reported by amg_server_result), not on what else is running: in a lane it
+ * equals pcg_solve's result bit for bit; in a slot it is the same bit for bit
+ * as in any other slot or mix and equals column c of pcg_solve_multi with
+ * the same K. Both meet rtol; they differ by summation order only.
  *
  * Memory: the resident hierarchies (all device bytes each handle holds) plus
  * every engine fit in hbm_budget bytes (0: the hierarchies' bytes plus the
@@ -198,10 +202,13 @@ typedef struct {
     int maxit;         /* iterations per request, at most */
     double rtol;       /* relative residual target per request */
     size_t hbm_budget; /* device bytes for hierarchies plus engines; 0: see above */
+    int solo;          /* 1: a whole-solve lane per admitted mesh (no extra memory) */
+    int batch_min;     /* with a lane: an idle engine starts once this many requests wait (>= 1) */
+    int lane_priority; /* 1: lanes on the highest stream priority, engines on the lowest */
 } amg_server_params;
 
-/* FCG32, 8 slots, 2 engines per mesh, chunk 4, queue 4096, maxit 1000,
- * rtol 1e-8, budget 0. */
+/* FCG32, 4 slots, 2 engines per mesh, chunk 4, queue 4096, maxit 1000,
+ * rtol 1e-8, budget 0, solo 1, batch_min 3, lane_priority 0. */
 void amg_server_default_params(amg_server_params *p);
 
 /* Engine plan (host only, no device call). Mesh i needs resident[i] bytes for
@@ -251,10 +258,11 @@ int amg_server_progress(amg_server s, int wait, int *finished);
 /* Outcome of a request. *done = 0 while it is queued or running; once it is
  * 1 the record is released and the ticket is no longer known. status: the
  * request's AMG_* code (AMG_ERR_NOCONV with x = last iterate, as pcg_solve);
- * iters; true_rel = ||b - A x|| / ||b||; times (3 doubles, may be NULL):
- * ms waiting in the queue, ms in a slot, ms from submit to finish. Returns
- * AMG_ERR_ARG for an unknown ticket. */
-int amg_server_result(amg_server s, int64_t ticket, int *done, int *status, int *iters, double *true_rel,
+ * iters; true_rel = ||b - A x|| / ||b||; lane: 0 if it ran in a whole-solve
+ * lane, 1 in an engine slot; times (3 doubles, may be NULL): ms waiting in
+ * the queue, ms running, ms from submit to finish. Returns AMG_ERR_ARG for an
+ * unknown ticket. */
+int amg_server_result(amg_server s, int64_t ticket, int *done, int *status, int *iters, double *true_rel, int *lane,
                       double *times);
 
 /* Waits for running chunks and frees every engine (not the hierarchies). */

@@ -42,7 +42,8 @@ class AmgParams(C.Structure):
 
 class ServerParams(C.Structure):
     _fields_ = [("mode", C.c_int), ("slots", C.c_int), ("max_engines", C.c_int), ("chunk", C.c_int),
-                ("queue_cap", C.c_int), ("maxit", C.c_int), ("rtol", C.c_double), ("hbm_budget", C.c_size_t)]
+                ("queue_cap", C.c_int), ("maxit", C.c_int), ("rtol", C.c_double), ("hbm_budget", C.c_size_t),
+                ("solo", C.c_int), ("batch_min", C.c_int), ("lane_priority", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -118,7 +119,8 @@ def load(build_if_missing: bool = True):
     lib.amg_server_submit.restype = I
     lib.amg_server_progress.argtypes = [P, I, C.POINTER(I)]
     lib.amg_server_progress.restype = I
-    lib.amg_server_result.argtypes = [P, I64, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(D), P]
+    lib.amg_server_result.argtypes = [P, I64, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(I),
+                                      P]
     lib.amg_server_result.restype = I
     lib.amg_server_destroy.argtypes = [P]
     lib.amg_server_destroy.restype = None
@@ -419,6 +421,7 @@ class ServeResult:
     status: int
     iters: int
     true_rel: float
+    lane: int          # 0: whole-solve lane, 1: engine slot
     queue_ms: float
     run_ms: float
     total_ms: float
@@ -432,15 +435,17 @@ class Server:
     (None before). Buffers passed to ``submit`` are kept referenced here until
     the request's result has been read."""
 
-    def __init__(self, amgs, mode: str = "fcg32", slots: int = 8, max_engines: int = 2, chunk: int = 4,
-                 queue_cap: int = 4096, rtol: float = 1e-8, maxit: int = 1000, hbm_budget: int = 0, loads=None):
+    def __init__(self, amgs, mode: str = "fcg32", slots: int = 4, max_engines: int = 2, chunk: int = 4,
+                 queue_cap: int = 4096, rtol: float = 1e-8, maxit: int = 1000, hbm_budget: int = 0, loads=None,
+                 solo: bool = True, batch_min: int = 3, lane_priority: bool = False):
         lib = load()
         self.amgs = list(amgs)
         p = ServerParams()
         lib.amg_server_default_params(C.byref(p))
         p.mode = _MODES[mode] if isinstance(mode, str) else int(mode)
         p.slots, p.max_engines, p.chunk, p.queue_cap = slots, max_engines, chunk, queue_cap
-        p.rtol, p.maxit, p.hbm_budget = rtol, maxit, int(hbm_budget)
+        p.rtol, p.maxit, p.hbm_budget, p.solo = rtol, maxit, int(hbm_budget), int(bool(solo))
+        p.batch_min, p.lane_priority = batch_min, int(bool(lane_priority))
         arr = (C.c_void_p * len(self.amgs))(*[a._h.value for a in self.amgs])
         ld = None if loads is None else np.ascontiguousarray(loads, dtype=np.float64)
         srv = C.c_void_p()
@@ -500,17 +505,17 @@ class Server:
         return f.value
 
     def result(self, ticket: int):
-        done, sts, it = C.c_int(), C.c_int(), C.c_int()
+        done, sts, it, lane = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         tr = C.c_double()
         tm = np.zeros(3)
         st = load().amg_server_result(self._s, ticket, C.byref(done), C.byref(sts), C.byref(it), C.byref(tr),
-                                          tm.ctypes.data)
+                                      C.byref(lane), tm.ctypes.data)
         if st:
             raise AmgError(st, last_error())
         if not done.value:
             return None
         self._keep.pop(ticket, None)
-        return ServeResult(sts.value, it.value, tr.value, float(tm[0]), float(tm[1]), float(tm[2]))
+        return ServeResult(sts.value, it.value, tr.value, lane.value, float(tm[0]), float(tm[1]), float(tm[2]))
 
     def drain(self, tickets):
         """Run until every ticket has finished; returns {ticket: ServeResult}."""

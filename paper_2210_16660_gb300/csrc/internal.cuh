@@ -237,6 +237,10 @@ void free_profile(amg_hier *h);
 int solve_multi_impl(amg_hier *h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
                      double *res_hist, cudaStream_t s);
 void free_multi(amg_hier *h);
+int solve_prepare(amg_hier *h, int mode, int maxit);
+int solve_launch(amg_hier *h, int mode, const double *b, const double *x0, double rtol, int maxit, cudaStream_t s);
+int solve_collect(amg_hier *h, int mode, double *x, cudaStream_t s, int *status, int *iters, double *true_rel,
+                  int64_t *kernels);
 int mws_alloc(amg_hier *h, Mem &M, MultiWS &W, int K, int hist_cap, int which);
 void mws_free(Mem &M, MultiWS &W);
 size_t mws_bytes(amg_hier *h, int K, int hist_cap, int which);

@@ -5,13 +5,16 @@
 // from the previous step's solution (Sec. 5).
 //
 // Continuous batching: every mesh has engines of K right-hand-side slots
-// (the multi-column kernels). A request takes a free slot of its mesh; the
-// host visits an engine between chunks of `chunk` iterations, hands finished
-// columns back, and starts queued requests in the freed slots while the
-// other columns carry on from where they were. Each engine has its own stream
-// and its own captured chunk graph, so engines (of one mesh or of several)
-// overlap on the device. A request's arithmetic is that of its own column
-// only, so its result does not depend on what shares the engine.
+// (the multi-column kernels) and a whole-solve lane (the single-column
+// kernels, one graph launch per solve). A request goes to its mesh's lane if
+// the lane is idle (at low load a request runs at the speed of a lone
+// solve), else to a free slot; the host visits an engine between chunks of
+// `chunk` iterations, hands finished columns back, and starts queued
+// requests in the freed slots while the other columns carry on from where
+// they were. Each lane and engine has its own stream (engines their own
+// captured chunk graph), so they overlap on the device. A request's
+// arithmetic is that of its own column only, so its result does not depend
+// on what shares the engine.
 //
 // Memory: the resident hierarchies and all engine workspaces fit in a byte
 // budget; amg_serve_plan (host only) picks the engine count per mesh.
@@ -56,6 +59,16 @@ struct Request {
     int status = AMG_OK, iters = 0;
     double true_rel = 0.0;
     double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
+    int lane = 0;  // 0: whole-solve lane, 1: a slot of a batching engine
+};
+
+// Whole-solve lane of one mesh: the single right-hand-side kernels (one graph
+// launch per solve) on the hierarchy's own resident vectors.
+struct Lane {
+    amg_hier *h = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    int64_t ticket = -1;
 };
 
 struct Engine {
@@ -82,6 +95,7 @@ struct amg_server_s {
     std::vector<int> engines_of;
     std::vector<size_t> engine_bytes, resident;
     std::vector<Engine *> eng;
+    std::vector<Lane> lane;  // per mesh; h == nullptr: none
     std::vector<std::deque<int64_t>> queue;
     std::unordered_map<int64_t, Request> req;
     int64_t next_ticket = 1;
@@ -124,7 +138,12 @@ int engine_create(amg_server_s *sv, int mesh, Engine **out) {
     int n = h->lev[0].A.n;
     int K = sv->prm.slots;
     int st = AMG_OK;
-    cudaError_t ce = cudaStreamCreateWithFlags(&e->s, cudaStreamNonBlocking);
+    // With lane_priority, engines run at the lowest stream priority: they fill
+    // what the whole-solve lanes leave of the device.
+    int least = 0, greatest = 0;
+    cudaError_t ce = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    int prio = sv->prm.lane_priority ? least : 0;
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&e->s, cudaStreamNonBlocking, prio);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming);
     if (ce != cudaSuccess) st = cuda_fail(ce, "serving engine stream", __FILE__, __LINE__);
     e->mem.stream = e->s;
@@ -199,10 +218,15 @@ int harvest(amg_server_s *sv, Engine *e, int *finished) {
     return AMG_OK;
 }
 
-// Starts queued requests of this engine's mesh in its free slots.
+// Starts queued requests of this engine's mesh in its free slots. An idle
+// engine starts only once batch_min requests wait (when the mesh has a lane:
+// a lone request is served faster by waiting for the lane than by a slot).
 int admit(amg_server_s *sv, Engine *e) {
     auto &qu = sv->queue[e->mesh];
     if (qu.empty()) return AMG_OK;
+    bool idle = true;
+    for (int64_t t : e->slot) idle &= t < 0;
+    if (idle && sv->lane[e->mesh].h && (int)qu.size() < sv->prm.batch_min) return AMG_OK;
     int n = e->h->lev[0].A.n;
     size_t bytes = sizeof(double) * (size_t)n;
     unsigned mask = 0;
@@ -225,6 +249,7 @@ int admit(amg_server_s *sv, Engine *e) {
         sv->launches++;
         e->slot[q] = t;
         r.t_start = t0;
+        r.lane = 1;
         mask |= 1u << q;
         sv->queued--;
         sv->running++;
@@ -232,6 +257,36 @@ int admit(amg_server_s *sv, Engine *e) {
     if (!mask) return AMG_OK;
     PCG_TRY(mws_admit(e->h, e->W, sv->prm.mode, mask, e->s));
     sv->launches += 2;
+    return AMG_OK;
+}
+
+int lane_start(amg_server_s *sv, Lane &ln, int mesh) {
+    auto &qu = sv->queue[mesh];
+    if (qu.empty() || ln.ticket >= 0) return AMG_OK;
+    int64_t t = qu.front();
+    qu.pop_front();
+    Request &r = sv->req[t];
+    PCG_TRY(solve_launch(ln.h, sv->prm.mode, r.b, r.x0, sv->prm.rtol, sv->prm.maxit, ln.s));
+    PCG_CK(cudaEventRecord(ln.ev, ln.s));
+    ln.ticket = t;
+    r.t_start = now_s();
+    r.lane = 0;
+    sv->queued--;
+    sv->running++;
+    return AMG_OK;
+}
+
+int lane_finish(amg_server_s *sv, Lane &ln, int *finished) {
+    Request &r = sv->req[ln.ticket];
+    int64_t k = 0;
+    PCG_TRY(solve_collect(ln.h, sv->prm.mode, r.x, ln.s, &r.status, &r.iters, &r.true_rel, &k));
+    PCG_CK(cudaStreamSynchronize(ln.s));
+    sv->launches += k;
+    r.done = true;
+    r.t_done = now_s();
+    sv->running--;
+    ln.ticket = -1;
+    if (finished) (*finished)++;
     return AMG_OK;
 }
 
@@ -252,8 +307,11 @@ void amg_server_default_params(amg_server_params *p) {
     if (!p) return;
     memset(p, 0, sizeof(*p));
     p->mode = AMG_MODE_FCG32;
-    p->slots = 8;
+    p->slots = 4;
     p->max_engines = 2;
+    p->solo = 1;
+    p->batch_min = 3;
+    p->lane_priority = 0;
     p->chunk = 4;
     p->queue_cap = 4096;
     p->maxit = 1000;
@@ -317,8 +375,10 @@ int amg_server_create(const amg_server_params *p, int m, const amg_handle *meshe
     const amg_server_params &P = *p;
     if ((P.mode != AMG_MODE_FCG32 && P.mode != AMG_MODE_PCG64) ||
         (P.slots != 4 && P.slots != 8 && P.slots != 16 && P.slots != 32) || P.max_engines < 1 || P.chunk < 1 ||
-        P.queue_cap < 0 || P.maxit < 0 || !(P.rtol >= 0.0)) {
-        set_error("amg_server_create: bad parameters (mode, slots in {4,8,16,32}, max_engines >= 1, chunk >= 1)");
+        P.queue_cap < 0 || P.maxit < 0 || !(P.rtol >= 0.0) || (P.solo != 0 && P.solo != 1) || P.batch_min < 1 ||
+        (P.lane_priority != 0 && P.lane_priority != 1)) {
+        set_error("amg_server_create: bad parameters (mode, slots in {4,8,16,32}, max_engines >= 1, chunk >= 1, "
+                  "solo 0 or 1, batch_min >= 1, lane_priority 0 or 1)");
         return AMG_ERR_ARG;
     }
     for (int i = 0; i < m; i++) {
@@ -360,6 +420,21 @@ int amg_server_create(const amg_server_params *p, int m, const amg_handle *meshe
     sv->budget = budget;
     int st = amg_serve_plan(m, sv->resident.data(), sv->engine_bytes.data(), load, budget, P.max_engines,
                             sv->engines_of.data(), &sv->used);
+    sv->lane.resize(m);
+    for (int i = 0; i < m && !st && P.solo; i++) {
+        if (!sv->engines_of[i]) continue;
+        Lane &ln = sv->lane[i];
+        ln.h = sv->meshes[i];
+        // With lane_priority, lanes run at the highest priority, so a request
+        // that finds its lane idle runs at close to the speed of a lone solve.
+        int least = 0, greatest = 0;
+        cudaError_t ce = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        int prio = P.lane_priority ? greatest : 0;
+        if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&ln.s, cudaStreamNonBlocking, prio);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ln.ev, cudaEventDisableTiming);
+        if (ce != cudaSuccess) st = cuda_fail(ce, "serving lane stream", __FILE__, __LINE__);
+        if (!st) st = solve_prepare(ln.h, P.mode, P.maxit);
+    }
     for (int i = 0; i < m && !st; i++)
         for (int k = 0; k < sv->engines_of[i] && !st; k++) {
             Engine *e = nullptr;
@@ -442,6 +517,17 @@ int amg_server_progress(amg_server sv, int wait, int *finished) {
     int fin = 0;
     for (;;) {
         bool busy = false, ready = false;
+        for (Lane &ln : sv->lane) {
+            if (ln.ticket < 0) continue;
+            cudaError_t q = cudaEventQuery(ln.ev);
+            if (q == cudaErrorNotReady) {
+                busy = true;
+                continue;
+            }
+            if (q != cudaSuccess) return cuda_fail(q, "serving lane", __FILE__, __LINE__);
+            ready = true;
+            PCG_TRY(lane_finish(sv, ln, &fin));
+        }
         for (Engine *e : sv->eng) {
             if (!e->inflight) continue;
             cudaError_t q = cudaEventQuery(e->ev);
@@ -457,7 +543,10 @@ int amg_server_progress(amg_server sv, int wait, int *finished) {
         if (ready || !busy || !wait) break;
         std::this_thread::yield();
     }
-    // Idle engines: take queued work, then run one chunk if any slot is in use.
+    // An idle whole-solve lane takes the head of its mesh's queue; idle engines
+    // take what is left, then run one chunk if any slot is in use.
+    for (int i = 0; i < (int)sv->lane.size(); i++)
+        if (sv->lane[i].h) PCG_TRY(lane_start(sv, sv->lane[i], i));
     for (Engine *e : sv->eng) {
         if (e->inflight) continue;
         PCG_TRY(admit(sv, e));
@@ -470,7 +559,7 @@ int amg_server_progress(amg_server sv, int wait, int *finished) {
 }
 
 int amg_server_result(amg_server sv, int64_t ticket, int *done, int *status, int *iters, double *true_rel,
-                      double *times) {
+                      int *lane, double *times) {
     set_error("");
     if (done) *done = 0;
     if (!sv) {
@@ -488,6 +577,7 @@ int amg_server_result(amg_server sv, int64_t ticket, int *done, int *status, int
     if (status) *status = r.status;
     if (iters) *iters = r.iters;
     if (true_rel) *true_rel = r.true_rel;
+    if (lane) *lane = r.lane;
     if (times) {
         times[0] = 1e3 * (r.t_start - r.t_submit);
         times[1] = 1e3 * (r.t_done - r.t_start);
@@ -499,6 +589,11 @@ int amg_server_result(amg_server sv, int64_t ticket, int *done, int *status, int
 
 void amg_server_destroy(amg_server sv) {
     if (!sv) return;
+    for (Lane &ln : sv->lane) {
+        if (ln.s) cudaStreamSynchronize(ln.s);
+        if (ln.ev) cudaEventDestroy(ln.ev);
+        if (ln.s) cudaStreamDestroy(ln.s);
+    }
     for (Engine *e : sv->eng) engine_free(e);
     delete sv;
 }

@@ -1016,6 +1016,55 @@ int ensure_hist(amg_hier *h, int maxit) {
     return AMG_OK;
 }
 
+// Serving lane. solve_prepare makes the whole-solve graph of `mode` (and a
+// history of maxit + 1) ready; solve_launch starts one solve on s without
+// waiting (b, x0: host or device, copied into h's own vectors) and copies the
+// final state to the pinned mirror; once s has passed it, solve_collect
+// writes x (host or device; zeros when b = 0) and the outcome.
+int solve_prepare(amg_hier *h, int mode, int maxit) {
+    PCG_TRY(ensure_hist(h, maxit));
+    if (!h->gexec[mode]) PCG_TRY(build_graph(h, mode));
+    return AMG_OK;
+}
+
+int solve_launch(amg_hier *h, int mode, const double *b, const double *x0, double rtol, int maxit, cudaStream_t s) {
+    int n = h->lev[0].A.n;
+    h->mem.stream = s;
+    PCG_TRY(solve_prepare(h, mode, maxit));
+    PCG_CK(cudaMemcpyAsync(h->b, b, sizeof(double) * n, cudaMemcpyDefault, s));
+    PCG_CK(cudaMemcpyAsync(h->x, x0, sizeof(double) * n, cudaMemcpyDefault, s));
+    Ctl c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.rtol = rtol;
+    c0.maxit = maxit;
+    c0.mode = mode;
+    c0.restart = 1;
+    *h->ctl_host = c0;
+    PCG_CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    PCG_CK(cudaGraphLaunch(h->gexec[mode], s));
+    PCG_CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    return AMG_OK;
+}
+
+int solve_collect(amg_hier *h, int mode, double *x, cudaStream_t s, int *status, int *iters, double *true_rel,
+                  int64_t *kernels) {
+    int n = h->lev[0].A.n;
+    const Ctl &c = *h->ctl_host;
+    if (c.done == 1 && c.bnorm == 0.0) {
+        k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->x, n);
+        PCG_LAUNCH_CK();
+    }
+    PCG_CK(cudaMemcpyAsync(x, h->x, sizeof(double) * n, cudaMemcpyDefault, s));
+    int64_t k = h->graph_prefix_kernels + (int64_t)c.bodies * h->graph_body_kernels[mode];
+    h->launches += k;
+    if (kernels) *kernels = k;
+    if (status) *status = c.done ? c.status : AMG_ERR_NOCONV;
+    if (iters) *iters = c.iter;
+    if (true_rel) *true_rel = c.true_rel;
+    h->last_true_rel = c.true_rel;
+    return AMG_OK;
+}
+
 int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, int *iters, double *res_hist,
                cudaStream_t s) {
     if (!b || !x || !(rtol >= 0.0) || maxit < 0) {

@@ -52,11 +52,13 @@ def prepare_meshes(sizes=(64, 128, 192), ratio: float = 1.04, seed: int = 5, poo
     return meshes
 
 
-def make_server(meshes: list[Mesh], mode: str, slots: int = 8, max_engines: int = 2, chunk: int = 4,
-                hbm_budget: int = 0, queue_cap: int = 1 << 20, rtol: float = 1e-8, maxit: int = 1000) -> B.Server:
+def make_server(meshes: list[Mesh], mode: str, slots: int = 4, max_engines: int = 2, chunk: int = 4,
+                hbm_budget: int = 0, queue_cap: int = 1 << 20, rtol: float = 1e-8, maxit: int = 1000,
+                solo: bool = True, batch_min: int = 3, lane_priority: bool = False) -> B.Server:
     loads = [float(m.problem.A.n) for m in meshes]
     return B.Server([m.amg for m in meshes], mode=mode, slots=slots, max_engines=max_engines, chunk=chunk,
-                    queue_cap=queue_cap, rtol=rtol, maxit=maxit, hbm_budget=hbm_budget, loads=loads)
+                    queue_cap=queue_cap, rtol=rtol, maxit=maxit, hbm_budget=hbm_budget, loads=loads, solo=solo,
+                    batch_min=batch_min, lane_priority=lane_priority)
 
 
 def run_stream(server: B.Server, meshes: list[Mesh], rate: float, count: int, seed: int = 5) -> dict:
@@ -67,7 +69,7 @@ def run_stream(server: B.Server, meshes: list[Mesh], rate: float, count: int, se
     which = W.uniform_choices(count, len(meshes), seed)
     used = [0] * len(meshes)
     outstanding: dict[int, tuple[int, float]] = {}
-    lat, iters, rels, statuses, queue_ms = [], [], [], [], []
+    lat, iters, rels, statuses, queue_ms, lanes = [], [], [], [], [], []
     rejected = 0
     nxt = 0
     torch.cuda.synchronize()
@@ -100,6 +102,7 @@ def run_stream(server: B.Server, meshes: list[Mesh], rate: float, count: int, se
             rels.append(r.true_rel)
             statuses.append(r.status)
             queue_ms.append(r.queue_ms)
+            lanes.append(r.lane)
             t_last = tnow
             if t_first_done is None:
                 t_first_done = tnow
@@ -116,26 +119,80 @@ def run_stream(server: B.Server, meshes: list[Mesh], rate: float, count: int, se
         "p50_ms": float(np.percentile(lat_a, 50)),
         "p99_ms": float(np.percentile(lat_a, 99)),
         "mean_queue_ms": float(np.mean(queue_ms)) if queue_ms else 0.0,
+        "in_lane": int(len(lanes) - sum(lanes)),
         "mean_iters": float(np.mean(iters)) if iters else 0.0,
         "max_true_rel": float(np.max(rels)) if rels else 0.0,
         "all_ok": bool(statuses) and all(s == B.OK for s in statuses),
     }
 
 
+def run_sequential(meshes: list[Mesh], mode: str, rate: float, count: int, seed: int = 5,
+                   rtol: float = 1e-8, maxit: int = 1000) -> dict:
+    """The same request stream served one request at a time by pcg_solve
+    (first come, first served, no batching): the plain solver as a server."""
+    import torch
+    arrivals = W.poisson_arrivals(rate, count, seed)
+    which = W.uniform_choices(count, len(meshes), seed)
+    used = [0] * len(meshes)
+    for m in meshes:
+        m.amg.set_mode(mode)
+    lat, iters, rels = [], [], []
+    ok = True
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    try:
+        for k in range(count):
+            while time.perf_counter() - t0 < arrivals[k]:
+                pass
+            m = int(which[k])
+            b, x0 = meshes[m].steps[used[m] % len(meshes[m].steps)]
+            used[m] += 1
+            x = x0.clone()
+            r = meshes[m].amg.solve(b, x, rtol=rtol, maxit=maxit, hist=False)
+            lat.append(1e3 * (time.perf_counter() - t0 - arrivals[k]))
+            iters.append(r.iters)
+            rels.append(r.true_rel)
+            ok = ok and r.status == B.OK
+    finally:
+        for m in meshes:
+            m.amg.set_mode("fcg32")
+    span = time.perf_counter() - t0
+    lat_a = np.asarray(lat)
+    return {"rate": None if not np.isfinite(rate) else rate, "requests": count, "completed": count,
+            "span_s": span, "solves_per_s": count / span, "p50_ms": float(np.percentile(lat_a, 50)),
+            "p99_ms": float(np.percentile(lat_a, 99)), "mean_iters": float(np.mean(iters)),
+            "max_true_rel": float(np.max(rels)), "all_ok": ok}
+
+
 def serve_modes(meshes: list[Mesh], count: int, load_fraction: float = 0.7, seed: int = 5, **server_kw) -> dict:
-    """For each mode: saturated throughput (every request queued at t = 0),
-    then latency at ``load_fraction`` of that throughput."""
-    out = {}
-    for mode in ("fcg32", "pcg64"):
+    """Three servers on the same request streams:
+
+    * ``fp64_plain``: one request at a time through pcg_solve in float64 PCG;
+    * ``fp64``: the batching server in float64 PCG;
+    * ``mixed``: the batching server with the float32 V-cycle in FCG(1).
+
+    Each is run saturated (every request queued at t = 0: throughput), at a
+    common arrival rate of ``load_fraction`` times the plain server's
+    saturated throughput (latency, all three stable), and the batching
+    servers also at ``load_fraction`` of their own saturated throughput."""
+    rtol = server_kw.get("rtol", 1e-8)
+    maxit = server_kw.get("maxit", 1000)
+    run_sequential(meshes, "pcg64", float("inf"), max(8, count // 8), seed + 1, rtol, maxit)   # warm-up
+    plain_sat = run_sequential(meshes, "pcg64", float("inf"), count, seed, rtol, maxit)
+    common = load_fraction * plain_sat["solves_per_s"]
+    out = {"common_rate": common,
+           "fp64_plain": {"saturated": plain_sat,
+                          "at_common_rate": run_sequential(meshes, "pcg64", common, count, seed + 2, rtol, maxit)}}
+    for name, mode in (("mixed", "fcg32"), ("fp64", "pcg64")):
         srv = make_server(meshes, mode, **server_kw)
         try:
             run_stream(srv, meshes, float("inf"), max(8, count // 8), seed + 1)       # warm-up
             sat = run_stream(srv, meshes, float("inf"), count, seed)
-            rate = load_fraction * sat["solves_per_s"]
-            lat = run_stream(srv, meshes, rate, count, seed + 2)
+            at_common = run_stream(srv, meshes, common, count, seed + 2)
+            at_own = run_stream(srv, meshes, load_fraction * sat["solves_per_s"], count, seed + 3)
         finally:
             srv.close()
-        out[mode] = {"saturated": sat, "at_load": lat}
+        out[name] = {"saturated": sat, "at_common_rate": at_common, "at_own_load": at_own}
     return out
 
 
@@ -143,19 +200,24 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--sizes", type=int, nargs="+", default=[64, 128, 192])
     ap.add_argument("--count", type=int, default=400)
-    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--engines", type=int, default=2)
     ap.add_argument("--chunk", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=0.0)
+    ap.add_argument("--no-solo", action="store_true", help="engines only, no whole-solve lanes")
+    ap.add_argument("--batch-min", type=int, default=3)
     ap.add_argument("--rates", type=float, nargs="*", default=[],
                     help="arrival rates to sweep (per s); default: saturation and 70%% of it")
     a = ap.parse_args(argv)
     meshes = prepare_meshes(tuple(a.sizes))
-    kw = dict(slots=a.slots, max_engines=a.engines, chunk=a.chunk, hbm_budget=int(a.budget_gb * 2 ** 30))
+    kw = dict(slots=a.slots, max_engines=a.engines, chunk=a.chunk, hbm_budget=int(a.budget_gb * 2 ** 30),
+              solo=not a.no_solo, batch_min=a.batch_min)
     if not a.rates:
         print(json.dumps(serve_modes(meshes, a.count, **kw)))
         return
     for mode in ("fcg32", "pcg64"):
+        for rate in a.rates:
+            print(json.dumps({"mode": mode, "server": "plain", **run_sequential(meshes, mode, rate, a.count)}))
         srv = make_server(meshes, mode, **kw)
         try:
             for rate in a.rates:

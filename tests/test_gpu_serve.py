@@ -4,7 +4,8 @@ A request's result must not depend on what it shares the device with: the
 same request served alone and in a mix (other meshes, other slots, other
 engines, admitted while others are mid-solve) gives the same x bit for bit,
 and it equals the matching column of pcg_solve_multi with the same slot
-count. Each result also meets the single-solve bar against the oracle
+count; a request that ran in a whole-solve lane equals pcg_solve bit for
+bit. Each result also meets the single-solve bar against the oracle
 (iterations within +-1, true residual <= rtol, ||x - x_oracle|| <= 1e-6
 ||x_oracle||). Budget admission, the queue cap and the special requests
 (b = 0, a converged x0, maxit exhausted, host buffers) are covered too.
@@ -37,9 +38,20 @@ def _serve_alone(srv, m, b, x0):
     return x, r
 
 
+def _lone_solve(mesh, mode, b, x0):
+    mesh.amg.set_mode(mode)
+    x = x0.clone()
+    r = mesh.amg.solve(b, x, rtol=RTOL, hist=False)
+    mesh.amg.set_mode("fcg32")
+    return x, r
+
+
+@pytest.mark.parametrize("solo", [False, True])
 @pytest.mark.parametrize("mode", ["fcg32", "pcg64"])
-def test_alone_and_in_the_mix_are_identical(meshes, mode):
-    srv = S.make_server(meshes, mode, slots=4, max_engines=2, chunk=3)
+def test_alone_and_in_the_mix_are_identical(meshes, mode, solo):
+    """Engine slots: the same bits alone and in the mix. Whole-solve lanes:
+    the same bits as pcg_solve. Which of the two a request got is reported."""
+    srv = S.make_server(meshes, mode, slots=4, max_engines=2, chunk=3, solo=solo)
     reqs = [(i % 3, (i // 3) % 3) for i in range(16)]
     xs, tickets = [], []
     for j, (m, k) in enumerate(reqs):
@@ -53,13 +65,23 @@ def test_alone_and_in_the_mix_are_identical(meshes, mode):
             srv.progress(wait=True)
     res = srv.drain(tickets)
     assert srv.info()["running"] == 0 and srv.info()["queued"] == 0
+    lanes = [res[t].lane for t in tickets]
+    if solo:
+        assert 0 in lanes and 1 in lanes
+    else:
+        assert set(lanes) == {1}
+    alone = S.make_server(meshes, mode, slots=4, max_engines=1, chunk=3, solo=False)
     for j, (m, k) in enumerate(reqs):
         r = res[tickets[j]]
         assert r.status == B.OK and r.true_rel <= RTOL
         b, x0 = meshes[m].steps[k]
-        xa, ra = _serve_alone(srv, m, b, x0)
-        assert torch.equal(xa, xs[j]), (j, m, k, float((xa - xs[j]).abs().max()))
+        if r.lane == 1:
+            xa, ra = _serve_alone(alone, m, b, x0)
+        else:
+            xa, ra = _lone_solve(meshes[m], mode, b, x0)
+        assert torch.equal(xa, xs[j]), (j, m, k, r.lane, float((xa - xs[j]).abs().max()))
         assert ra.iters == r.iters
+    alone.close()
     # against the oracle from the same warm start (one request per mesh)
     for m in range(3):
         b, x0 = meshes[m].steps[0]
@@ -74,10 +96,23 @@ def test_alone_and_in_the_mix_are_identical(meshes, mode):
     srv.close()
 
 
+def test_lane_and_slot_results_agree_within_tolerance(meshes):
+    """The same request in a lane and in a slot: both meet rtol and differ
+    by summation order only."""
+    for m in range(3):
+        b, x0 = meshes[m].steps[1]
+        xl, rl = _lone_solve(meshes[m], "fcg32", b, x0)
+        srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1, solo=False)
+        xs, rs = _serve_alone(srv, m, b, x0)
+        srv.close()
+        assert abs(rl.iters - rs.iters) <= 1
+        assert (xl - xs).norm().item() <= 1e-6 * xl.norm().item()
+
+
 def test_requests_join_an_engine_mid_solve(meshes):
     """Two requests start, two more join the same engine between chunks while
     the first two are still iterating; all four equal their solo results."""
-    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1, chunk=2)
+    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1, chunk=2, solo=False)
     m = 2
     xs, tickets = [], []
     for k in (0, 1):
@@ -116,7 +151,7 @@ def test_served_equals_multi_column(meshes, mode):
     st, it, _, sts, _ = mesh.amg.solve_multi(Bm, X, rtol=RTOL)
     mesh.amg.set_mode("fcg32")
     assert st == 0
-    srv = S.make_server(meshes, mode, slots=4, max_engines=1, chunk=5)
+    srv = S.make_server(meshes, mode, slots=4, max_engines=1, chunk=5, solo=False)
     xs, tickets = [], []
     for c in range(4):
         x = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -155,7 +190,7 @@ def test_budget_admission(meshes):
 
 
 def test_queue_cap(meshes):
-    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1, queue_cap=2)
+    srv = S.make_server(meshes, "fcg32", slots=4, max_engines=1, queue_cap=2, solo=False)
     b, x0 = meshes[0].steps[0]
     outs = [torch.empty_like(b) for _ in range(3)]
     assert srv.submit(0, b, x0, outs[0])[0] == B.OK
