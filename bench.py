@@ -521,7 +521,9 @@ def run_ours(args):
             if cnt == 0:
                 continue
             entry = {"avg_ms": ms / cnt, "launches": cnt, "share_of_profiled": ms / prof[mode]["total_ms"]}
-            if k != "coarse_levels":
+            if k == "residual":
+                entry["note"] = "runs a full sweep only when the recursive residual met rtol; other launches exit"
+            elif k != "coarse_levels":
                 bl = algorithmic_bytes(k, mode, n0, nnz0, n1, ib0)
                 entry["algorithmic_bytes"] = bl
                 entry["gbs"] = bl / (ms / cnt * 1e-3) / 1e9

@@ -34,6 +34,35 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
     } while (0)
 #define PCG_LAUNCH_CK() PCG_CK(cudaGetLastError())
 
+// -------------------------------------------- programmatic dependent launch
+// A solve kernel launched with launch_k(pdl = true, ...) may be scheduled
+// while the kernel before it on the stream is still running. It calls
+// pdl_enter() first: that waits until the preceding kernel has completed and
+// its writes are visible, then lets the next kernel be scheduled. So the
+// order of memory effects is that of plain stream order; only the launch
+// and block scheduling of the next kernel overlap the tail of this one.
+// Without the launch attribute both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // -------------------------------------------------------------- allocator
 // Device allocations of one handle: every pointer is tracked with its size
 // so the handle can free everything and enforce its byte budget.
@@ -213,13 +242,13 @@ struct amg_hier {
     int graph_body_kernels[2] = {0, 0};
     int use_graph = 1;
     int no_col16 = 0;
+    int pdl = 1;  // programmatic dependent launch between solve kernels
     int graph_gen = 0;       // bumped whenever captured graphs go stale
-    // fused tail: levels tail_first..L run in one cooperative kernel
+    // cluster tail: levels tail_first..L run in one thread-block cluster
     int tail_first = 0;      // 0 = no tail (every level launched separately)
-    int tail_grid = 0;
+    int tail_ctas = 0;       // CTAs of the cluster
     pcgamg::TailLevel<float> *tail32 = nullptr;
     pcgamg::TailLevel<double> *tail64 = nullptr;
-    unsigned *tail_bar = nullptr;  // grid barrier: arrivals, generation
     // multi right-hand-side solves
     pcgamg::MultiWS multi;
     int multi_k = 0;

@@ -28,24 +28,70 @@ __device__ __forceinline__ X ld_mat(const X *p) {
 __device__ __forceinline__ int col_of(int32_t c, int) { return c; }
 __device__ __forceinline__ int col_of(int16_t c, int row) { return row + (int)c; }
 
+// Column/value loads of entries k..k+U-1 of a row (masked past w: column =
+// row, value 0, never used).
+template <int U, bool STREAM, typename IDX, typename T>
+__device__ __forceinline__ void sell_chunk(const IDX *__restrict__ c, const T *__restrict__ a, int k, int w, int row,
+                                           int (&j)[U], T (&v)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        if (k + u < w) {
+            j[u] = col_of(ld_mat<STREAM>(c + 32 * (k + u)), row);
+            v[u] = ld_mat<STREAM>(a + 32 * (k + u));
+        } else {
+            j[u] = row;
+            v[u] = T(0);
+        }
+    }
+}
+
+// Entries are summed one by one in storage order (acc += a_k x(j_k)), so
+// the result does not depend on U or on the pipelining. For U <= 4 (large
+// levels) the column/value loads of the next chunk are issued before the
+// FMAs of the current one, so a chunk costs about one dependent round trip
+// (its gathers) instead of two, and the last, partial chunk is loaded as one
+// masked chunk. U = 16 (small levels) loads whole chunks, then the rest one
+// entry at a time (its registers allow no second buffer).
 template <int U, bool STREAM, typename IDX, typename T, typename F>
 __device__ __forceinline__ T sell_row(const IDX *__restrict__ c, const T *__restrict__ a, int w, int row, F xval) {
     T acc = 0;
-    int k = 0;
-    for (; k + U <= w; k += U) {
+    if constexpr (U <= 4) {
         int j[U];
-        T v[U], x[U];
+        T v[U];
+        sell_chunk<U, STREAM>(c, a, 0, w, row, j, v);
+        for (int k = 0; k < w; k += U) {
+            T x[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            j[u] = col_of(ld_mat<STREAM>(c + 32 * (k + u)), row);
-            v[u] = ld_mat<STREAM>(a + 32 * (k + u));
+            for (int u = 0; u < U; u++) x[u] = (k + u < w) ? xval(j[u]) : T(0);
+            int jn[U];
+            T vn[U];
+            sell_chunk<U, STREAM>(c, a, k + U, w, row, jn, vn);
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (k + u < w) acc += v[u] * x[u];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                j[u] = jn[u];
+                v[u] = vn[u];
+            }
         }
+    } else {
+        int k = 0;
+        for (; k + U <= w; k += U) {
+            int j[U];
+            T v[U], x[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) x[u] = xval(j[u]);
+            for (int u = 0; u < U; u++) {
+                j[u] = col_of(ld_mat<STREAM>(c + 32 * (k + u)), row);
+                v[u] = ld_mat<STREAM>(a + 32 * (k + u));
+            }
 #pragma unroll
-        for (int u = 0; u < U; u++) acc += v[u] * x[u];
+            for (int u = 0; u < U; u++) x[u] = xval(j[u]);
+#pragma unroll
+            for (int u = 0; u < U; u++) acc += v[u] * x[u];
+        }
+        for (; k < w; k++) acc += ld_mat<STREAM>(a + 32 * k) * xval(col_of(ld_mat<STREAM>(c + 32 * k), row));
     }
-    for (; k < w; k++) acc += ld_mat<STREAM>(a + 32 * k) * xval(col_of(ld_mat<STREAM>(c + 32 * k), row));
     return acc;
 }
 

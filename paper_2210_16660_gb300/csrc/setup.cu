@@ -750,6 +750,8 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
     // PCGAMG_COL16=0 keeps int32 columns on every level.
     const char *c16 = getenv("PCGAMG_COL16");
     if (c16 && c16[0] == '0') h->no_col16 = 1;
+    const char *pd = getenv("PCGAMG_PDL");
+    if (pd && pd[0] == '0') h->pdl = 0;
     if (!A || A->n <= 0 || A->n >= (int64_t)1 << 31 || A->nnz < A->n || A->nnz >= (int64_t)1 << 31 ||
         !A->row_ptr || !A->col || !A->val) {
         set_error("amg_setup: bad CSR sizes or NULL arrays");

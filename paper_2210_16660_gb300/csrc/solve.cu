@@ -34,8 +34,12 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
 #include "sell_row.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pcgamg {
 
@@ -131,6 +135,7 @@ __global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_down(
     int n, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
     const T *__restrict__ xpre, const T *__restrict__ b, const T *__restrict__ p, T *__restrict__ t,
     const Ctl *__restrict__ ctl) {
+    pdl_enter();
     if (ctl->done) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         SELL_ROW_BEGIN
@@ -144,6 +149,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong(int n, const T *__restrict__ xpre, const T *__restrict__ p,
                                                     const int32_t *__restrict__ agg, const T *__restrict__ xc,
                                                     T *__restrict__ xp, const Ctl *__restrict__ ctl) {
+    pdl_enter();
     if (ctl->done) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         T x = ldg(xpre + i);
@@ -161,6 +167,7 @@ __global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_post(
     int n, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
     const T *__restrict__ xp, const T *__restrict__ b, const T *__restrict__ dinv, TZ *__restrict__ z,
     const double *__restrict__ r64, const double *__restrict__ qold, double *partials, Ctl *ctl) {
+    pdl_enter();
     if (ctl->done) return;
     double rz = 0.0, zq = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -190,6 +197,7 @@ __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t *__re
                                                      const int32_t *__restrict__ ridx, const T *__restrict__ t,
                                                      TO *__restrict__ bc, const T *__restrict__ dinvc,
                                                      T *__restrict__ xprec, const Ctl *__restrict__ ctl) {
+    pdl_enter();
     if (ctl->done) return;
     int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
@@ -204,6 +212,7 @@ template <typename TO>
 __global__ void __launch_bounds__(kBlock) k_coarse(int nL, const double *__restrict__ ainv,
                                                    const double *__restrict__ bL, TO *__restrict__ xL,
                                                    const Ctl *__restrict__ ctl) {
+    pdl_enter();
     if (ctl->done) return;
     int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (row >= nL) return;
@@ -222,6 +231,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_only(int n, const double *__r
                                                         const double *__restrict__ r, double *__restrict__ z,
                                                         const double *__restrict__ qold, double *partials,
                                                         Ctl *ctl) {
+    pdl_enter();
     if (ctl->done) return;
     double rz = 0.0, zq = 0.0;
     int lane = threadIdx.x & 31;
@@ -254,6 +264,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_only(int n, const double *__r
 // p = z + beta p (beta = 0 on a restart gives p = z).
 __global__ void __launch_bounds__(kBlock) k_axpy_p(int n, const double *__restrict__ z, double *__restrict__ p,
                                                    const Ctl *__restrict__ ctl) {
+    pdl_enter();
     if (ctl->done) return;
     double beta = ctl->beta;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -266,6 +277,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int32_t *__rest
                                                     const IDX *__restrict__ col, const double *__restrict__ val,
                                                     const double *__restrict__ p, double *__restrict__ q,
                                                     double *partials, Ctl *ctl) {
+    pdl_enter();
     if (ctl->done) return;
     double pq = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -316,6 +328,7 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, const double *__restri
                                                    const double *__restrict__ q, double *__restrict__ x,
                                                    double *__restrict__ r, REmit em, double *partials, Ctl *ctl,
                                                    double *hist) {
+    pdl_enter();
     if (ctl->done) return;
     double alpha = ctl->alpha;
     double rr = 0.0;
@@ -354,6 +367,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_residual(int n, const int32_t *__
                                                         const double *__restrict__ val, const double *__restrict__ b,
                                                         const double *__restrict__ x, double *__restrict__ r,
                                                         REmit em, double *partials, Ctl *ctl, double *hist) {
+    pdl_enter();
     if (ctl->done) return;
     if (!INIT && !ctl->check) return;
     double rr = 0.0, bb = 0.0;
@@ -421,46 +435,21 @@ __global__ void k_set_cond(cudaGraphConditionalHandle hc, Ctl *ctl, int count_bo
 inline int grid_rows(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
 
-// ------------------------------------------------------------ fused tail
-// Levels with few rows are latency-bound: a separate launch per sweep costs
-// more than the sweep. The tail runs every V-cycle phase of levels
-// tail_first..L in one cooperative launch (one block per SM, guaranteed
-// co-resident), phases separated by a grid barrier:
+// ------------------------------------------------------------ cluster tail
+// Levels with few rows are latency-bound: a launch per sweep costs more than
+// the sweep. The tail runs every V-cycle phase of levels tail_first..L in one
+// launch of a single thread-block cluster (h->tail_ctas CTAs, co-scheduled by
+// the hardware, one per SM), phases separated by the cluster barrier:
 //   down_l, restrict_l (l = first..L-1), coarse solve, then
 //   prolong+post_l (l = L-1..first, prolongation formed per entry).
-// Data written in one phase and read in a later one is loaded with __ldcg
-// (L2, coherent across SMs); read-only data with __ldg.
+// The barrier's release/acquire semantics at cluster scope make the global
+// writes of one phase visible to every CTA of the cluster in the next; data
+// written in one phase and read in a later one is loaded with __ldcg (L2),
+// read-only data with __ldg. Every thread passes the same sequence of
+// barriers (the loop bounds are kernel arguments, the early exit reads a
+// value no thread of this launch writes), so no barrier is left waiting.
 constexpr int kTailThreads = 512;
-constexpr int kTailRows = 40000;
-constexpr unsigned kBarrierSpins = 1u << 22;
-
-// Grid-wide barrier: arrival counter + generation word, bounded spin.
-// Returns false (in every thread of the block) when the wait gave up.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned *gen = bar + 1;
-        unsigned g = *gen;
-        __threadfence();
-        unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned spins = 0;
-            while (*gen == g) {
-                if (++spins > kBarrierSpins) { ok = 0; break; }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
+constexpr int kTailRows = 12000;
 
 template <typename T, typename IDX, typename F>
 __device__ __forceinline__ T tail_row(int i, const int32_t *sptr, const IDX *col, const T *val, F xval) {
@@ -498,17 +487,17 @@ __device__ __forceinline__ void tail_up(const TailLevel<T> &L, const T *xc, int 
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__restrict__ lv, int nt,
                                                           const double *__restrict__ ainv, int nL, double *bL,
-                                                          Ctl *ctl, unsigned *bar) {
+                                                          const Ctl *__restrict__ ctl) {
+    pdl_enter();
+    cg::cluster_group cluster = cg::this_cluster();
     if (ctl->done) return;
     int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    bool ok = true;
-    for (int k = 0; k + 1 < nt && ok; k++) {
-        TailLevel<T> L = lv[k];
+    for (int k = 0; k + 1 < nt; k++) {
+        const TailLevel<T> L = lv[k];
         tail_down(L, tid, nth);
-        ok = grid_barrier(bar);
-        if (!ok) break;
+        cluster.sync();
         bool last = (k + 2 == nt);
-        TailLevel<T> C = lv[k + 1];
+        const TailLevel<T> C = lv[k + 1];
         for (int I = tid; I < L.nc; I += nth) {
             T sum = 0;
             for (int32_t q = __ldg(L.rptr + I); q < __ldg(L.rptr + I + 1); q++) sum += __ldcg(L.t + __ldg(L.ridx + q));
@@ -519,45 +508,72 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
                 C.xpre[I] = __ldg(C.dinv + I) * sum;
             }
         }
-        ok = grid_barrier(bar);
+        cluster.sync();
     }
-    if (ok) {
-        // coarsest: x_L = A_L^{-1} b_L, one warp per row
-        int warp = tid >> 5, nwarp = nth >> 5, lane = threadIdx.x & 31;
-        T *xL = lv[nt - 1].x;
-        for (int row = warp; row < nL; row += nwarp) {
-            const double *a = ainv + (int64_t)row * nL;
-            double sacc = 0.0;
-            for (int j = lane; j < nL; j += 32) sacc += __ldg(a + j) * __ldcg(bL + j);
+    // coarsest: x_L = A_L^{-1} b_L, one warp per row
+    int warp = tid >> 5, nwarp = nth >> 5, lane = threadIdx.x & 31;
+    T *xL = lv[nt - 1].x;
+    for (int row = warp; row < nL; row += nwarp) {
+        const double *a = ainv + (int64_t)row * nL;
+        double sacc = 0.0;
+        for (int j = lane; j < nL; j += 32) sacc += __ldg(a + j) * __ldcg(bL + j);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
-            if (lane == 0) xL[row] = (T)sacc;
-        }
-        ok = grid_barrier(bar);
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+        if (lane == 0) xL[row] = (T)sacc;
     }
-    for (int k = nt - 2; k >= 0 && ok; k--) {
+    cluster.sync();
+    for (int k = nt - 2; k >= 0; k--) {
         tail_up(lv[k], (const T *)lv[k + 1].x, tid, nth);
-        if (k > 0) ok = grid_barrier(bar);
-    }
-    if (!ok && threadIdx.x == 0) {
-        ctl->status = AMG_ERR_TIMEOUT;
-        ctl->done = 2;
+        if (k > 0) cluster.sync();
     }
 }
 
 template <typename T>
 int launch_tail(amg_hier *h, const TailLevel<T> *lv, int nt, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(h->tail_grid);
+    cfg.gridDim = dim3(h->tail_ctas);
     cfg.blockDim = dim3(kTailThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = h->tail_ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    PCG_CK(cudaLaunchKernelEx(&cfg, k_tail<T>, lv, nt, (const double *)h->Ainv, h->nL, h->bL, h->ctl, h->tail_bar));
+    cfg.numAttrs = h->pdl ? 2 : 1;
+    PCG_CK(cudaLaunchKernelEx(&cfg, k_tail<T>, lv, nt, (const double *)h->Ainv, h->nL, h->bL, (const Ctl *)h->ctl));
+    return AMG_OK;
+}
+
+// Largest cluster (16, else 8) of k_tail<T> that the device can schedule.
+template <typename T>
+int tail_cluster_size(int *ctas) {
+    *ctas = 0;
+    PCG_CK(cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    for (int c : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(kTailThreads);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_tail<T>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (n >= 1) {
+            *ctas = c;
+            return AMG_OK;
+        }
+    }
     return AMG_OK;
 }
 
@@ -649,7 +665,8 @@ REmit remit(amg_hier *h) {
         }                                           \
     } while (0)
 
-// z = B r (one V-cycle in precision T), including rho / beta.
+// z = B r (one V-cycle in precision T), including rho / beta. Kernels are
+// launched with programmatic dependent launch when h->pdl (see pdl_enter).
 template <typename T, bool FCG>
 int launch_vcycle(amg_hier *h, cudaStream_t s) {
     using P = LP<T>;
@@ -658,10 +675,11 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     Ctl *ctl = h->ctl;
     Level &l0 = lev[0];
     const T *b0 = P::r0(h);
+    const bool pdl = h->pdl;
     int g0 = sizeof(T) == 4 ? h->grid32 : h->grid64;
     prof_begin(h, 0, s);
-    WITH_COLS(l0.S, (k_down<T, IDX, kUnroll, true><<<g0, kBlock, 0, s>>>(l0.A.n, l0.S.sptr, cols, P::val(l0),
-                                                                         P::xpre(l0), b0, P::p(l0), P::t(l0), ctl)));
+    WITH_COLS(l0.S, (launch_k(pdl, k_down<T, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n, l0.S.sptr, cols,
+                              P::val(l0), P::xpre(l0), b0, P::p(l0), P::t(l0), ctl)));
     prof_end(h, s);
     prof_begin(h, 5, s);
     // levels handled by separate launches: 0..F-1; the tail runs F..L
@@ -670,44 +688,45 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
         Level &lv = lev[l];
         int n = lv.A.n;
         if (l > 0 && n > kSmallRows)
-            WITH_COLS(lv.S, (k_down<T, IDX, kUnroll, false><<<grid_rows(n), kBlock, 0, s>>>(
-                                n, lv.S.sptr, cols, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl)));
+            WITH_COLS(lv.S, (launch_k(pdl, k_down<T, IDX, kUnroll, false>, grid_rows(n), kBlock, s, n, lv.S.sptr,
+                                      cols, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl)));
         else if (l > 0)
-            WITH_COLS(lv.S, (k_down<T, IDX, kUnrollSmall, false><<<grid_rows(n), kBlock, 0, s>>>(
-                                n, lv.S.sptr, cols, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl)));
+            WITH_COLS(lv.S, (launch_k(pdl, k_down<T, IDX, kUnrollSmall, false>, grid_rows(n), kBlock, s, n,
+                                      lv.S.sptr, cols, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl)));
         if (l + 1 == L)
-            k_restrict<T, double, false><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, P::t(lv),
-                                                                             h->bL, nullptr, nullptr, ctl);
+            launch_k(pdl, k_restrict<T, double, false>, grid_rows(lv.nc), kBlock, s, lv.nc, lv.rptr, lv.ridx,
+                     P::t(lv), h->bL, nullptr, nullptr, ctl);
         else
-            k_restrict<T, T, true><<<grid_rows(lv.nc), kBlock, 0, s>>>(lv.nc, lv.rptr, lv.ridx, P::t(lv),
-                                                                       P::b(lev[l + 1]), P::dinv(lev[l + 1]),
-                                                                       P::xpre(lev[l + 1]), ctl);
+            launch_k(pdl, k_restrict<T, T, true>, grid_rows(lv.nc), kBlock, s, lv.nc, lv.rptr, lv.ridx, P::t(lv),
+                     P::b(lev[l + 1]), P::dinv(lev[l + 1]), P::xpre(lev[l + 1]), ctl);
     }
     if (F < L) {
         PCG_TRY(launch_tail<T>(h, TailPick<T>::get(h), L - F + 1, s));
     } else {
-        k_coarse<T><<<(h->nL * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(h->nL, h->Ainv, h->bL, P::x(lev[L]), ctl);
+        launch_k(pdl, k_coarse<T>, (h->nL * 32 + kBlock - 1) / kBlock, kBlock, s, h->nL, h->Ainv, h->bL,
+                 P::x(lev[L]), ctl);
     }
     for (int l = F - 1; l >= 1; l--) {
         Level &lv = lev[l];
         int n = lv.A.n;
-        k_prolong<T><<<grid_rows(n), kBlock, 0, s>>>(n, P::xpre(lv), P::p(lv), lv.agg, P::x(lev[l + 1]), P::xp(lv),
-                                                     ctl);
+        launch_k(pdl, k_prolong<T>, grid_rows(n), kBlock, s, n, P::xpre(lv), P::p(lv), lv.agg, P::x(lev[l + 1]),
+                 P::xp(lv), ctl);
         if (n > kSmallRows)
-            WITH_COLS(lv.S, (k_post<T, T, false, false, IDX, kUnroll, false><<<grid_rows(n), kBlock, 0, s>>>(
-                                n, lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv), nullptr,
-                                nullptr, nullptr, ctl)));
+            WITH_COLS(lv.S, (launch_k(pdl, k_post<T, T, false, false, IDX, kUnroll, false>, grid_rows(n), kBlock, s,
+                                      n, lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv),
+                                      nullptr, nullptr, nullptr, ctl)));
         else
-            WITH_COLS(lv.S, (k_post<T, T, false, false, IDX, kUnrollSmall, false><<<grid_rows(n), kBlock, 0, s>>>(
-                                n, lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv), nullptr,
-                                nullptr, nullptr, ctl)));
+            WITH_COLS(lv.S, (launch_k(pdl, k_post<T, T, false, false, IDX, kUnrollSmall, false>, grid_rows(n),
+                                      kBlock, s, n, lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv),
+                                      P::x(lv), nullptr, nullptr, nullptr, ctl)));
     }
     prof_end(h, s);
     prof_begin(h, 1, s);
-    k_prolong<T><<<h->gridv, kBlock, 0, s>>>(l0.A.n, P::xpre(l0), P::p(l0), l0.agg, P::x(lev[1]), P::xp(l0), ctl);
-    WITH_COLS(l0.S, (k_post<T, double, true, FCG, IDX, kUnroll, true><<<g0, kBlock, 0, s>>>(
-                        l0.A.n, l0.S.sptr, cols, P::val(l0), P::xp(l0), b0, P::dinv(l0), h->z, h->r, h->q,
-                        h->partials, ctl)));
+    launch_k(pdl, k_prolong<T>, h->gridv, kBlock, s, l0.A.n, P::xpre(l0), P::p(l0), l0.agg, P::x(lev[1]),
+             P::xp(l0), ctl);
+    WITH_COLS(l0.S, (launch_k(pdl, k_post<T, double, true, FCG, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n,
+                              l0.S.sptr, cols, P::val(l0), P::xp(l0), b0, P::dinv(l0), h->z, h->r, h->q, h->partials,
+                              ctl)));
     prof_end(h, s);
     h->launches += (h->tail_first > 0) ? 4 * h->tail_first + 1 : 4 * L + 1;
     PCG_LAUNCH_CK();
@@ -719,9 +738,10 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
     int L = (int)h->lev.size() - 1;
     Level &l0 = h->lev[0];
     int n = l0.A.n;
+    const bool pdl = h->pdl;
     if (L == 0) {
-        k_coarse_only<MODE == AMG_MODE_FCG32, MODE == AMG_MODE_FCG32>
-            <<<h->gridv, kBlock, 0, s>>>(h->nL, h->Ainv, h->r, h->z, h->q, h->partials, h->ctl);
+        launch_k(pdl, k_coarse_only<MODE == AMG_MODE_FCG32, MODE == AMG_MODE_FCG32>, h->gridv, kBlock, s, h->nL,
+                 h->Ainv, h->r, h->z, h->q, h->partials, h->ctl);
         h->launches += 1;
     } else if (MODE == AMG_MODE_FCG32) {
         PCG_TRY((launch_vcycle<float, true>(h, s)));
@@ -729,18 +749,19 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
         PCG_TRY((launch_vcycle<double, false>(h, s)));
     }
     prof_begin(h, 6, s);
-    k_axpy_p<<<h->gridv, kBlock, 0, s>>>(n, h->z, h->p, h->ctl);
+    launch_k(pdl, k_axpy_p, h->gridv, kBlock, s, n, h->z, h->p, h->ctl);
     prof_end(h, s);
     prof_begin(h, 2, s);
-    WITH_COLS(l0.S, (k_spmv<IDX><<<h->grid64, kBlock, 0, s>>>(n, l0.S.sptr, cols, l0.S.v64, h->p, h->q, h->partials,
-                                                               h->ctl)));
+    WITH_COLS(l0.S, (launch_k(pdl, k_spmv<IDX>, h->grid64, kBlock, s, n, l0.S.sptr, cols, l0.S.v64, h->p, h->q,
+                              h->partials, h->ctl)));
     prof_end(h, s);
     prof_begin(h, 3, s);
-    k_update<MODE><<<h->gridv, kBlock, 0, s>>>(n, h->p, h->q, h->x, h->r, remit(h), h->partials, h->ctl, h->hist);
+    launch_k(pdl, k_update<MODE>, h->gridv, kBlock, s, n, h->p, h->q, h->x, h->r, remit(h), h->partials, h->ctl,
+             h->hist);
     prof_end(h, s);
     prof_begin(h, 4, s);
-    WITH_COLS(l0.S, (k_residual<false, MODE, IDX><<<h->grid64, kBlock, 0, s>>>(
-                        n, l0.S.sptr, cols, l0.S.v64, h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
+    WITH_COLS(l0.S, (launch_k(pdl, k_residual<false, MODE, IDX>, h->grid64, kBlock, s, n, l0.S.sptr, cols, l0.S.v64,
+                              h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
     prof_end(h, s);
     h->launches += 4;
     PCG_LAUNCH_CK();
@@ -757,13 +778,12 @@ int launch_prefix(amg_hier *h, cudaStream_t s) {
     int n = l0.A.n;
     k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->p, n);
     k_zero<<<grid_rows(n), kBlock, 0, s>>>(h->q, n);
-    if (h->tail_bar) PCG_CK(cudaMemsetAsync(h->tail_bar, 0, 2 * sizeof(unsigned), s));
     if (h->mode == AMG_MODE_FCG32)
-        WITH_COLS(l0.S, (k_residual<true, AMG_MODE_FCG32, IDX><<<h->grid64, kBlock, 0, s>>>(
-                            n, l0.S.sptr, cols, l0.S.v64, h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
+        WITH_COLS(l0.S, (launch_k(h->pdl, k_residual<true, AMG_MODE_FCG32, IDX>, h->grid64, kBlock, s, n, l0.S.sptr,
+                                  cols, l0.S.v64, h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
     else
-        WITH_COLS(l0.S, (k_residual<true, AMG_MODE_PCG64, IDX><<<h->grid64, kBlock, 0, s>>>(
-                            n, l0.S.sptr, cols, l0.S.v64, h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
+        WITH_COLS(l0.S, (launch_k(h->pdl, k_residual<true, AMG_MODE_PCG64, IDX>, h->grid64, kBlock, s, n, l0.S.sptr,
+                                  cols, l0.S.v64, h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
     h->launches += 3;
     PCG_LAUNCH_CK();
     return AMG_OK;
@@ -884,11 +904,11 @@ bool is_device_ptr(const void *p) {
 
 }  // namespace
 
-// Fused tail: the first level (>= 1) with at most kTailRows rows through the
+// Cluster tail: the first level (>= 1) with at most kTailRows rows through the
 // coarsest, when at least one level lies between it and the coarsest.
-// Opt-in with PCGAMG_TAIL=1: inside the whole-solve graph a cooperative
-// kernel node measured slower on GB300 than the separate launches it
-// replaces, so the default keeps one launch per sweep.
+// Opt-in with PCGAMG_TAIL=1: inside the whole-solve graph the separate
+// launches it replaces cost about as much on GB300 (128^3: the same solve
+// rate with float32 levels, 2.6% slower with float64 levels).
 int setup_tail(amg_hier *h) {
     int L = (int)h->lev.size() - 1;
     h->tail_first = 0;
@@ -898,15 +918,12 @@ int setup_tail(amg_hier *h) {
     for (int l = 1; l < L; l++)
         if (h->lev[l].A.n <= kTailRows) { F = l; break; }
     if (F == 0) return AMG_OK;
-    int dev = h->device, sms = 0, per = 0, coop = 0;
-    PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PCG_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    if (!coop) return AMG_OK;
-    PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tail<double>, kTailThreads, 0));
-    int per32 = 0;
-    PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, k_tail<float>, kTailThreads, 0));
-    if (per < 1 || per32 < 1) return AMG_OK;
-    h->tail_grid = sms;
+    int c32 = 0, c64 = 0;
+    PCG_TRY(tail_cluster_size<float>(&c32));
+    PCG_TRY(tail_cluster_size<double>(&c64));
+    int ctas = c32 < c64 ? c32 : c64;
+    if (ctas < 1) return AMG_OK;
+    h->tail_ctas = ctas;
     int nt = L - F + 1;
     std::vector<TailLevel<float>> t32(nt);
     std::vector<TailLevel<double>> t64(nt);
@@ -933,10 +950,8 @@ int setup_tail(amg_hier *h) {
     Mem &M = h->mem;
     PCG_TRY(alloc(M, &h->tail32, nt));
     PCG_TRY(alloc(M, &h->tail64, nt));
-    PCG_TRY(alloc(M, &h->tail_bar, 2));
     PCG_CK(cudaMemcpyAsync(h->tail32, t32.data(), sizeof(TailLevel<float>) * nt, cudaMemcpyHostToDevice, M.stream));
     PCG_CK(cudaMemcpyAsync(h->tail64, t64.data(), sizeof(TailLevel<double>) * nt, cudaMemcpyHostToDevice, M.stream));
-    PCG_CK(cudaMemsetAsync(h->tail_bar, 0, 2 * sizeof(unsigned), M.stream));
     PCG_CK(cudaStreamSynchronize(M.stream));
     h->tail_first = F;
     return AMG_OK;
