@@ -49,7 +49,7 @@ extern "C" {
 #define AMG_ERR_NOCONV 4    /* maxit V-cycles without meeting rtol; x = last iterate */
 #define AMG_ERR_NAN 5       /* NaN or Inf in the iteration */
 #define AMG_ERR_CUDA 6      /* a CUDA runtime call failed */
-#define AMG_ERR_TIMEOUT 7   /* a bounded device-side wait expired */
+#define AMG_ERR_TIMEOUT 7   /* reserved: no kernel waits on another, no call returns it */
 #define AMG_ERR_COARSE 8    /* coarsening stalled with more than 4096 rows left */
 #define AMG_ERR_BUSY 9      /* serving: the request queue is full */
 
