@@ -61,6 +61,7 @@ def parse_args(argv=None):
     ap.add_argument("--serve-chunk", type=int, default=4)
     ap.add_argument("--serve-batch-min", type=int, default=3)
     ap.add_argument("--serve-no-solo", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the fixed sweep launch shapes")
     return ap.parse_args(argv)
 
 
@@ -347,6 +348,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     amg = B.AMG.from_csr(prob.A, mode="fcg32", stream=stream)
     setup = amg.setup_times()
+    tune = {"enabled": not args.no_autotune}
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tune["changed"] = amg.autotune(reps=10, stream=stream)
+        tune["ms"] = 1e3 * (time.perf_counter() - t0)
+        tune["shapes"] = [amg.level_shape(lvl) for lvl in range(len(amg.info()))]
     levels = amg.info()
     bs = [torch.from_numpy(b).to(device) for b in rhs]
     x = torch.zeros(prob.A.n, dtype=torch.float64, device=device)
@@ -404,6 +411,9 @@ def run_ours(args):
         sizes = W.batch_sizes(args.batch_count, 24, 112, seed=3)
         bprobs = [W.make_problem(Nn, args.ratio, seed=3000 + k) for k, Nn in enumerate(sizes)]
         bamgs = [B.AMG.from_csr(p.A, mode="fcg32", stream=stream) for p in bprobs]
+        if not args.no_autotune:
+            for a in bamgs:
+                a.autotune(reps=10, stream=stream)
         bb = [torch.from_numpy(p.b).to(device) for p in bprobs]
         bx = [torch.zeros_like(v) for v in bb]
         bt = B.Batch(bamgs)
@@ -447,6 +457,9 @@ def run_ours(args):
     if args.serve_count > 0:
         from paper_2210_16660_gb300 import serving as SV
         meshes = SV.prepare_meshes(tuple(args.serve_sizes), ratio=args.ratio, seed=5, pool=4, device=device)
+        if not args.no_autotune:
+            for mm in meshes:
+                mm.amg.autotune(reps=10, stream=stream)
         kw = dict(slots=args.serve_slots, max_engines=args.serve_engines, chunk=args.serve_chunk,
                   rtol=args.rtol, maxit=args.maxit, solo=not args.serve_no_solo, batch_min=args.serve_batch_min)
         srv = SV.make_server(meshes, "fcg32", **kw)
@@ -565,6 +578,7 @@ def run_ours(args):
                      "latency_ms": {"p50": pct(f64["lat_ms"], 50), "p99": pct(f64["lat_ms"], 99)},
                      "iters": statistics.median(f64["iters"]), "gpu_launches": f64["launches"]},
             "setup_ms": setup,
+            "autotune": tune,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline,
             "kernels": per_kernel,

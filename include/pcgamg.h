@@ -268,6 +268,30 @@ int amg_server_result(amg_server s, int64_t ticket, int *done, int *status, int 
 /* Waits for running chunks and frees every engine (not the hierarchies). */
 void amg_server_destroy(amg_server s);
 
+/* Launch-shape tuner (no counterpart in the paper: it picks how the sweeps
+ * are launched on this device, not what they compute). For every level
+ * l >= 1 with sweeps, each V-cycle precision and each of the down and post
+ * sweeps, it times four launch shapes -- rows loading 4 or 16 entries per
+ * chunk, times a one-wave grid-stride grid or one thread per row -- `reps`
+ * launches each (reps < 1: 1) on `stream`, and moves to the fastest when it
+ * beats the current shape by more than 3%. Every
+ * shape sums a row's entries in storage order, so solves give the same bits
+ * before and after tuning; only their speed changes. The level work vectors
+ * are overwritten; captured solve graphs are rebuilt on the next solve.
+ * *changed (may be NULL): shapes that differ from before. Call it between
+ * solves, not while a batch or server holding h is in use. */
+int amg_autotune(amg_handle h, int reps, int *changed, void *stream);
+
+/* Launch shapes of a level (4 ints: float down, float post, float64 down,
+ * float64 post; bit 0 = 16-entry chunks, bit 1 = one thread per row). Level
+ * 0's sweeps have a fixed shape and report 0. */
+int amg_level_shape(amg_handle h, int level, int *shape);
+
+/* Sets the launch shapes of level 1..L (same 4-int layout, values 0..3);
+ * for manual tuning and for tests that check every shape gives the same
+ * result. Errors: AMG_ERR_ARG. */
+int amg_set_level_shape(amg_handle h, int level, const int *shape);
+
 /* True relative residual ||b - A x|| / ||b|| at the end of the last solve on h. */
 double amg_last_true_residual(amg_handle h);
 

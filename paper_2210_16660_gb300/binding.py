@@ -27,7 +27,8 @@ EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode
            "amg_level_layout", "amg_residual_noalloc", "pcg_solve_multi", "amg_multi_info",
            "amg_batch_create", "pcg_solve_batch", "amg_batch_destroy", "amg_server_default_params",
            "amg_serve_plan", "amg_server_create", "amg_server_mesh_info", "amg_server_info", "amg_server_submit",
-           "amg_server_progress", "amg_server_result", "amg_server_destroy")
+           "amg_server_progress", "amg_server_result", "amg_server_destroy", "amg_autotune", "amg_level_shape",
+           "amg_set_level_shape")
 
 
 class AmgCsr(C.Structure):
@@ -124,6 +125,12 @@ def load(build_if_missing: bool = True):
     lib.amg_server_result.restype = I
     lib.amg_server_destroy.argtypes = [P]
     lib.amg_server_destroy.restype = None
+    lib.amg_autotune.argtypes = [P, I, C.POINTER(I), P]
+    lib.amg_autotune.restype = I
+    lib.amg_level_shape.argtypes = [P, I, P]
+    lib.amg_level_shape.restype = I
+    lib.amg_set_level_shape.argtypes = [P, I, P]
+    lib.amg_set_level_shape.restype = I
     lib.amg_destroy.argtypes = [P]
     lib.amg_destroy.restype = None
     lib.amg_last_error.argtypes = []
@@ -344,6 +351,29 @@ class AMG:
         cnt = np.zeros(7, np.int64)
         load().amg_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, 7)
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KINDS)}
+
+    def autotune(self, reps: int = 5, stream=None) -> int:
+        """``amg_autotune``: pick each level's fastest sweep launch shape; returns how many changed."""
+        c = C.c_int(0)
+        st = load().amg_autotune(self._h, reps, C.byref(c), _stream_ptr(stream))
+        if st:
+            raise AmgError(st, last_error())
+        return c.value
+
+    def level_shape(self, level: int) -> list[int]:
+        """``amg_level_shape``: [float down, float post, float64 down, float64 post]."""
+        out = np.zeros(4, np.int32)
+        st = load().amg_level_shape(self._h, level, out.ctypes.data)
+        if st:
+            raise AmgError(st, last_error())
+        return [int(v) for v in out]
+
+    def set_level_shape(self, level: int, shape) -> None:
+        """``amg_set_level_shape`` (levels 1..L)."""
+        arr = np.ascontiguousarray(shape, dtype=np.int32)
+        st = load().amg_set_level_shape(self._h, level, arr.ctypes.data)
+        if st:
+            raise AmgError(st, last_error())
 
     def launch_count(self) -> int:
         return int(load().amg_launch_count(self._h))

@@ -161,6 +161,51 @@ int pcg_solve(amg_handle h, const double *b, double *x, double rtol, int maxit, 
 
 double amg_last_true_residual(amg_handle h) { return h ? h->last_true_rel : -1.0; }
 
+int amg_autotune(amg_handle h, int reps, int *changed, void *stream) {
+    set_error("");
+    int c = 0;
+    if (changed) *changed = 0;
+    if (!h) {
+        set_error("amg_autotune: NULL handle");
+        return AMG_ERR_ARG;
+    }
+    int st = autotune_impl(h, (cudaStream_t)stream, reps, &c);
+    if (changed) *changed = c;
+    return st;
+}
+
+int amg_set_level_shape(amg_handle h, int level, const int *shape) {
+    set_error("");
+    if (!h || !shape || level < 1 || level >= (int)h->lev.size()) {
+        set_error("amg_set_level_shape: bad handle, level (1..L) or input");
+        return AMG_ERR_ARG;
+    }
+    for (int i = 0; i < 4; i++)
+        if (shape[i] < 0 || shape[i] > 3) {
+            set_error("amg_set_level_shape: shape values are 0..3");
+            return AMG_ERR_ARG;
+        }
+    for (int p = 0; p < 2; p++)
+        for (int k = 0; k < 2; k++) h->lev[level].shape[p][k] = (unsigned char)shape[2 * p + k];
+    for (auto &g : h->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    h->graph_gen++;
+    return AMG_OK;
+}
+
+int amg_level_shape(amg_handle h, int level, int *shape) {
+    set_error("");
+    if (!h || !shape || level < 0 || level >= (int)h->lev.size()) {
+        set_error("amg_level_shape: bad handle, level or output");
+        return AMG_ERR_ARG;
+    }
+    for (int p = 0; p < 2; p++)
+        for (int k = 0; k < 2; k++) shape[2 * p + k] = h->lev[level].shape[p][k];
+    return AMG_OK;
+}
+
 int pcg_solve_multi(amg_handle h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
                     double *res_hist, void *stream) {
     set_error("");

@@ -126,6 +126,14 @@ struct Level {
     // D^-1 b (xpre) and the prolongated guess (xp)
     double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr, *xpre64 = nullptr, *xp64 = nullptr;
     float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *xpre32 = nullptr, *xp32 = nullptr;
+    // Launch shape of this level's down and post sweeps (levels >= 1), per
+    // V-cycle precision [0 float, 1 double] and sweep [0 down, 1 post]:
+    // bit 0 = rows load 16 entries per chunk (else 4), bit 1 = one thread per
+    // row (else one wave of resident blocks, grid-stride). Set by setup to
+    // the fixed rule (16-entry chunks up to kSmallRows rows, one thread per
+    // row) and by amg_autotune to the fastest measured shape. The shape never
+    // changes a result: every shape sums a row's entries in storage order.
+    unsigned char shape[2][2] = {{0, 0}, {0, 0}};
 };
 
 // Device-resident Krylov state; every scalar of the iteration lives here so
@@ -223,6 +231,7 @@ struct amg_hier {
     pcgamg::Ctl *ctl_host = nullptr;  // pinned mirror
     int nblk = 0;                // largest level-0 grid (sizes the partial sums)
     int grid32 = 0, grid64 = 0, gridv = 0;  // one wave of the float32 sweeps, float64 sweeps, vector kernels
+    int wave[2][2][2] = {};      // blocks in one wave: [float, double][down, post][4- or 16-entry chunks]
     double last_true_rel = 0.0;
     double setup_ms[4] = {0, 0, 0, 0};
     // kernel timing (amg_profile)
@@ -267,6 +276,7 @@ int solve_multi_impl(amg_hier *h, int k, const double *B, double *X, double rtol
                      double *res_hist, cudaStream_t s);
 void free_multi(amg_hier *h);
 int solve_prepare(amg_hier *h, int mode, int maxit);
+int autotune_impl(amg_hier *h, cudaStream_t s, int reps, int *changed);
 int solve_launch(amg_hier *h, int mode, const double *b, const double *x0, double rtol, int maxit, cudaStream_t s);
 int solve_collect(amg_hier *h, int mode, double *x, cudaStream_t s, int *status, int *iters, double *true_rel,
                   int64_t *kernels);

@@ -665,6 +665,48 @@ REmit remit(amg_hier *h) {
         }                                           \
     } while (0)
 
+template <typename T>
+constexpr int prec_index() { return sizeof(T) == 4 ? 0 : 1; }
+
+int shape_grid(const amg_hier *h, int n, int pi, int sweep, unsigned char shape) {
+    int g = grid_rows(n);
+    if (shape & 2) return g;
+    int w = h->wave[pi][sweep][shape & 1];
+    return w > 0 && w < g ? w : g;
+}
+
+// Down sweep of level l >= 1 with the given launch shape.
+template <typename T>
+void launch_down(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
+    using P = LP<T>;
+    Level &lv = h->lev[l];
+    int n = lv.A.n;
+    int g = shape_grid(h, n, prec_index<T>(), 0, shape);
+    if (shape & 1)
+        WITH_COLS(lv.S, (launch_k(h->pdl, k_down<T, IDX, kUnrollSmall, false>, g, kBlock, s, n, lv.S.sptr, cols,
+                                  P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), (const Ctl *)h->ctl)));
+    else
+        WITH_COLS(lv.S, (launch_k(h->pdl, k_down<T, IDX, kUnroll, false>, g, kBlock, s, n, lv.S.sptr, cols,
+                                  P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), (const Ctl *)h->ctl)));
+}
+
+// Post sweep of level l >= 1 (z = x_l) with the given launch shape.
+template <typename T>
+void launch_post(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
+    using P = LP<T>;
+    Level &lv = h->lev[l];
+    int n = lv.A.n;
+    int g = shape_grid(h, n, prec_index<T>(), 1, shape);
+    if (shape & 1)
+        WITH_COLS(lv.S, (launch_k(h->pdl, k_post<T, T, false, false, IDX, kUnrollSmall, false>, g, kBlock, s, n,
+                                  lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv),
+                                  (const double *)nullptr, (const double *)nullptr, (double *)nullptr, h->ctl)));
+    else
+        WITH_COLS(lv.S, (launch_k(h->pdl, k_post<T, T, false, false, IDX, kUnroll, false>, g, kBlock, s, n,
+                                  lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv),
+                                  (const double *)nullptr, (const double *)nullptr, (double *)nullptr, h->ctl)));
+}
+
 // z = B r (one V-cycle in precision T), including rho / beta. Kernels are
 // launched with programmatic dependent launch when h->pdl (see pdl_enter).
 template <typename T, bool FCG>
@@ -686,13 +728,7 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     int F = h->tail_first > 0 ? h->tail_first : L;
     for (int l = 0; l < F; l++) {
         Level &lv = lev[l];
-        int n = lv.A.n;
-        if (l > 0 && n > kSmallRows)
-            WITH_COLS(lv.S, (launch_k(pdl, k_down<T, IDX, kUnroll, false>, grid_rows(n), kBlock, s, n, lv.S.sptr,
-                                      cols, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl)));
-        else if (l > 0)
-            WITH_COLS(lv.S, (launch_k(pdl, k_down<T, IDX, kUnrollSmall, false>, grid_rows(n), kBlock, s, n,
-                                      lv.S.sptr, cols, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), ctl)));
+        if (l > 0) launch_down<T>(h, l, lv.shape[prec_index<T>()][0], s);
         if (l + 1 == L)
             launch_k(pdl, k_restrict<T, double, false>, grid_rows(lv.nc), kBlock, s, lv.nc, lv.rptr, lv.ridx,
                      P::t(lv), h->bL, nullptr, nullptr, ctl);
@@ -711,14 +747,7 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
         int n = lv.A.n;
         launch_k(pdl, k_prolong<T>, grid_rows(n), kBlock, s, n, P::xpre(lv), P::p(lv), lv.agg, P::x(lev[l + 1]),
                  P::xp(lv), ctl);
-        if (n > kSmallRows)
-            WITH_COLS(lv.S, (launch_k(pdl, k_post<T, T, false, false, IDX, kUnroll, false>, grid_rows(n), kBlock, s,
-                                      n, lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv),
-                                      nullptr, nullptr, nullptr, ctl)));
-        else
-            WITH_COLS(lv.S, (launch_k(pdl, k_post<T, T, false, false, IDX, kUnrollSmall, false>, grid_rows(n),
-                                      kBlock, s, n, lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv),
-                                      P::x(lv), nullptr, nullptr, nullptr, ctl)));
+        launch_post<T>(h, l, lv.shape[prec_index<T>()][1], s);
     }
     prof_end(h, s);
     prof_begin(h, 1, s);
@@ -1000,6 +1029,25 @@ int alloc_solve_workspace(amg_hier *h) {
     PCG_TRY(wave((const void *)k_spmv<int32_t>, &h->grid64));
     PCG_TRY(wave((const void *)k_update<AMG_MODE_FCG32>, &h->gridv));
     h->nblk = std::max(h->grid32, std::max(h->grid64, h->gridv));
+    // One wave of each coarse-level sweep variant, and the fixed shape rule.
+    const void *fns[2][2][2] = {
+        {{(const void *)k_down<float, int16_t, kUnroll, false>, (const void *)k_down<float, int16_t, kUnrollSmall, false>},
+         {(const void *)k_post<float, float, false, false, int16_t, kUnroll, false>,
+          (const void *)k_post<float, float, false, false, int16_t, kUnrollSmall, false>}},
+        {{(const void *)k_down<double, int16_t, kUnroll, false>, (const void *)k_down<double, int16_t, kUnrollSmall, false>},
+         {(const void *)k_post<double, double, false, false, int16_t, kUnroll, false>,
+          (const void *)k_post<double, double, false, false, int16_t, kUnrollSmall, false>}}};
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            for (int c = 0; c < 2; c++) {
+                int per = 0;
+                PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fns[a][b][c], kBlock, 0));
+                h->wave[a][b][c] = sms * (per > 0 ? per : 1);
+            }
+    for (size_t l = 1; l < h->lev.size(); l++) {
+        unsigned char d = (unsigned char)((h->lev[l].A.n <= kSmallRows ? 1 : 0) | 2);
+        for (auto &pr : h->lev[l].shape) pr[0] = pr[1] = d;
+    }
     PCG_TRY(alloc(M, &h->b, n));
     PCG_TRY(alloc(M, &h->x, n));
     PCG_TRY(alloc(M, &h->r, n));
@@ -1015,6 +1063,77 @@ int alloc_solve_workspace(amg_hier *h) {
     PCG_TRY(alloc(M, &h->hist, h->hist_cap));
     PCG_TRY(setup_tail(h));
     return AMG_OK;
+}
+
+// Launch-shape tuner: for every level l in 1..L-1 (the levels with down and
+// post sweeps), each V-cycle precision and each sweep, times the four shapes
+// (4- or 16-entry chunks x one-wave or one-thread-per-row grid) on this
+// device, `reps` launches each after one warm-up launch, and moves to the
+// fastest only if it beats the current shape by more than 3% (so timing
+// noise does not flip shapes). Work vectors are zeroed first; the inputs
+// only set the timing. Captured solve graphs are dropped.
+template <typename T>
+int tune_level(amg_hier *h, int l, cudaStream_t s, int reps, cudaEvent_t e0, cudaEvent_t e1, int *changed) {
+    int pi = prec_index<T>();
+    Level &lv = h->lev[l];
+    for (int sweep = 0; sweep < 2; sweep++) {
+        float best = 0.0f, cur = 0.0f;
+        int pick = -1;
+        for (int shape = 0; shape < 4; shape++) {
+            for (int r = -1; r < reps; r++) {
+                if (r == 0) PCG_CK(cudaEventRecord(e0, s));
+                if (sweep == 0) launch_down<T>(h, l, (unsigned char)shape, s);
+                else launch_post<T>(h, l, (unsigned char)shape, s);
+            }
+            PCG_CK(cudaEventRecord(e1, s));
+            PCG_CK(cudaEventSynchronize(e1));
+            PCG_LAUNCH_CK();
+            float ms = 0.0f;
+            PCG_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (shape == lv.shape[pi][sweep]) cur = ms;
+            if (pick < 0 || ms < best) {
+                best = ms;
+                pick = shape;
+            }
+        }
+        if (best > 0.97f * cur) pick = lv.shape[pi][sweep];
+        if (lv.shape[pi][sweep] != pick) (*changed)++;
+        lv.shape[pi][sweep] = (unsigned char)pick;
+    }
+    return AMG_OK;
+}
+
+int autotune_impl(amg_hier *h, cudaStream_t s, int reps, int *changed) {
+    int L = (int)h->lev.size() - 1;
+    *changed = 0;
+    if (reps < 1) reps = 1;
+    PCG_CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+    for (int l = 1; l <= L; l++) {
+        Level &lv = h->lev[l];
+        size_t n = (size_t)lv.A.n;
+        for (float *v : {lv.b32, lv.x32, lv.t32, lv.xpre32, lv.xp32})
+            if (v) PCG_CK(cudaMemsetAsync(v, 0, n * sizeof(float), s));
+        for (double *v : {lv.b64, lv.x64, lv.t64, lv.xpre64, lv.xp64})
+            if (v) PCG_CK(cudaMemsetAsync(v, 0, n * sizeof(double), s));
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = AMG_OK;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) st = cuda_fail(ce, "autotune events", __FILE__, __LINE__);
+    for (int l = 1; l < L && !st; l++) {
+        st = tune_level<float>(h, l, s, reps, e0, e1, changed);
+        if (!st) st = tune_level<double>(h, l, s, reps, e0, e1, changed);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (auto &g : h->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    h->graph_gen++;
+    PCG_CK(cudaStreamSynchronize(s));
+    return st;
 }
 
 // Makes room for maxit+1 history values (invalidates captured graphs).

@@ -305,3 +305,36 @@ def test_full_size_128_graded(mode):
     assert res.status == 0 and abs(res.iters - ref["iters"]) <= 1
     assert np.linalg.norm(prob.b - W.spmv(prob.A, xs)) / np.linalg.norm(prob.b) <= RTOL
     assert np.linalg.norm(xs - ref["x"]) / np.linalg.norm(ref["x"]) <= X_TOL
+
+
+@pytest.mark.parametrize("mode", ["pcg64", "fcg32"])
+def test_every_launch_shape_gives_the_same_bits(mode):
+    """Sweep launch shapes (chunk depth x grid form) change speed only: each
+    forced shape, and the tuner's pick, reproduce the default solve bit for
+    bit (rows are summed in storage order whatever the shape)."""
+    prob = W.make_problem(40, 1.04, seed=12)
+    b = torch.from_numpy(prob.b).cuda()
+    amg = B.AMG.from_csr(prob.A, mode=mode)
+    L = len(amg.info())
+    assert amg.level_shape(0) == [0, 0, 0, 0]
+    x0 = torch.zeros_like(b)
+    r0 = amg.solve(b, x0)
+    assert r0.status == 0
+    for shape in range(4):
+        for lvl in range(1, L):
+            amg.set_level_shape(lvl, [shape] * 4)
+        x = torch.zeros_like(b)
+        r = amg.solve(b, x)
+        assert r.iters == r0.iters and torch.equal(x, x0), shape
+    before = [amg.level_shape(lvl) for lvl in range(L)]
+    changed = amg.autotune(reps=2)
+    after = [amg.level_shape(lvl) for lvl in range(L)]
+    assert changed == sum(u != v for a, c in zip(before, after) for u, v in zip(a, c))
+    assert after[0] == [0, 0, 0, 0] and all(0 <= v <= 3 for s in after for v in s)
+    x = torch.zeros_like(b)
+    r = amg.solve(b, x)
+    assert r.iters == r0.iters and torch.equal(x, x0)
+    with pytest.raises(B.AmgError):
+        amg.set_level_shape(0, [0, 0, 0, 0])
+    with pytest.raises(B.AmgError):
+        amg.set_level_shape(1, [4, 0, 0, 0])
