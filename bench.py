@@ -51,6 +51,9 @@ def parse_args(argv=None):
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--multi-k", type=int, default=32, help="right-hand sides of the multi-column form (0: skip)")
+    ap.add_argument("--multi-N", type=int, default=160, help="mesh of the multi-column form (N^3 nodes)")
+    ap.add_argument("--large", action="store_true",
+                    help="instead of the default run: one 320^3 mesh, 8 right-hand sides, per-level rates")
     ap.add_argument("--multi-reps", type=int, default=3)
     ap.add_argument("--batch-count", type=int, default=48, help="independent systems of the batched form (0: skip)")
     ap.add_argument("--serve-count", type=int, default=160,
@@ -300,6 +303,7 @@ def timed_solves(amg, bs, x, steps, warmup, rtol, maxit, torch, stream, dist, de
     if profile:
         amg.profile(True)
         amg.profile_read()
+        amg.profile_levels()
     launches0 = amg.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     iters = []
@@ -321,12 +325,51 @@ def timed_solves(amg, bs, x, steps, warmup, rtol, maxit, torch, stream, dist, de
     torch.cuda.synchronize()
     launches = amg.launch_count() - launches0
     prof = amg.profile_read() if profile else None
+    lev_prof = amg.profile_levels() if profile else None
     if profile:
         amg.profile(False)
     lat = [a.elapsed_time(b) for a, b in ev]
     total_ms = t_all0.elapsed_time(t_all1)
     return {"total_ms": total_ms, "lat_ms": lat, "iters": iters, "launches": launches, "prof": prof,
-            "true_rel": res.true_rel}
+            "levels": lev_prof, "true_rel": res.true_rel}
+
+
+def level_table(amg, lev_prof, mode: str, peak: float) -> list:
+    """Per-level V-cycle time and HBM rate from a profiled pass.
+
+    Algorithmic bytes per V-cycle of level l (each array once, gathered
+    vectors once; vb = value bytes of the V-cycle precision, ib = column
+    bytes, matrices as stored with their slice padding):
+      down (l >= 1): matrix nnz_l (vb + ib) + xpre, b, p, t n_l vb;
+      restriction l -> l+1: t n_l vb + member lists 4 (n_l + n_{l+1})
+        + b, xpre, dinv of l+1 (float64 b on the coarsest);
+      up (l >= 1): prolongation xpre, p, xp n_l vb + agg 4 n_l + x_{l+1};
+        post: matrix nnz_l (vb + ib) + xp, b, dinv, x n_l vb;
+      coarsest: the dense inverse 8 n_L^2 + b_L, x_L.
+    """
+    ms, cnt = lev_prof
+    info = amg.info()
+    L = len(info) - 1
+    vb = 4 if mode == "fcg32" else 8
+    out = []
+    for lvl in range(L + 1):
+        n = info[lvl][0]
+        lay = amg.level_layout(lvl)
+        z, ib = lay["stored"], lay["index_bytes"]
+        nc = info[lvl + 1][0] if lvl < L else 0
+        down = up = 0.0
+        if lvl < L:
+            restr = n * vb + 4 * (n + nc) + (nc * 8 if lvl + 1 == L else 3 * nc * vb)
+            down = restr + (z * (vb + ib) + 4 * n * vb if lvl > 0 else 0)
+            up = (3 * n * vb + 4 * n + nc * vb + z * (vb + ib) + 4 * n * vb) if lvl > 0 else 0
+        else:
+            down = 8 * n * n + 16 * n
+        t = ms[lvl][0] / max(cnt[lvl][0], 1) + ms[lvl][1] / max(cnt[lvl][1], 1) + ms[lvl][2] / max(cnt[lvl][2], 1)
+        byt = down + up
+        out.append({"level": lvl, "n": n, "stored": z, "us_per_vcycle": 1e3 * t,
+                    "algorithmic_bytes": byt, "gbs": byt / (t * 1e-3) / 1e9 if t > 0 else None,
+                    "frac_of_hbm": byt / (t * 1e-3) / 1e9 / peak if t > 0 else None})
+    return out
 
 
 def pct(v, q):
@@ -377,14 +420,21 @@ def run_ours(args):
     # multi right-hand-side form: k columns of the same system in one solve
     multi = {}
     if args.multi_k > 0:
-        Bm, _ = W.make_rhs(prob, args.multi_k, seed=args.seed + 2000)
+        r_m = W.capped_grading(args.multi_N, args.ratio)
+        mprob = prob if args.multi_N == args.N else W.make_problem(args.multi_N, r_m, seed=4)
+        mamg = amg if mprob is prob else B.AMG.from_csr(mprob.A, mode="fcg32", stream=stream)
+        if mamg is not amg and not args.no_autotune:
+            mamg.autotune(reps=10, stream=stream)
+        Bm, _ = W.make_rhs(mprob, args.multi_k, seed=args.seed + 2000)
         Bd = torch.from_numpy(Bm).to(device)
         Xd = torch.zeros_like(Bd)
+        multi["workload"] = f"q1_hex_{args.multi_N}^3_zgrade{r_m}"
+        multi["n"] = mprob.A.n
         for mode in ("fcg32", "pcg64"):
-            amg.set_mode(mode)
+            mamg.set_mode(mode)
             for _ in range(max(1, min(args.warmup, 2))):
                 Xd.zero_()
-                amg.solve_multi(Bd, Xd, rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)
+                mamg.solve_multi(Bd, Xd, rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             reps = args.multi_reps
@@ -392,7 +442,7 @@ def run_ours(args):
             e0.record(stream)
             for _ in range(reps):
                 Xd.zero_()
-                st, it, _, sts, tr = amg.solve_multi(Bd, Xd, rtol=args.rtol, maxit=args.maxit, stream=stream,
+                st, it, _, sts, tr = mamg.solve_multi(Bd, Xd, rtol=args.rtol, maxit=args.maxit, stream=stream,
                                                      hist=False)
                 if st != 0:
                     raise RuntimeError(f"multi solve failed: {sts}")
@@ -400,10 +450,24 @@ def run_ours(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
+            # the same right-hand sides one at a time (whole-solve graphs)
+            xs = torch.zeros(mprob.A.n, dtype=torch.float64, device=device)
+            cols = [Bd[:, c].contiguous() for c in range(min(args.multi_k, 4))]
+            mamg.solve(cols[0], xs, rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)
+            e0.record(stream)
+            for col in cols:
+                xs.zero_()
+                mamg.solve(col, xs, rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms1 = e0.elapsed_time(e1) / len(cols)
             multi[mode] = {"k": args.multi_k, "ms_per_multi_solve": ms,
                            "solves_per_s": args.multi_k / (ms / 1e3), "max_iters": max(its),
-                           "max_true_rel": float(np.max(tr))}
-        amg.set_mode("fcg32")
+                           "max_true_rel": float(np.max(tr)), "single_solves_per_s": 1e3 / ms1}
+        mamg.set_mode("fcg32")
+        if mamg is not amg:
+            mamg.close()
+        del Bd, Xd
 
     # batched form: independent graded systems of uneven size, one launch
     batch = {}
@@ -546,6 +610,8 @@ def run_ours(args):
 
     per_kernel = kernel_table("fcg32")
     per_kernel64 = kernel_table("pcg64")
+    levels32 = level_table(amg, prof["fcg32"]["levels"], "fcg32", peak)
+    levels64 = level_table(amg, prof["pcg64"]["levels"], "pcg64", peak)
     cand = {k: v for k, v in per_kernel.items() if k not in ("coarse_levels", "residual")}
     dom = max(cand, key=lambda k: cand[k]["avg_ms"] * cand[k]["launches"])
     roofline = {"kernel": kernel_names[dom], "bound": "hbm", "achieved": cand[dom]["gbs"], "peak": peak,
@@ -583,6 +649,8 @@ def run_ours(args):
             "roofline": roofline,
             "kernels": per_kernel,
             "kernels_fp64": per_kernel64,
+            "levels": levels32,
+            "levels_fp64": levels64,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": m["launches"],
@@ -595,8 +663,71 @@ def run_ours(args):
     return 0
 
 
+def run_large(args):
+    """One 320^3 mesh (32.8M dofs, z spacing range capped as for the serving
+    meshes), 8 right-hand sides in one multi-column solve and one at a time,
+    both modes, with per-level V-cycle rates from a profiled pass."""
+    import torch
+    from paper_2210_16660_gb300 import binding as B
+    from paper_2210_16660_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    N, k = 320, 8
+    r = W.capped_grading(N, args.ratio)
+    t0 = time.perf_counter()
+    prob = W.make_problem(N, r, seed=6)
+    Bm, _ = W.make_rhs(prob, k, seed=1006)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    amg = B.AMG.from_csr(prob.A, mode="fcg32", stream=stream)
+    setup = amg.setup_times()
+    if not args.no_autotune:
+        amg.autotune(reps=10, stream=stream)
+    info = amg.info()
+    Bd = torch.from_numpy(Bm).to(device)
+    Xd = torch.zeros_like(Bd)
+    peak = measured_peaks().get("hbm_gbs") or 6800.0
+    out = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    for mode in ("fcg32", "pcg64"):
+        amg.set_mode(mode)
+        Xd.zero_()
+        amg.solve_multi(Bd, Xd, rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        Xd.zero_()
+        e0.record(stream)
+        st, it, _, sts, tr = amg.solve_multi(Bd, Xd, rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if st != 0:
+            raise RuntimeError(f"multi solve failed: {sts}")
+        ms_multi = e0.elapsed_time(e1)
+        cols = [Bd[:, c].contiguous() for c in range(k)]
+        x = torch.zeros(prob.A.n, dtype=torch.float64, device=device)
+        single = timed_solves(amg, cols, x, k, 1, args.rtol, args.maxit, torch, stream, None, device)
+        prof = timed_solves(amg, cols, x, 2, 1, args.rtol, args.maxit, torch, stream, None, device, profile=True)
+        out[mode] = {"multi": {"k": k, "ms": ms_multi, "solves_per_s": k / (ms_multi / 1e3),
+                               "max_iters": int(it.max()), "max_true_rel": float(np.max(tr))},
+                     "single": {"solves_per_s": k / (single["total_ms"] / 1e3),
+                                "iters": statistics.median(single["iters"]), "true_rel": single["true_rel"]},
+                     "levels": level_table(amg, prof["levels"], mode, peak)}
+    clocks = sampler.stop()
+    line = {"metric": "solves/s at rel.res 1e-8 (8 right-hand sides), mixed vs FP64; HBM GB/s per V-cycle level",
+            "config": {"workload": f"q1_hex_{N}^3_zgrade{r}", "n": prob.A.n, "nnz": prob.A.nnz, "rhs": k,
+                       "levels": len(info), "generation_s": gen_s},
+            "setup_ms": setup, "mixed": out["fcg32"], "fp64": out["pcg64"], "clocks": clocks,
+            "peak_hbm_gbs": peak}
+    print(json.dumps(line), flush=True)
+    amg.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.large:
+        return run_large(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

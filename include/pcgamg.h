@@ -270,24 +270,27 @@ void amg_server_destroy(amg_server s);
 
 /* Launch-shape tuner (no counterpart in the paper: it picks how the sweeps
  * are launched on this device, not what they compute). For every level
- * l >= 1 with sweeps, each V-cycle precision and each of the down and post
- * sweeps, it times four launch shapes -- rows loading 4 or 16 entries per
- * chunk, times a one-wave grid-stride grid or one thread per row -- `reps`
- * launches each (reps < 1: 1) on `stream`, and moves to the fastest when it
- * beats the current shape by more than 3%. Every
- * shape sums a row's entries in storage order, so solves give the same bits
- * before and after tuning; only their speed changes. The level work vectors
- * are overwritten; captured solve graphs are rebuilt on the next solve.
- * *changed (may be NULL): shapes that differ from before. Call it between
- * solves, not while a batch or server holding h is in use. */
+ * l >= 1 with sweeps, each V-cycle precision and each of the down phase
+ * (down sweep + restriction) and the up phase (prolongation + post sweep),
+ * it times eight launch shapes -- rows loading 4 or 16 entries per chunk,
+ * times a one-wave grid-stride grid or one thread per row, times two
+ * launches or one fused launch (down sweep and restriction by aggregate;
+ * prolongation formed per gathered entry inside the post sweep) -- `reps`
+ * runs each (reps < 1: 1) on `stream`, and moves to the fastest when it
+ * beats the current shape by more than 3%. Every shape forms the same
+ * values and sums a row's entries in storage order, so solves give the same
+ * bits before and after tuning; only their speed changes. The level work
+ * vectors are overwritten; captured solve graphs are rebuilt on the next
+ * solve. *changed (may be NULL): shapes that differ from before. Call it
+ * between solves, not while a batch or server holding h is in use. */
 int amg_autotune(amg_handle h, int reps, int *changed, void *stream);
 
-/* Launch shapes of a level (4 ints: float down, float post, float64 down,
- * float64 post; bit 0 = 16-entry chunks, bit 1 = one thread per row). Level
- * 0's sweeps have a fixed shape and report 0. */
+/* Launch shapes of a level (4 ints: float down, float up, float64 down,
+ * float64 up; bit 0 = 16-entry chunks, bit 1 = one thread per row, bit 2 =
+ * fused launch). Level 0's sweeps have a fixed shape and report 0. */
 int amg_level_shape(amg_handle h, int level, int *shape);
 
-/* Sets the launch shapes of level 1..L (same 4-int layout, values 0..3);
+/* Sets the launch shapes of level 1..L (same 4-int layout, values 0..7);
  * for manual tuning and for tests that check every shape gives the same
  * result. Errors: AMG_ERR_ARG. */
 int amg_set_level_shape(amg_handle h, int level, const int *shape);
@@ -332,6 +335,15 @@ int amg_profile(amg_handle h, int enable);
  * V-cycle), 6 p = z + beta p. ms and counts are host arrays of length
  * nkinds (<= 7). */
 int amg_profile_read(amg_handle h, double *ms, int64_t *counts, int nkinds);
+
+/* Per-level V-cycle time (ms) and span counts since the last read, then
+ * reset (recorded while amg_profile is on). For level l, entries 3l, 3l+1,
+ * 3l+2: the down phase (level l's down sweep, l >= 1, and the restriction
+ * to level l+1), the up phase (prolongation to level l and its post sweep,
+ * l >= 1) and the coarsest solve (on the coarsest level's entry, or on the
+ * first level of the cluster tail when that is on). ms, counts: host arrays
+ * of 3 nlev values (nlev <= 32), or NULL. */
+int amg_profile_levels(amg_handle h, int nlev, double *ms, int64_t *counts);
 
 /* Kernels launched by solves on h since setup (every launch, including the
  * ones that find the solve finished and return at once). */

@@ -28,7 +28,7 @@ EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode
            "amg_batch_create", "pcg_solve_batch", "amg_batch_destroy", "amg_server_default_params",
            "amg_serve_plan", "amg_server_create", "amg_server_mesh_info", "amg_server_info", "amg_server_submit",
            "amg_server_progress", "amg_server_result", "amg_server_destroy", "amg_autotune", "amg_level_shape",
-           "amg_set_level_shape")
+           "amg_set_level_shape", "amg_profile_levels")
 
 
 class AmgCsr(C.Structure):
@@ -131,6 +131,8 @@ def load(build_if_missing: bool = True):
     lib.amg_level_shape.restype = I
     lib.amg_set_level_shape.argtypes = [P, I, P]
     lib.amg_set_level_shape.restype = I
+    lib.amg_profile_levels.argtypes = [P, I, P, P]
+    lib.amg_profile_levels.restype = I
     lib.amg_destroy.argtypes = [P]
     lib.amg_destroy.restype = None
     lib.amg_last_error.argtypes = []
@@ -367,6 +369,16 @@ class AMG:
         if st:
             raise AmgError(st, last_error())
         return [int(v) for v in out]
+
+    def profile_levels(self):
+        """``amg_profile_levels``: (ms[L+1, 3], counts[L+1, 3]) per level: down, up, coarsest."""
+        nl = len(self.info())
+        ms = np.zeros(3 * nl)
+        cnt = np.zeros(3 * nl, np.int64)
+        st = load().amg_profile_levels(self._h, nl, ms.ctypes.data, cnt.ctypes.data)
+        if st:
+            raise AmgError(st, last_error())
+        return ms.reshape(nl, 3), cnt.reshape(nl, 3)
 
     def set_level_shape(self, level: int, shape) -> None:
         """``amg_set_level_shape`` (levels 1..L)."""

@@ -181,8 +181,8 @@ int amg_set_level_shape(amg_handle h, int level, const int *shape) {
         return AMG_ERR_ARG;
     }
     for (int i = 0; i < 4; i++)
-        if (shape[i] < 0 || shape[i] > 3) {
-            set_error("amg_set_level_shape: shape values are 0..3");
+        if (shape[i] < 0 || shape[i] > 7) {
+            set_error("amg_set_level_shape: shape values are 0..7");
             return AMG_ERR_ARG;
         }
     for (int p = 0; p < 2; p++)
@@ -326,6 +326,25 @@ int amg_profile_read(amg_handle h, double *ms, int64_t *counts, int nkinds) {
         h->prof_ms[k] = 0;
         h->prof_n[k] = 0;
     }
+    return AMG_OK;
+}
+
+int amg_profile_levels(amg_handle h, int nlev, double *ms, int64_t *counts) {
+    set_error("");
+    if (!h || nlev < 0 || nlev > amg_hier::kMaxProfLevels) {
+        set_error("amg_profile_levels: bad handle or nlev (at most %d)", amg_hier::kMaxProfLevels);
+        return AMG_ERR_ARG;
+    }
+    for (int l = 0; l < nlev; l++)
+        for (int p = 0; p < 3; p++) {
+            if (ms) ms[3 * l + p] = h->lev_ms[l][p];
+            if (counts) counts[3 * l + p] = h->lev_n[l][p];
+        }
+    for (int l = 0; l < amg_hier::kMaxProfLevels; l++)
+        for (int p = 0; p < 3; p++) {
+            h->lev_ms[l][p] = 0;
+            h->lev_n[l][p] = 0;
+        }
     return AMG_OK;
 }
 

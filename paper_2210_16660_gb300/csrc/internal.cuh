@@ -126,13 +126,16 @@ struct Level {
     // D^-1 b (xpre) and the prolongated guess (xp)
     double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr, *xpre64 = nullptr, *xp64 = nullptr;
     float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *xpre32 = nullptr, *xp32 = nullptr;
-    // Launch shape of this level's down and post sweeps (levels >= 1), per
-    // V-cycle precision [0 float, 1 double] and sweep [0 down, 1 post]:
+    // Launch shape of this level's down and up phases (levels >= 1), per
+    // V-cycle precision [0 float, 1 double] and phase [0 down, 1 up]:
     // bit 0 = rows load 16 entries per chunk (else 4), bit 1 = one thread per
-    // row (else one wave of resident blocks, grid-stride). Set by setup to
+    // row (else one wave of resident blocks, grid-stride), bit 2 = one fused
+    // launch (down sweep + restriction by aggregate; prolongation formed per
+    // gathered entry inside the post sweep) instead of two. Set by setup to
     // the fixed rule (16-entry chunks up to kSmallRows rows, one thread per
-    // row) and by amg_autotune to the fastest measured shape. The shape never
-    // changes a result: every shape sums a row's entries in storage order.
+    // row, separate launches) and by amg_autotune to the fastest measured
+    // shape. The shape never changes a result: every shape forms the same
+    // values and sums a row's entries in storage order.
     unsigned char shape[2][2] = {{0, 0}, {0, 0}};
 };
 
@@ -242,6 +245,10 @@ struct amg_hier {
     int ev_kind[256] = {0};
     double prof_ms[kKinds] = {0};
     int64_t prof_n[kKinds] = {0};
+    // per-level V-cycle spans: [level][down, up, coarsest]
+    static constexpr int kMaxProfLevels = 32;
+    double lev_ms[kMaxProfLevels][3] = {};
+    int64_t lev_n[kMaxProfLevels][3] = {};
     int64_t launches = 0;
     // whole-solve CUDA graph per mode: prefix kernels, then a device-side
     // while loop whose body runs two iterations

@@ -207,6 +207,66 @@ __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t *__re
     if (PRE) xprec[I] = ldg(dinvc + I) * s;
 }
 
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// Down sweep fused with the restriction it feeds, one thread per coarse row
+// I: t_i = p_i (b_i - sum_j a_ij xpre_j) for each member i of aggregate I
+// (members in increasing index order), summed into b_c[I] (and, with PRE,
+// xpre_c = dinv_c b_c). Same arithmetic, in the same order, as k_down
+// followed by k_restrict; t is never stored.
+template <typename T, typename TO, bool PRE, typename IDX, int U>
+__global__ void __launch_bounds__(kBlock) k_down_restrict(int nc, const int32_t *__restrict__ rptr,
+                                                          const int32_t *__restrict__ ridx,
+                                                          const int32_t *__restrict__ sptr,
+                                                          const IDX *__restrict__ col, const T *__restrict__ val,
+                                                          const T *__restrict__ xpre, const T *__restrict__ b,
+                                                          const T *__restrict__ p, TO *__restrict__ bc,
+                                                          const T *__restrict__ dinvc, T *__restrict__ xprec,
+                                                          const Ctl *__restrict__ ctl) {
+    pdl_enter();
+    if (ctl->done) return;
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    T sum = 0;
+    for (int32_t q = ldg(rptr + I); q < ldg(rptr + I + 1); q++) {
+        int i = ldg(ridx + q);
+        SELL_ROW_BEGIN
+        T acc = sell_row<U, false>(c_, a_, w_, i, [&](int j) { return ldg(xpre + j); });
+        // rounded product (never contracted into the sum), as k_down stores t
+        T t = mul_rn(ldg(p + i), ldg(b + i) - acc);
+        sum += t;
+    }
+    bc[I] = (TO)sum;
+    if (PRE) xprec[I] = ldg(dinvc + I) * sum;
+}
+
+// Prolongation fused into the post sweep: xp_j = xpre_j + p_j x_c[agg_j] is
+// formed for every gathered entry (and for the row itself), then
+// z_i = xp_i + dinv_i (b_i - sum_j a_ij xp_j). Same values as k_prolong
+// followed by k_post; xp is never stored.
+template <typename T, typename IDX, int U>
+__global__ void __launch_bounds__(kBlock) k_prolong_post(int n, const int32_t *__restrict__ sptr,
+                                                         const IDX *__restrict__ col, const T *__restrict__ val,
+                                                         const T *__restrict__ xpre, const T *__restrict__ p,
+                                                         const int32_t *__restrict__ agg, const T *__restrict__ xc,
+                                                         const T *__restrict__ b, const T *__restrict__ dinv,
+                                                         T *__restrict__ z, const Ctl *__restrict__ ctl) {
+    pdl_enter();
+    if (ctl->done) return;
+    auto xp = [&](int j) {
+        T x = ldg(xpre + j);
+        int a = ldg(agg + j);
+        if (a >= 0) x += ldg(p + j) * ldg(xc + a);
+        return x;
+    };
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        SELL_ROW_BEGIN
+        T acc = sell_row<U, false>(c_, a_, w_, i, xp);
+        z[i] = xp(i) + ldg(dinv + i) * (ldg(b + i) - acc);
+    }
+}
+
 // x_L = A_L^{-1} b_L, one warp per row; TO = float rounds the float64 result.
 template <typename TO>
 __global__ void __launch_bounds__(kBlock) k_coarse(int nL, const double *__restrict__ ainv,
@@ -581,27 +641,42 @@ int tail_cluster_size(int *ctas) {
 // CUDA-event spans around kernel launches (only when profiling is on).
 // kinds: 0 down0, 1 up0 (prolong0 + post0), 2 q = A p, 3 update,
 // 4 true residual, 5 levels >= 1 and the coarsest solve, 6 p = z + beta p.
-constexpr int kEvPairs = 96;
+constexpr int kEvPairs = 256;
 
-void prof_begin(amg_hier *h, int kind, cudaStream_t s) {
-    if (!h->profile || h->ev_used + 2 > (int)h->ev.size()) return;
-    h->ev_kind[h->ev_used / 2] = kind;
-    cudaEventRecord(h->ev[h->ev_used], s);
-}
+// Opens a span of `kind` (kinds < kKinds: the kernel kinds above; kinds
+// kLevelSpan + 3 l + phase: level l's down (0: down + restriction), up (1:
+// prolongation + post) or coarsest (2) phase). Returns the span's slot or -1.
+constexpr int kLevelSpan = 100;
 
-void prof_end(amg_hier *h, cudaStream_t s) {
-    if (!h->profile || h->ev_used + 2 > (int)h->ev.size()) return;
-    cudaEventRecord(h->ev[h->ev_used + 1], s);
+int prof_begin(amg_hier *h, int kind, cudaStream_t s) {
+    if (!h->profile || h->ev_used + 2 > (int)h->ev.size()) return -1;
+    int slot = h->ev_used;
+    h->ev_kind[slot / 2] = kind;
+    cudaEventRecord(h->ev[slot], s);
     h->ev_used += 2;
+    return slot;
 }
 
-// Fold the recorded spans into the per-kind totals (stream already synchronised).
+void prof_end(amg_hier *h, int slot, cudaStream_t s) {
+    if (slot < 0) return;
+    cudaEventRecord(h->ev[slot + 1], s);
+}
+
+// Fold the recorded spans into the totals (stream already synchronised).
 void prof_collect(amg_hier *h) {
     for (int k = 0; k + 1 < h->ev_used; k += 2) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]) == cudaSuccess) {
-            h->prof_ms[h->ev_kind[k / 2]] += ms;
-            h->prof_n[h->ev_kind[k / 2]] += 1;
+        if (cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]) != cudaSuccess) continue;
+        int kind = h->ev_kind[k / 2];
+        if (kind >= kLevelSpan) {
+            int l = (kind - kLevelSpan) / 3, ph = (kind - kLevelSpan) % 3;
+            if (l < amg_hier::kMaxProfLevels) {
+                h->lev_ms[l][ph] += ms;
+                h->lev_n[l][ph] += 1;
+            }
+        } else {
+            h->prof_ms[kind] += ms;
+            h->prof_n[kind] += 1;
         }
     }
     h->ev_used = 0;
@@ -675,7 +750,7 @@ int shape_grid(const amg_hier *h, int n, int pi, int sweep, unsigned char shape)
     return w > 0 && w < g ? w : g;
 }
 
-// Down sweep of level l >= 1 with the given launch shape.
+// Down sweep of level l >= 1 with the given launch shape (bits 0 and 1).
 template <typename T>
 void launch_down(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
     using P = LP<T>;
@@ -688,6 +763,52 @@ void launch_down(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
     else
         WITH_COLS(lv.S, (launch_k(h->pdl, k_down<T, IDX, kUnroll, false>, g, kBlock, s, n, lv.S.sptr, cols,
                                   P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), (const Ctl *)h->ctl)));
+}
+
+// Restriction from level l to l+1 (the coarsest gets float64 b_L).
+template <typename T>
+void launch_restrict(amg_hier *h, int l, cudaStream_t s) {
+    using P = LP<T>;
+    auto &lev = h->lev;
+    Level &lv = lev[l];
+    const Ctl *ctl = h->ctl;
+    if (l + 2 == (int)lev.size())
+        launch_k(h->pdl, k_restrict<T, double, false>, grid_rows(lv.nc), kBlock, s, lv.nc, lv.rptr, lv.ridx,
+                 (const T *)P::t(lv), h->bL, (const T *)nullptr, (T *)nullptr, ctl);
+    else
+        launch_k(h->pdl, k_restrict<T, T, true>, grid_rows(lv.nc), kBlock, s, lv.nc, lv.rptr, lv.ridx,
+                 (const T *)P::t(lv), P::b(lev[l + 1]), P::dinv(lev[l + 1]), P::xpre(lev[l + 1]), ctl);
+}
+
+// Down phase of level l >= 1: down sweep then restriction, or (shape bit 2)
+// both in one launch by aggregate.
+template <typename T>
+void launch_down_phase(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
+    using P = LP<T>;
+    if (!(shape & 4)) {
+        launch_down<T>(h, l, shape, s);
+        launch_restrict<T>(h, l, s);
+        return;
+    }
+    auto &lev = h->lev;
+    Level &lv = lev[l];
+    const Ctl *ctl = h->ctl;
+    int g = grid_rows(lv.nc);
+    bool last = l + 2 == (int)lev.size();
+#define PCG_DR(U)                                                                                                   \
+    do {                                                                                                            \
+        if (last)                                                                                                   \
+            WITH_COLS(lv.S, (launch_k(h->pdl, k_down_restrict<T, double, false, IDX, U>, g, kBlock, s, lv.nc,      \
+                                      lv.rptr, lv.ridx, lv.S.sptr, cols, P::val(lv), P::xpre(lv), P::b(lv),         \
+                                      P::p(lv), h->bL, (const T *)nullptr, (T *)nullptr, ctl)));                    \
+        else                                                                                                        \
+            WITH_COLS(lv.S, (launch_k(h->pdl, k_down_restrict<T, T, true, IDX, U>, g, kBlock, s, lv.nc, lv.rptr,   \
+                                      lv.ridx, lv.S.sptr, cols, P::val(lv), P::xpre(lv), P::b(lv), P::p(lv),        \
+                                      P::b(lev[l + 1]), P::dinv(lev[l + 1]), P::xpre(lev[l + 1]), ctl)));           \
+    } while (0)
+    if (shape & 1) PCG_DR(kUnrollSmall);
+    else PCG_DR(kUnroll);
+#undef PCG_DR
 }
 
 // Post sweep of level l >= 1 (z = x_l) with the given launch shape.
@@ -707,6 +828,32 @@ void launch_post(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
                                   (const double *)nullptr, (const double *)nullptr, (double *)nullptr, h->ctl)));
 }
 
+// Up phase of level l >= 1: prolongation then post sweep, or (shape bit 2)
+// the prolongation formed per gathered entry inside the post sweep.
+template <typename T>
+void launch_up_phase(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
+    using P = LP<T>;
+    auto &lev = h->lev;
+    Level &lv = lev[l];
+    int n = lv.A.n;
+    const Ctl *ctl = h->ctl;
+    if (!(shape & 4)) {
+        launch_k(h->pdl, k_prolong<T>, grid_rows(n), kBlock, s, n, (const T *)P::xpre(lv), P::p(lv), lv.agg,
+                 (const T *)P::x(lev[l + 1]), P::xp(lv), ctl);
+        launch_post<T>(h, l, shape, s);
+        return;
+    }
+    int g = shape_grid(h, n, prec_index<T>(), 1, shape);
+    if (shape & 1)
+        WITH_COLS(lv.S, (launch_k(h->pdl, k_prolong_post<T, IDX, kUnrollSmall>, g, kBlock, s, n, lv.S.sptr, cols,
+                                  P::val(lv), (const T *)P::xpre(lv), P::p(lv), lv.agg, (const T *)P::x(lev[l + 1]),
+                                  (const T *)P::b(lv), P::dinv(lv), P::x(lv), ctl)));
+    else
+        WITH_COLS(lv.S, (launch_k(h->pdl, k_prolong_post<T, IDX, kUnroll>, g, kBlock, s, n, lv.S.sptr, cols,
+                                  P::val(lv), (const T *)P::xpre(lv), P::p(lv), lv.agg, (const T *)P::x(lev[l + 1]),
+                                  (const T *)P::b(lv), P::dinv(lv), P::x(lv), ctl)));
+}
+
 // z = B r (one V-cycle in precision T), including rho / beta. Kernels are
 // launched with programmatic dependent launch when h->pdl (see pdl_enter).
 template <typename T, bool FCG>
@@ -719,45 +866,55 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     const T *b0 = P::r0(h);
     const bool pdl = h->pdl;
     int g0 = sizeof(T) == 4 ? h->grid32 : h->grid64;
-    prof_begin(h, 0, s);
+    int sp1 = prof_begin(h, 0, s);
     WITH_COLS(l0.S, (launch_k(pdl, k_down<T, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n, l0.S.sptr, cols,
                               P::val(l0), P::xpre(l0), b0, P::p(l0), P::t(l0), ctl)));
-    prof_end(h, s);
-    prof_begin(h, 5, s);
+    prof_end(h, sp1, s);
+    int sp2 = prof_begin(h, 5, s);
     // levels handled by separate launches: 0..F-1; the tail runs F..L
     int F = h->tail_first > 0 ? h->tail_first : L;
+    // per-level spans (profiling only): level l's down phase is its down
+    // sweep and the restriction that leaves it (level 0: the restriction)
+    int kernels = 1;  // down sweep of level 0
     for (int l = 0; l < F; l++) {
         Level &lv = lev[l];
-        if (l > 0) launch_down<T>(h, l, lv.shape[prec_index<T>()][0], s);
-        if (l + 1 == L)
-            launch_k(pdl, k_restrict<T, double, false>, grid_rows(lv.nc), kBlock, s, lv.nc, lv.rptr, lv.ridx,
-                     P::t(lv), h->bL, nullptr, nullptr, ctl);
-        else
-            launch_k(pdl, k_restrict<T, T, true>, grid_rows(lv.nc), kBlock, s, lv.nc, lv.rptr, lv.ridx, P::t(lv),
-                     P::b(lev[l + 1]), P::dinv(lev[l + 1]), P::xpre(lev[l + 1]), ctl);
+        int spl = prof_begin(h, kLevelSpan + 3 * l, s);
+        unsigned char sh = lv.shape[prec_index<T>()][0];
+        if (l == 0) {
+            launch_restrict<T>(h, 0, s);
+            kernels += 1;
+        } else {
+            launch_down_phase<T>(h, l, sh, s);
+            kernels += (sh & 4) ? 1 : 2;
+        }
+        prof_end(h, spl, s);
     }
+    int spc = prof_begin(h, kLevelSpan + 3 * F + 2, s);
     if (F < L) {
         PCG_TRY(launch_tail<T>(h, TailPick<T>::get(h), L - F + 1, s));
     } else {
         launch_k(pdl, k_coarse<T>, (h->nL * 32 + kBlock - 1) / kBlock, kBlock, s, h->nL, h->Ainv, h->bL,
                  P::x(lev[L]), ctl);
     }
+    prof_end(h, spc, s);
     for (int l = F - 1; l >= 1; l--) {
         Level &lv = lev[l];
-        int n = lv.A.n;
-        launch_k(pdl, k_prolong<T>, grid_rows(n), kBlock, s, n, P::xpre(lv), P::p(lv), lv.agg, P::x(lev[l + 1]),
-                 P::xp(lv), ctl);
-        launch_post<T>(h, l, lv.shape[prec_index<T>()][1], s);
+        int spl = prof_begin(h, kLevelSpan + 3 * l + 1, s);
+        unsigned char sh = lv.shape[prec_index<T>()][1];
+        launch_up_phase<T>(h, l, sh, s);
+        kernels += (sh & 4) ? 1 : 2;
+        prof_end(h, spl, s);
     }
-    prof_end(h, s);
-    prof_begin(h, 1, s);
+    kernels += 1 + 2;  // coarsest (or tail), prolongation and post sweep of level 0
+    prof_end(h, sp2, s);
+    int sp3 = prof_begin(h, 1, s);
     launch_k(pdl, k_prolong<T>, h->gridv, kBlock, s, l0.A.n, P::xpre(l0), P::p(l0), l0.agg, P::x(lev[1]),
              P::xp(l0), ctl);
     WITH_COLS(l0.S, (launch_k(pdl, k_post<T, double, true, FCG, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n,
                               l0.S.sptr, cols, P::val(l0), P::xp(l0), b0, P::dinv(l0), h->z, h->r, h->q, h->partials,
                               ctl)));
-    prof_end(h, s);
-    h->launches += (h->tail_first > 0) ? 4 * h->tail_first + 1 : 4 * L + 1;
+    prof_end(h, sp3, s);
+    h->launches += kernels;
     PCG_LAUNCH_CK();
     return AMG_OK;
 }
@@ -777,21 +934,21 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
     } else {
         PCG_TRY((launch_vcycle<double, false>(h, s)));
     }
-    prof_begin(h, 6, s);
+    int sp4 = prof_begin(h, 6, s);
     launch_k(pdl, k_axpy_p, h->gridv, kBlock, s, n, h->z, h->p, h->ctl);
-    prof_end(h, s);
-    prof_begin(h, 2, s);
+    prof_end(h, sp4, s);
+    int sp5 = prof_begin(h, 2, s);
     WITH_COLS(l0.S, (launch_k(pdl, k_spmv<IDX>, h->grid64, kBlock, s, n, l0.S.sptr, cols, l0.S.v64, h->p, h->q,
                               h->partials, h->ctl)));
-    prof_end(h, s);
-    prof_begin(h, 3, s);
+    prof_end(h, sp5, s);
+    int sp6 = prof_begin(h, 3, s);
     launch_k(pdl, k_update<MODE>, h->gridv, kBlock, s, n, h->p, h->q, h->x, h->r, remit(h), h->partials, h->ctl,
              h->hist);
-    prof_end(h, s);
-    prof_begin(h, 4, s);
+    prof_end(h, sp6, s);
+    int sp7 = prof_begin(h, 4, s);
     WITH_COLS(l0.S, (launch_k(pdl, k_residual<false, MODE, IDX>, h->grid64, kBlock, s, n, l0.S.sptr, cols, l0.S.v64,
                               h->b, h->x, h->r, remit(h), h->partials, h->ctl, h->hist)));
-    prof_end(h, s);
+    prof_end(h, sp7, s);
     h->launches += 4;
     PCG_LAUNCH_CK();
     return AMG_OK;
@@ -1066,12 +1223,14 @@ int alloc_solve_workspace(amg_hier *h) {
 }
 
 // Launch-shape tuner: for every level l in 1..L-1 (the levels with down and
-// post sweeps), each V-cycle precision and each sweep, times the four shapes
-// (4- or 16-entry chunks x one-wave or one-thread-per-row grid) on this
-// device, `reps` launches each after one warm-up launch, and moves to the
-// fastest only if it beats the current shape by more than 3% (so timing
-// noise does not flip shapes). Work vectors are zeroed first; the inputs
-// only set the timing. Captured solve graphs are dropped.
+// post sweeps), each V-cycle precision and each phase (down: down sweep +
+// restriction; up: prolongation + post sweep), times the eight shapes
+// (4- or 16-entry chunks x one-wave or one-thread-per-row grid x separate or
+// fused launches) on this device, `reps` runs each after one warm-up run,
+// and moves to the fastest only if it beats the current shape by more than
+// 3% (so timing noise does not flip shapes). Work vectors are zeroed first;
+// the inputs only set the timing. Captured solve graphs are dropped.
+constexpr int kShapes = 8;
 template <typename T>
 int tune_level(amg_hier *h, int l, cudaStream_t s, int reps, cudaEvent_t e0, cudaEvent_t e1, int *changed) {
     int pi = prec_index<T>();
@@ -1079,11 +1238,11 @@ int tune_level(amg_hier *h, int l, cudaStream_t s, int reps, cudaEvent_t e0, cud
     for (int sweep = 0; sweep < 2; sweep++) {
         float best = 0.0f, cur = 0.0f;
         int pick = -1;
-        for (int shape = 0; shape < 4; shape++) {
+        for (int shape = 0; shape < kShapes; shape++) {
             for (int r = -1; r < reps; r++) {
                 if (r == 0) PCG_CK(cudaEventRecord(e0, s));
-                if (sweep == 0) launch_down<T>(h, l, (unsigned char)shape, s);
-                else launch_post<T>(h, l, (unsigned char)shape, s);
+                if (sweep == 0) launch_down_phase<T>(h, l, (unsigned char)shape, s);
+                else launch_up_phase<T>(h, l, (unsigned char)shape, s);
             }
             PCG_CK(cudaEventRecord(e1, s));
             PCG_CK(cudaEventSynchronize(e1));
