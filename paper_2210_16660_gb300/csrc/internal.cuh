@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "pcgamg.h"
+#include "tail_plan.h"
 
 namespace pcgamg {
 
@@ -162,17 +163,6 @@ struct Ctl {
 };
 
 // One level of the fused small-level tail of the V-cycle (device copy).
-template <typename T>
-struct TailLevel {
-    int n, nc;
-    const int32_t *sptr;
-    const int32_t *col;
-    const int16_t *col16;   // used when not null
-    const T *val, *dinv, *p;
-    const int32_t *agg, *rptr, *ridx;
-    T *b, *x, *t, *xpre;
-};
-
 // Device-resident state of a multi right-hand-side solve (K <= 32 columns).
 struct CtlM {
     double bnorm[32], rho[32], rho_old[32], pq[32], pq_old[32], alpha[32], beta[32], rel[32], true_rel[32];
@@ -260,11 +250,13 @@ struct amg_hier {
     int no_col16 = 0;
     int pdl = 1;  // programmatic dependent launch between solve kernels
     int graph_gen = 0;       // bumped whenever captured graphs go stale
-    // cluster tail: levels tail_first..L run in one thread-block cluster
-    int tail_first = 0;      // 0 = no tail (every level launched separately)
-    int tail_ctas = 0;       // CTAs of the cluster
-    pcgamg::TailLevel<float> *tail32 = nullptr;
-    pcgamg::TailLevel<double> *tail64 = nullptr;
+    // shared-memory cluster tail: levels tail_first..L in one cluster launch,
+    // per V-cycle precision [float, double]
+    int tail_first[2] = {0, 0};  // 0 = no tail (every level launched separately)
+    int tail_ctas[2] = {0, 0};   // CTAs of the cluster
+    pcgamg::SmemTailPlan tail_plan[2] = {};   // [float, double] V-cycle
+    unsigned char *tail_blob[2] = {nullptr, nullptr};
+    size_t tail_smem[2] = {0, 0};
     // multi right-hand-side solves
     pcgamg::MultiWS multi;
     int multi_k = 0;
@@ -284,6 +276,9 @@ int solve_multi_impl(amg_hier *h, int k, const double *B, double *X, double rtol
 void free_multi(amg_hier *h);
 int solve_prepare(amg_hier *h, int mode, int maxit);
 int autotune_impl(amg_hier *h, cudaStream_t s, int reps, int *changed);
+int setup_smem_tail(amg_hier *h);
+template <typename T>
+int launch_smem_tail(amg_hier *h, cudaStream_t s);
 int solve_launch(amg_hier *h, int mode, const double *b, const double *x0, double rtol, int maxit, cudaStream_t s);
 int solve_collect(amg_hier *h, int mode, double *x, cudaStream_t s, int *status, int *iters, double *true_rel,
                   int64_t *kernels);

@@ -34,12 +34,8 @@
 #include <algorithm>
 #include <type_traits>
 
-#include <cooperative_groups.h>
-
 #include "internal.cuh"
 #include "sell_row.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace pcgamg {
 
@@ -495,148 +491,6 @@ __global__ void k_set_cond(cudaGraphConditionalHandle hc, Ctl *ctl, int count_bo
 inline int grid_rows(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
 
-// ------------------------------------------------------------ cluster tail
-// Levels with few rows are latency-bound: a launch per sweep costs more than
-// the sweep. The tail runs every V-cycle phase of levels tail_first..L in one
-// launch of a single thread-block cluster (h->tail_ctas CTAs, co-scheduled by
-// the hardware, one per SM), phases separated by the cluster barrier:
-//   down_l, restrict_l (l = first..L-1), coarse solve, then
-//   prolong+post_l (l = L-1..first, prolongation formed per entry).
-// The barrier's release/acquire semantics at cluster scope make the global
-// writes of one phase visible to every CTA of the cluster in the next; data
-// written in one phase and read in a later one is loaded with __ldcg (L2),
-// read-only data with __ldg. Every thread passes the same sequence of
-// barriers (the loop bounds are kernel arguments, the early exit reads a
-// value no thread of this launch writes), so no barrier is left waiting.
-constexpr int kTailThreads = 512;
-constexpr int kTailRows = 12000;
-
-template <typename T, typename IDX, typename F>
-__device__ __forceinline__ T tail_row(int i, const int32_t *sptr, const IDX *col, const T *val, F xval) {
-    int s = i >> 5, lane = i & 31;
-    int32_t base = __ldg(sptr + s);
-    int w = (__ldg(sptr + s + 1) - base) >> 5;
-    return sell_row<kUnrollSmall, false>(col + base + lane, val + base + lane, w, i, xval);
-}
-
-template <typename T>
-__device__ __forceinline__ void tail_down(const TailLevel<T> &L, int tid, int nth) {
-    for (int i = tid; i < L.n; i += nth) {
-        auto xv = [&](int j) { return __ldcg(L.xpre + j); };
-        T acc = L.col16 ? tail_row<T>(i, L.sptr, L.col16, L.val, xv) : tail_row<T>(i, L.sptr, L.col, L.val, xv);
-        L.t[i] = __ldg(L.p + i) * (__ldcg(L.b + i) - acc);
-    }
-}
-
-// Fused prolongation + post-smooth: xp_j = xpre_j + p_j xc[agg_j] per entry.
-template <typename T>
-__device__ __forceinline__ void tail_up(const TailLevel<T> &L, const T *xc, int tid, int nth) {
-    for (int i = tid; i < L.n; i += nth) {
-        auto xp = [&](int j) {
-            T x = __ldcg(L.xpre + j);
-            int a = __ldg(L.agg + j);
-            if (a >= 0) x += __ldg(L.p + j) * __ldcg(xc + a);
-            return x;
-        };
-        T acc = L.col16 ? tail_row<T>(i, L.sptr, L.col16, L.val, xp) : tail_row<T>(i, L.sptr, L.col, L.val, xp);
-        L.x[i] = xp(i) + __ldg(L.dinv + i) * (__ldcg(L.b + i) - acc);
-    }
-}
-
-// lv[0..nt-1]: levels first..L (lv[nt-1] is the coarsest: only x is used).
-template <typename T>
-__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__restrict__ lv, int nt,
-                                                          const double *__restrict__ ainv, int nL, double *bL,
-                                                          const Ctl *__restrict__ ctl) {
-    pdl_enter();
-    cg::cluster_group cluster = cg::this_cluster();
-    if (ctl->done) return;
-    int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    for (int k = 0; k + 1 < nt; k++) {
-        const TailLevel<T> L = lv[k];
-        tail_down(L, tid, nth);
-        cluster.sync();
-        bool last = (k + 2 == nt);
-        const TailLevel<T> C = lv[k + 1];
-        for (int I = tid; I < L.nc; I += nth) {
-            T sum = 0;
-            for (int32_t q = __ldg(L.rptr + I); q < __ldg(L.rptr + I + 1); q++) sum += __ldcg(L.t + __ldg(L.ridx + q));
-            if (last) {
-                bL[I] = (double)sum;
-            } else {
-                C.b[I] = sum;
-                C.xpre[I] = __ldg(C.dinv + I) * sum;
-            }
-        }
-        cluster.sync();
-    }
-    // coarsest: x_L = A_L^{-1} b_L, one warp per row
-    int warp = tid >> 5, nwarp = nth >> 5, lane = threadIdx.x & 31;
-    T *xL = lv[nt - 1].x;
-    for (int row = warp; row < nL; row += nwarp) {
-        const double *a = ainv + (int64_t)row * nL;
-        double sacc = 0.0;
-        for (int j = lane; j < nL; j += 32) sacc += __ldg(a + j) * __ldcg(bL + j);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
-        if (lane == 0) xL[row] = (T)sacc;
-    }
-    cluster.sync();
-    for (int k = nt - 2; k >= 0; k--) {
-        tail_up(lv[k], (const T *)lv[k + 1].x, tid, nth);
-        if (k > 0) cluster.sync();
-    }
-}
-
-template <typename T>
-int launch_tail(amg_hier *h, const TailLevel<T> *lv, int nt, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(h->tail_ctas);
-    cfg.blockDim = dim3(kTailThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = h->tail_ctas;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = h->pdl ? 2 : 1;
-    PCG_CK(cudaLaunchKernelEx(&cfg, k_tail<T>, lv, nt, (const double *)h->Ainv, h->nL, h->bL, (const Ctl *)h->ctl));
-    return AMG_OK;
-}
-
-// Largest cluster (16, else 8) of k_tail<T> that the device can schedule.
-template <typename T>
-int tail_cluster_size(int *ctas) {
-    *ctas = 0;
-    PCG_CK(cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    for (int c : {16, 8}) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(c);
-        cfg.blockDim = dim3(kTailThreads);
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = c;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_tail<T>, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (n >= 1) {
-            *ctas = c;
-            return AMG_OK;
-        }
-    }
-    return AMG_OK;
-}
-
 // ------------------------------------------------------------ profiling
 // CUDA-event spans around kernel launches (only when profiling is on).
 // kinds: 0 down0, 1 up0 (prolong0 + post0), 2 q = A p, 3 update,
@@ -708,17 +562,6 @@ struct LP<double> {
     static double *xpre(Level &l) { return l.xpre64; }
     static double *xp(Level &l) { return l.xp64; }
     static const double *r0(const amg_hier *h) { return h->r; }
-};
-
-template <typename T>
-struct TailPick;
-template <>
-struct TailPick<float> {
-    static const TailLevel<float> *get(amg_hier *h) { return h->tail32; }
-};
-template <>
-struct TailPick<double> {
-    static const TailLevel<double> *get(amg_hier *h) { return h->tail64; }
 };
 
 REmit remit(amg_hier *h) {
@@ -872,7 +715,7 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     prof_end(h, sp1, s);
     int sp2 = prof_begin(h, 5, s);
     // levels handled by separate launches: 0..F-1; the tail runs F..L
-    int F = h->tail_first > 0 ? h->tail_first : L;
+    int F = h->tail_first[prec_index<T>()] > 0 ? h->tail_first[prec_index<T>()] : L;
     // per-level spans (profiling only): level l's down phase is its down
     // sweep and the restriction that leaves it (level 0: the restriction)
     int kernels = 1;  // down sweep of level 0
@@ -891,7 +734,7 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     }
     int spc = prof_begin(h, kLevelSpan + 3 * F + 2, s);
     if (F < L) {
-        PCG_TRY(launch_tail<T>(h, TailPick<T>::get(h), L - F + 1, s));
+        PCG_TRY(launch_smem_tail<T>(h, s));
     } else {
         launch_k(pdl, k_coarse<T>, (h->nL * 32 + kBlock - 1) / kBlock, kBlock, s, h->nL, h->Ainv, h->bL,
                  P::x(lev[L]), ctl);
@@ -1090,57 +933,13 @@ bool is_device_ptr(const void *p) {
 
 }  // namespace
 
-// Cluster tail: the first level (>= 1) with at most kTailRows rows through the
-// coarsest, when at least one level lies between it and the coarsest.
-// Opt-in with PCGAMG_TAIL=1: inside the whole-solve graph the separate
-// launches it replaces cost about as much on GB300 (128^3: the same solve
-// rate with float32 levels, 2.6% slower with float64 levels).
+// Shared-memory cluster tail (tail.cu); PCGAMG_TAIL=0 launches every level
+// separately instead.
 int setup_tail(amg_hier *h) {
-    int L = (int)h->lev.size() - 1;
-    h->tail_first = 0;
+    h->tail_first[0] = h->tail_first[1] = 0;
     const char *e = getenv("PCGAMG_TAIL");
-    if (!e || e[0] != '1') return AMG_OK;
-    int F = 0;
-    for (int l = 1; l < L; l++)
-        if (h->lev[l].A.n <= kTailRows) { F = l; break; }
-    if (F == 0) return AMG_OK;
-    int c32 = 0, c64 = 0;
-    PCG_TRY(tail_cluster_size<float>(&c32));
-    PCG_TRY(tail_cluster_size<double>(&c64));
-    int ctas = c32 < c64 ? c32 : c64;
-    if (ctas < 1) return AMG_OK;
-    h->tail_ctas = ctas;
-    int nt = L - F + 1;
-    std::vector<TailLevel<float>> t32(nt);
-    std::vector<TailLevel<double>> t64(nt);
-    for (int k = 0; k < nt; k++) {
-        Level &lv = h->lev[F + k];
-        TailLevel<float> &a = t32[k];
-        TailLevel<double> &b = t64[k];
-        a.n = b.n = lv.A.n;
-        a.nc = b.nc = lv.nc;
-        a.sptr = b.sptr = lv.S.sptr;
-        a.col = b.col = lv.S.col;
-        a.col16 = b.col16 = lv.S.col16;
-        a.val = lv.S.v32; b.val = lv.S.v64;
-        a.dinv = lv.dinv32; b.dinv = lv.dinv;
-        a.p = lv.p32; b.p = lv.p;
-        a.agg = b.agg = lv.agg;
-        a.rptr = b.rptr = lv.rptr;
-        a.ridx = b.ridx = lv.ridx;
-        a.b = lv.b32; b.b = lv.b64;
-        a.x = lv.x32; b.x = lv.x64;
-        a.t = lv.t32; b.t = lv.t64;
-        a.xpre = lv.xpre32; b.xpre = lv.xpre64;
-    }
-    Mem &M = h->mem;
-    PCG_TRY(alloc(M, &h->tail32, nt));
-    PCG_TRY(alloc(M, &h->tail64, nt));
-    PCG_CK(cudaMemcpyAsync(h->tail32, t32.data(), sizeof(TailLevel<float>) * nt, cudaMemcpyHostToDevice, M.stream));
-    PCG_CK(cudaMemcpyAsync(h->tail64, t64.data(), sizeof(TailLevel<double>) * nt, cudaMemcpyHostToDevice, M.stream));
-    PCG_CK(cudaStreamSynchronize(M.stream));
-    h->tail_first = F;
-    return AMG_OK;
+    if (e && e[0] == '0') return AMG_OK;
+    return setup_smem_tail(h);
 }
 
 int set_profile(amg_hier *h, int enable) {
