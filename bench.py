@@ -351,6 +351,9 @@ def level_table(amg, lev_prof, mode: str, peak: float) -> list:
     info = amg.info()
     L = len(info) - 1
     vb = 4 if mode == "fcg32" else 8
+    # the coarsest span sits on the first level of the shared-memory tail
+    # (when there is one): that level's time covers the tail levels below it
+    tail = next((lvl for lvl in range(L + 1) if cnt[lvl][2] > 0), L)
     out = []
     for lvl in range(L + 1):
         n = info[lvl][0]
@@ -366,9 +369,14 @@ def level_table(amg, lev_prof, mode: str, peak: float) -> list:
             down = 8 * n * n + 16 * n
         t = ms[lvl][0] / max(cnt[lvl][0], 1) + ms[lvl][1] / max(cnt[lvl][1], 1) + ms[lvl][2] / max(cnt[lvl][2], 1)
         byt = down + up
-        out.append({"level": lvl, "n": n, "stored": z, "us_per_vcycle": 1e3 * t,
-                    "algorithmic_bytes": byt, "gbs": byt / (t * 1e-3) / 1e9 if t > 0 else None,
-                    "frac_of_hbm": byt / (t * 1e-3) / 1e9 / peak if t > 0 else None})
+        row = {"level": lvl, "n": n, "stored": z, "us_per_vcycle": 1e3 * t,
+               "algorithmic_bytes": byt, "gbs": byt / (t * 1e-3) / 1e9 if t > 0 else None,
+               "frac_of_hbm": byt / (t * 1e-3) / 1e9 / peak if t > 0 else None}
+        if tail < L and lvl == tail:
+            row["note"] = f"time of the shared-memory cluster tail, levels {tail}..{L}"
+        elif lvl > tail:
+            row["note"] = f"inside the cluster tail of level {tail}"
+        out.append(row)
     return out
 
 

@@ -160,9 +160,13 @@ int fetch(std::vector<X> &dst, const X *src, size_t n) {
     return AMG_OK;
 }
 
+// The kernel's attributes are per function, shared by every hierarchy: the
+// dynamic shared-memory limit is set to the device maximum (never to one
+// plan's size, which a later hierarchy's setup would then shrink under an
+// earlier one's launches).
 template <typename T>
-int cluster_fits(int ctas, size_t smem) {
-    if (cudaFuncSetAttribute(k_tail_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+int cluster_fits(int ctas, size_t smem, int smem_max) {
+    if (cudaFuncSetAttribute(k_tail_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess ||
         cudaFuncSetAttribute(k_tail_smem<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -226,7 +230,7 @@ int plan_precision(amg_hier *h, int smem_max) {
             SmemTailPlan plan = {};
             std::vector<unsigned char> blob;
             size_t bytes = build_plan<T>(hl, ainv, ctas, plan, blob);
-            if (bytes > (size_t)smem_max || !cluster_fits<T>(ctas, bytes)) continue;
+            if (bytes > (size_t)smem_max || !cluster_fits<T>(ctas, bytes, smem_max)) continue;
             PCG_TRY(alloc(h->mem, &h->tail_blob[pi], blob.size()));
             PCG_CK(cudaMemcpy(h->tail_blob[pi], blob.data(), blob.size(), cudaMemcpyHostToDevice));
             h->tail_plan[pi] = plan;
