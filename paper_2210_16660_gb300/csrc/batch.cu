@@ -25,6 +25,8 @@ struct amg_batch_s {
 namespace pcgamg {
 namespace {
 
+int batch_capture(amg_batch_s *b);
+
 bool batch_is_dev(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -39,8 +41,19 @@ void batch_release_graph(amg_batch_s *b) {
     b->exec = nullptr;
 }
 
+// The systems' solves share the device, so they are captured without the
+// shared-memory tail (a 16-SM cluster waits for 16 free SMs while the other
+// branches hold them).
 int batch_build(amg_batch_s *b) {
     batch_release_graph(b);
+    int m = (int)b->hs.size();
+    for (amg_hier *h : b->hs) h->no_tail = 1;
+    int st = batch_capture(b);
+    for (amg_hier *h : b->hs) h->no_tail = 0;
+    return st;
+}
+
+int batch_capture(amg_batch_s *b) {
     int m = (int)b->hs.size();
     std::vector<PendingBody> pb(m);
     PCG_CK(cudaStreamBeginCapture(b->cs0, cudaStreamCaptureModeThreadLocal));

@@ -187,11 +187,7 @@ int amg_set_level_shape(amg_handle h, int level, const int *shape) {
         }
     for (int p = 0; p < 2; p++)
         for (int k = 0; k < 2; k++) h->lev[level].shape[p][k] = (unsigned char)shape[2 * p + k];
-    for (auto &g : h->gexec) {
-        if (g) cudaGraphExecDestroy(g);
-        g = nullptr;
-    }
-    h->graph_gen++;
+    drop_graphs(h);
     return AMG_OK;
 }
 

@@ -246,6 +246,11 @@ struct amg_hier {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_prefix_kernels = 0;
     int graph_body_kernels[2] = {0, 0};
+    // the same without the shared-memory tail (for solves that share the
+    // device: serving lanes; batch graphs capture that way too)
+    cudaGraphExec_t gexec_nt[2] = {nullptr, nullptr};
+    int graph_body_kernels_nt[2] = {0, 0};
+    int no_tail = 0;  // set while capturing a solve that must not use the tail
     int use_graph = 1;
     int no_col16 = 0;
     int pdl = 1;  // programmatic dependent launch between solve kernels
@@ -275,6 +280,7 @@ int solve_multi_impl(amg_hier *h, int k, const double *B, double *X, double rtol
                      double *res_hist, cudaStream_t s);
 void free_multi(amg_hier *h);
 int solve_prepare(amg_hier *h, int mode, int maxit);
+void drop_graphs(amg_hier *h);
 int autotune_impl(amg_hier *h, cudaStream_t s, int reps, int *changed);
 int setup_smem_tail(amg_hier *h);
 template <typename T>

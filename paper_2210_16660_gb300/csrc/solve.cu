@@ -715,7 +715,8 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     prof_end(h, sp1, s);
     int sp2 = prof_begin(h, 5, s);
     // levels handled by separate launches: 0..F-1; the tail runs F..L
-    int F = h->tail_first[prec_index<T>()] > 0 ? h->tail_first[prec_index<T>()] : L;
+    int tf = h->no_tail ? 0 : h->tail_first[prec_index<T>()];
+    int F = tf > 0 ? tf : L;
     // per-level spans (profiling only): level l's down phase is its down
     // sweep and the restriction that leaves it (level 0: the restriction)
     int kernels = 1;  // down sweep of level 0
@@ -895,29 +896,33 @@ namespace {
 
 // Whole solve as one graph: prefix (zero p/q, first residual, condition),
 // then a while node whose body is two iterations plus the condition kernel.
-int build_graph(amg_hier *h, int mode) {
+// tail = false builds the variant without the shared-memory tail.
+int build_graph(amg_hier *h, int mode, bool tail = true) {
     if (!h->cap_stream) PCG_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     cudaStream_t cs = h->cap_stream;
     PendingBody pb;
     int prefix = 0, body_k = 0;
+    cudaGraphExec_t &exec = tail ? h->gexec[mode] : h->gexec_nt[mode];
+    h->no_tail = tail ? 0 : 1;
     PCG_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int st = capture_solve_prefix(h, mode, cs, &pb, &prefix);
     cudaGraph_t full = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &full);
     if (!st && e != cudaSuccess) st = cuda_fail(e, "solve graph capture", __FILE__, __LINE__);
     if (!st) st = capture_solve_body(pb, cs, &body_k);
+    h->no_tail = 0;
     if (st) {
         if (full) cudaGraphDestroy(full);
         return st;
     }
-    e = cudaGraphInstantiate(&h->gexec[mode], full, 0);
+    e = cudaGraphInstantiate(&exec, full, 0);
     cudaGraphDestroy(full);
     if (e != cudaSuccess) {
-        h->gexec[mode] = nullptr;
+        exec = nullptr;
         return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
     }
     h->graph_prefix_kernels = prefix;
-    h->graph_body_kernels[mode] = body_k;
+    (tail ? h->graph_body_kernels : h->graph_body_kernels_nt)[mode] = body_k;
     return AMG_OK;
 }
 
@@ -955,10 +960,7 @@ int set_profile(amg_hier *h, int enable) {
 void free_profile(amg_hier *h) {
     for (auto &e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
-    for (auto &g : h->gexec) {
-        if (g) cudaGraphExecDestroy(g);
-        g = nullptr;
-    }
+    drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->cap_stream = nullptr;
 }
@@ -1085,13 +1087,20 @@ int autotune_impl(amg_hier *h, cudaStream_t s, int reps, int *changed) {
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    for (auto &g : h->gexec) {
-        if (g) cudaGraphExecDestroy(g);
-        g = nullptr;
-    }
-    h->graph_gen++;
+    drop_graphs(h);
     PCG_CK(cudaStreamSynchronize(s));
     return st;
+}
+
+// Drops every captured whole-solve graph of h (they are rebuilt on the next
+// solve) and marks batch graphs holding h as stale.
+void drop_graphs(amg_hier *h) {
+    for (auto *set : {h->gexec, h->gexec_nt})
+        for (int m = 0; m < 2; m++) {
+            if (set[m]) cudaGraphExecDestroy(set[m]);
+            set[m] = nullptr;
+        }
+    h->graph_gen++;
 }
 
 // Makes room for maxit+1 history values (invalidates captured graphs).
@@ -1100,11 +1109,7 @@ int ensure_hist(amg_hier *h, int maxit) {
     release(h->mem, h->hist);
     h->hist_cap = maxit + 1;
     PCG_TRY(alloc(h->mem, &h->hist, h->hist_cap));
-    for (auto &g : h->gexec) {
-        if (g) cudaGraphExecDestroy(g);
-        g = nullptr;
-    }
-    h->graph_gen++;
+    drop_graphs(h);
     return AMG_OK;
 }
 
@@ -1115,7 +1120,7 @@ int ensure_hist(amg_hier *h, int maxit) {
 // writes x (host or device; zeros when b = 0) and the outcome.
 int solve_prepare(amg_hier *h, int mode, int maxit) {
     PCG_TRY(ensure_hist(h, maxit));
-    if (!h->gexec[mode]) PCG_TRY(build_graph(h, mode));
+    if (!h->gexec_nt[mode]) PCG_TRY(build_graph(h, mode, false));
     return AMG_OK;
 }
 
@@ -1133,7 +1138,7 @@ int solve_launch(amg_hier *h, int mode, const double *b, const double *x0, doubl
     c0.restart = 1;
     *h->ctl_host = c0;
     PCG_CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-    PCG_CK(cudaGraphLaunch(h->gexec[mode], s));
+    PCG_CK(cudaGraphLaunch(h->gexec_nt[mode], s));
     PCG_CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     return AMG_OK;
 }
@@ -1147,7 +1152,7 @@ int solve_collect(amg_hier *h, int mode, double *x, cudaStream_t s, int *status,
         PCG_LAUNCH_CK();
     }
     PCG_CK(cudaMemcpyAsync(x, h->x, sizeof(double) * n, cudaMemcpyDefault, s));
-    int64_t k = h->graph_prefix_kernels + (int64_t)c.bodies * h->graph_body_kernels[mode];
+    int64_t k = h->graph_prefix_kernels + (int64_t)c.bodies * h->graph_body_kernels_nt[mode];
     h->launches += k;
     if (kernels) *kernels = k;
     if (status) *status = c.done ? c.status : AMG_ERR_NOCONV;
@@ -1170,11 +1175,7 @@ int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, 
         release(h->mem, h->hist);
         h->hist_cap = maxit + 1;
         PCG_TRY(alloc(h->mem, &h->hist, h->hist_cap));
-        for (auto &g : h->gexec) {
-            if (g) cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
-        h->graph_gen++;
+        drop_graphs(h);
     }
     bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
     PCG_CK(cudaMemcpyAsync(h->b, b, sizeof(double) * n, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
