@@ -28,7 +28,7 @@ namespace cg = cooperative_groups;
 namespace pcgamg {
 namespace {
 
-constexpr int kTThreads = 512;
+constexpr int kTThreads = 1024;
 template <typename T>
 __device__ __forceinline__ T *remote(cg::cluster_group &cl, T *p, uint32_t ref) {
     return cl.map_shared_rank(p, (unsigned)(ref >> 24)) + (ref & 0xffffffu);
@@ -36,6 +36,27 @@ __device__ __forceinline__ T *remote(cg::cluster_group &cl, T *p, uint32_t ref) 
 
 template <typename T>
 __device__ __forceinline__ T *at(unsigned char *smem, int off) { return reinterpret_cast<T *>(smem + off); }
+
+// sum_q val[q] vec(cp[q]) over row i, entries in storage order. The remote
+// loads of 8 entries are issued before their FMAs (the last chunk masked),
+// so a row costs about one distributed-shared-memory latency per 8 entries
+// instead of one per entry; the FMAs keep their order.
+template <typename T>
+__device__ __forceinline__ T row_dot(cg::cluster_group &cl, const int32_t *rp, const uint32_t *cp, const T *val,
+                                     T *vec, int i) {
+    constexpr int U = 8;
+    T acc = 0;
+    int e = rp[i + 1];
+    for (int q = rp[i]; q < e; q += U) {
+        T x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) x[u] = (q + u < e) ? *remote(cl, vec, cp[q + u]) : T(0);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (q + u < e) acc += val[q + u] * x[u];
+    }
+    return acc;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kTThreads, 1) k_tail_smem(SmemTailPlan plan, const unsigned char *__restrict__ blob,
@@ -75,8 +96,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tail_smem(SmemTailPlan plan, c
         const T *p = at<T>(smem, Lv.off_p);
         T *b = at<T>(smem, Lv.off_b), *t = at<T>(smem, Lv.off_t), *xpre = at<T>(smem, Lv.off_xpre);
         for (int i = tid; i < rows; i += nth) {
-            T acc = 0;
-            for (int q = rp[i]; q < rp[i + 1]; q++) acc += val[q] * *remote(cl, xpre, cp[q]);
+            T acc = row_dot(cl, rp, cp, val, xpre, i);
             t[i] = p[i] * (b[i] - acc);
         }
         cl.sync();
@@ -107,7 +127,19 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tail_smem(SmemTailPlan plan, c
         for (int row = warp; row < rows; row += nw) {
             const double *a = ainv + (size_t)row * C.n;
             double s = 0.0;
-            for (int j = lane; j < C.n; j += 32) s += a[j] * *remote(cl, bl, pack(j / C.rpc, j % C.rpc));
+            // the lane's entries j = lane, lane + 32, ... in the order of
+            // k_coarse, their b_L values loaded 4 at a time ahead of the FMAs
+            for (int j0 = lane; j0 < C.n; j0 += 4 * 32) {
+                double bv[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    int j = j0 + 32 * u;
+                    bv[u] = j < C.n ? *remote(cl, bl, pack(j / C.rpc, j % C.rpc)) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (j0 + 32 * u < C.n) s += a[j0 + 32 * u] * bv[u];
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
             if (lane == 0) xL[row] = (T)s;
@@ -136,8 +168,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tail_smem(SmemTailPlan plan, c
         const T *dinv = at<T>(smem, Lv.off_dinv);
         T *b = at<T>(smem, Lv.off_b), *x = at<T>(smem, Lv.off_x);
         for (int i = tid; i < rows; i += nth) {
-            T acc = 0;
-            for (int q = rp[i]; q < rp[i + 1]; q++) acc += val[q] * *remote(cl, xp, cp[q]);
+            T acc = row_dot(cl, rp, cp, val, xp, i);
             x[i] = xp[i] + dinv[i] * (b[i] - acc);
         }
         if (k > 0) cl.sync();
