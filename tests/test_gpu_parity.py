@@ -339,3 +339,36 @@ def test_every_launch_shape_gives_the_same_bits(mode):
         amg.set_level_shape(0, [0, 0, 0, 0])
     with pytest.raises(B.AmgError):
         amg.set_level_shape(1, [8, 0, 0, 0])
+
+
+def test_hand_worked_pairwise_aggregation_on_gpu():
+    """The device setup on the example worked by hand from Sec. 3.1
+    (tests/golden/path5_pairwise_aggregation.json): pass aggregates, the
+    composed map and the level-1 Galerkin matrix."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "path5_pairwise_aggregation.json")))
+    Ad = np.array(g["matrix_dense"], float)
+    n = Ad.shape[0]
+    rows, cols = np.nonzero(Ad)
+    rp = np.zeros(n + 1, np.int32)
+    np.cumsum(np.bincount(rows, minlength=n), out=rp[1:])
+    A = W.CSR(n, rp, cols.astype(np.int32), Ad[rows, cols])
+    amg = B.AMG.from_csr(A, coarse_max=1, n_pass=2)
+    assert len(amg.info()) == g["levels"]
+    a0, nc0 = amg.level_agg(0, 0)
+    assert list(a0) == g["pass0"]["agg"] and nc0 == len(g["pass0"]["w_c"])
+    a1, nc1 = amg.level_agg(0, 1)
+    assert list(a1) == g["pass1"]["agg"] and nc1 == g["pass1"]["n_c"]
+    ac, _ = amg.level_agg(0)
+    assert list(ac) == g["level0_composed"]["agg"]
+    rp1, ci1, v1 = amg.level_csr(1)
+    A1 = np.zeros((2, 2))
+    for i in range(2):
+        A1[i, ci1[rp1[i]:rp1[i + 1]]] = v1[rp1[i]:rp1[i + 1]]
+    np.testing.assert_allclose(A1, g["level1"]["A"], rtol=1e-15, atol=1e-15)
+    b = torch.ones(n, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    r = amg.solve(b, x, rtol=1e-12)
+    assert r.status == 0
+    np.testing.assert_allclose(x.cpu().numpy(), np.linalg.solve(Ad, np.ones(n)), rtol=1e-10)

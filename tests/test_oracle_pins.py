@@ -376,3 +376,47 @@ def test_indefinite_rejected():
     a = np.array([[1.0, 2.0, 0.0], [2.0, 1.0, 0.5], [0.0, 0.5, 1.0]])
     with pytest.raises(RuntimeError, match="status 3"):
         O.Hierarchy(_csr_from_dense(a), coarse_max=8, n_pass=1)
+
+
+def test_hand_worked_pairwise_aggregation():
+    """The oracle against a small example worked by hand from the equations
+    of Sec. 3.1 (tests/golden/path5_pairwise_aggregation.json): edge weights,
+    tie-break, numbering, normalised tentative prolongator, w_c and both
+    Galerkin products of two passes."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "path5_pairwise_aggregation.json")))
+    Ad = np.array(g["matrix_dense"], float)
+    n = Ad.shape[0]
+    rows, cols = np.nonzero(Ad)
+    rp = np.zeros(n + 1, np.int32)
+    np.cumsum(np.bincount(rows, minlength=n), out=rp[1:])
+    A = W.CSR(n, rp, cols.astype(np.int32), Ad[rows, cols])
+    w = np.ones(n)
+    for i, j in zip(rows, cols):
+        if i < j:
+            assert O.weight(Ad[i, j], Ad[i, i], Ad[j, j], w[i], w[j]) == pytest.approx(g["edge_weight"], rel=1e-15)
+    mate = O.match(A, w)
+    assert list(mate) == g["pass0"]["mate"]
+    agg, p, wc = O.aggregate(A, mate, w)
+    assert list(agg) == g["pass0"]["agg"]
+    np.testing.assert_allclose(p, g["pass0"]["p"], rtol=1e-15)
+    np.testing.assert_allclose(wc, g["pass0"]["w_c"], rtol=1e-15)
+    rpc, cic, vc = O.rap(A, agg, p, len(wc))
+    Ac = np.zeros((len(wc), len(wc)))
+    for i in range(len(wc)):
+        Ac[i, cic[rpc[i]:rpc[i + 1]]] = vc[rpc[i]:rpc[i + 1]]
+    np.testing.assert_allclose(Ac, g["pass0"]["A_c"], rtol=1e-15, atol=1e-15)
+    h = O.Hierarchy(A, coarse_max=1, n_pass=2)
+    assert h.nlevels == g["levels"]
+    a1, nc1 = h.pass_agg(0, 1)
+    assert list(a1) == g["pass1"]["agg"] and nc1 == g["pass1"]["n_c"]
+    L1 = h.level(1)
+    A1 = np.zeros((L1["n"], L1["n"]))
+    for i in range(L1["n"]):
+        A1[i, L1["col"][L1["row_ptr"][i]:L1["row_ptr"][i + 1]]] = L1["val"][L1["row_ptr"][i]:L1["row_ptr"][i + 1]]
+    np.testing.assert_allclose(A1, g["level1"]["A"], rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(L1["w"], g["level1"]["w"], rtol=1e-15)
+    cagg, cp = h.level_agg(0)
+    assert list(cagg) == g["level0_composed"]["agg"]
+    np.testing.assert_allclose(cp, g["level0_composed"]["p"], rtol=1e-15)
