@@ -56,3 +56,36 @@ def test_bad_arguments_are_rejected_on_the_host():
     assert lib.pcg_solve(None, None, None, 1e-8, 10, None, None, None) == binding.ERR_ARG
     assert b"NULL handle" in lib.amg_last_error()
     assert lib.amg_set_allocator(ctypes.c_void_p(1), None, None) == binding.ERR_ARG
+
+
+def test_host_side_checks_of_the_batched_serving_and_tuning_calls():
+    """Every entry point that takes a handle, batch or server rejects NULL
+    and bad sizes on the host with AMG_ERR_ARG and a message, without a
+    device call; the host-only planner and the server defaults need none."""
+    from paper_2210_16660_gb300 import binding
+    lib = binding.load()
+    E = binding.ERR_ARG
+    i = ctypes.c_int()
+    assert lib.pcg_solve_multi(None, 4, None, None, 1e-8, 10, None, None, None) == E
+    out = ctypes.c_void_p()
+    assert lib.amg_batch_create(0, None, ctypes.byref(out)) == E
+    assert lib.pcg_solve_batch(None, None, None, 1e-8, 10, None, None, None) == E
+    assert lib.amg_autotune(None, 5, ctypes.byref(i), None) == E
+    shape = (ctypes.c_int * 4)()
+    assert lib.amg_level_shape(None, 1, shape) == E
+    assert lib.amg_set_level_shape(None, 1, shape) == E
+    assert lib.amg_profile_levels(None, 1, None, None) == E
+    assert lib.amg_residual_noalloc(None, None, None, None, None, None) == E
+    p = binding.ServerParams()
+    lib.amg_server_default_params(ctypes.byref(p))
+    assert (p.mode, p.slots, p.max_engines, p.chunk, p.solo, p.batch_min) == (binding.MODE_FCG32, 4, 2, 4, 1, 3)
+    assert lib.amg_server_create(ctypes.byref(p), 0, None, None, ctypes.byref(out)) == E
+    t = ctypes.c_int64()
+    assert lib.amg_server_submit(None, 0, None, None, None, ctypes.byref(t)) == E
+    assert lib.amg_server_progress(None, 0, ctypes.byref(i)) == E
+    assert lib.amg_server_result(None, 1, None, None, None, None, None, None) == E
+    assert lib.amg_server_info(None, None, None, None, None, None) == E
+    assert lib.amg_server_mesh_info(None, 0, None, None, None, None) == E
+    assert lib.amg_last_error() != b""
+    lib.amg_server_destroy(None)
+    lib.amg_batch_destroy(None)
