@@ -116,6 +116,11 @@ int scan_exclusive(Mem &M, const Tin *in, T *out, int64_t n, T *total_host, cuda
     return AMG_OK;
 }
 
+__global__ void k_narrow(const int64_t *__restrict__ in, int32_t *__restrict__ out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int32_t)in[i];
+}
+
 // ------------------------------------------------------------ validation
 // flag bits: 1 column out of range or unsorted, 2 diagonal missing or <= 0,
 // 4 row pointer decreasing or wrong bounds, 8 not exactly symmetric.
@@ -671,9 +676,23 @@ int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
     PCG_TRY(alloc(M, &S.sptr, (size_t)S.nslices + 1));
     k_sell_width<<<grid_for(S.nslices), kBlock, 0, s>>>(n, S.nslices, lv.A.rp, sw);
     PCG_LAUNCH_CK();
-    int32_t tot = 0;
-    PCG_TRY(scan_exclusive(M, sw, S.sptr, S.nslices, &tot, s));
+    // slice offsets are int32: scan in int64 and refuse a level whose padded
+    // entries do not fit, instead of letting the offsets wrap
+    int64_t *sp64 = nullptr;
+    PCG_TRY(alloc(M, &sp64, (size_t)S.nslices + 1));
+    int64_t tot64 = 0;
+    PCG_TRY(scan_exclusive(M, sw, sp64, S.nslices, &tot64, s));
     release(M, sw);
+    if (tot64 > (int64_t)INT32_MAX) {
+        release(M, sp64);
+        set_error("amg_setup: level with %d rows needs %lld sliced-ELL entries (int32 offsets allow %d)", n,
+                  (long long)tot64, INT32_MAX);
+        return AMG_ERR_ARG;
+    }
+    k_narrow<<<grid_for((int64_t)S.nslices + 1), kBlock, 0, s>>>(sp64, S.sptr, (int64_t)S.nslices + 1);
+    PCG_LAUNCH_CK();
+    release(M, sp64);
+    int32_t tot = (int32_t)tot64;
     S.nnz_pad = tot;
     PCG_TRY(alloc(M, &S.col, tot));
     PCG_TRY(alloc(M, &S.v64, tot));
