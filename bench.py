@@ -629,6 +629,18 @@ def run_ours(args):
                 "avg_launch_ms": cand[dom]["avg_ms"],
                 "timing": "CUDA events around each launch in a profiled pass of the same steps"}
 
+    # the same kernel against the float64 pipe: one FMA per stored entry plus
+    # the p.q dot, at 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal at the
+    # 2070 MHz clock GB300 reports)
+    sp_entries = amg.level_layout(0)["stored"] + n0
+    fp64_peak = 152 * 2 * 2 * 2.070e9 / 1e9
+    roofline_fp64 = None
+    if "spmv" in per_kernel:
+        gf = 2 * sp_entries / (per_kernel["spmv"]["avg_ms"] * 1e-3) / 1e9
+        roofline_fp64 = {"kernel": "k_spmv", "bound": "alu", "achieved": gf, "peak": fp64_peak, "unit": "GFLOP/s",
+                         "frac": gf / fp64_peak, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                         "flops_per_launch": 2 * sp_entries}
+
     if rank == 0:
         h2d = 16 * n0
         d2h = 8 * n0 + 8 * (int(statistics.median(e2e_iters)) + 1)
@@ -655,6 +667,7 @@ def run_ours(args):
             "autotune": tune,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline,
+            "roofline_fp64_pipe": roofline_fp64,
             "kernels": per_kernel,
             "kernels_fp64": per_kernel64,
             "levels": levels32,
