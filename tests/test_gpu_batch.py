@@ -72,3 +72,30 @@ def test_batch_rejects_duplicate_handles():
     probs, amgs = _systems([9], ["fcg32"])
     with pytest.raises(B.AmgError):
         B.Batch([amgs[0], amgs[0]])
+
+
+def test_full_size_48_systems():
+    """The benchmark's batch: 48 graded systems of 24^3..112^3 nodes (23.0M
+    dofs) in one launch. Every system meets rtol by the host's own residual,
+    equals its own pcg_solve bit for bit, and the three smallest agree with
+    the oracle."""
+    sizes = W.batch_sizes(48, 24, 112, seed=3)
+    probs = [W.make_problem(Nn, 1.04, seed=3000 + k) for k, Nn in enumerate(sizes)]
+    amgs = [B.AMG.from_csr(p.A, mode="fcg32") for p in probs]
+    batch = B.Batch(amgs)
+    bs = [torch.from_numpy(p.b).cuda() for p in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    st, it, sts = batch.solve(bs, xs, rtol=RTOL, maxit=500)
+    assert st == 0 and list(sts) == [0] * 48
+    smallest = sorted(range(48), key=lambda k: sizes[k])[:3]
+    for k, p in enumerate(probs):
+        xh = xs[k].cpu().numpy()
+        assert np.linalg.norm(p.b - W.spmv(p.A, xh)) <= RTOL * np.linalg.norm(p.b), k
+        x1 = torch.zeros_like(bs[k])
+        r = amgs[k].solve(bs[k], x1, rtol=RTOL, maxit=500, hist=False)
+        assert r.iters == it[k] and torch.equal(x1, xs[k]), k
+        if k in smallest:
+            ref = O.Hierarchy(p.A, n_pass=2).solve(p.b, rtol=RTOL, maxit=1000, mode="fcg32")
+            assert abs(ref["iters"] - int(it[k])) <= 1
+            assert np.linalg.norm(xh - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+    batch.close()

@@ -247,3 +247,42 @@ def test_bad_server_arguments(meshes):
         srv.result(12345)
     assert srv.progress() == 0                # nothing to do
     srv.close()
+
+
+def test_full_size_serving_meshes():
+    """The benchmark's serving meshes (64^3, 128^3 and 192^3, resident) with
+    the default server: a burst of requests over all three, every one within
+    rtol by the host's own residual for one request per mesh, each equal to
+    its result served alone in the same kind of place, and the 64^3 request
+    against the oracle."""
+    meshes = S.prepare_meshes((64, 128, 192), ratio=1.04, seed=5, pool=2)
+    srv = S.make_server(meshes, "fcg32")
+    reqs = [(i % 3, (i // 3) % 2) for i in range(12)]
+    xs, tickets = [], []
+    for m, k in reqs:
+        b, x0 = meshes[m].steps[k]
+        x = torch.empty_like(b)
+        st, t = srv.submit(m, b, x0, x)
+        assert st == B.OK
+        xs.append(x)
+        tickets.append(t)
+    res = srv.drain(tickets)
+    assert all(res[t].status == B.OK and res[t].true_rel <= RTOL for t in tickets)
+    alone = S.make_server(meshes, "fcg32", solo=False)
+    for j in range(3):
+        m, k = reqs[j]
+        b, x0 = meshes[m].steps[k]
+        bh, xh = b.cpu().numpy(), xs[j].cpu().numpy()
+        A = meshes[m].problem.A
+        assert np.linalg.norm(bh - W.spmv(A, xh)) <= RTOL * np.linalg.norm(bh)
+        r = res[tickets[j]]
+        xa, ra = (_serve_alone(alone, m, b, x0) if r.lane == 1 else _lone_solve(meshes[m], "fcg32", b, x0))
+        assert torch.equal(xa, xs[j]) and ra.iters == r.iters, (j, r.lane)
+        if m == 0:
+            ref = O.Hierarchy(A, n_pass=2).solve(bh, x0=x0.cpu().numpy(), rtol=RTOL, maxit=1000, mode="fcg32")
+            assert abs(ref["iters"] - r.iters) <= 1
+            assert np.linalg.norm(xh - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+    alone.close()
+    srv.close()
+    for mm in meshes:
+        mm.amg.close()
