@@ -142,3 +142,46 @@ def test_problem_rhs():
     p = W.make_problem(6, 1.04, seed=3)
     assert np.all(p.x_star[p.wall] == 0)
     assert np.allclose(p.b, p.A.to_dense() @ p.x_star, rtol=1e-14, atol=1e-14)
+
+
+def test_poisson_arrivals_and_choices():
+    """The serving stream: arrivals start at 0, never go back, and their gaps
+    have the exponential mean 1/rate; an infinite rate queues everything at
+    0; mesh choices are uniform."""
+    a = W.poisson_arrivals(20.0, 20000, seed=5)
+    assert a[0] == 0.0 and np.all(np.diff(a) >= 0.0)
+    gaps = np.diff(a)
+    assert abs(gaps.mean() - 1 / 20.0) < 0.05 / 20.0
+    assert abs(np.median(gaps) - np.log(2) / 20.0) < 0.05 / 20.0   # exponential median
+    assert not W.poisson_arrivals(float("inf"), 7, seed=5).any()
+    np.testing.assert_array_equal(a, W.poisson_arrivals(20.0, 20000, seed=5))
+    c = W.uniform_choices(30000, 3, seed=5)
+    assert set(np.unique(c)) == {0, 1, 2}
+    assert np.all(np.abs(np.bincount(c) / 30000 - 1 / 3) < 0.01)
+
+
+def test_time_step_chain():
+    """Each step is warm-started from the previous exact solution, its
+    right-hand side is A x*_t, and x*_t stays zero on the Dirichlet wall."""
+    prob = W.make_problem(8, 1.04, seed=2)
+    chain = W.time_steps(prob, prob.x_star, 3, seed=9)
+    prev = prob.x_star
+    for b, x0, xs in chain:
+        np.testing.assert_array_equal(x0, prev)
+        np.testing.assert_array_equal(b, W.spmv(prob.A, xs))
+        assert not xs[prob.wall].any()
+        rms = np.sqrt(np.mean(prev * prev))
+        assert 0 < np.linalg.norm(xs - prev) / (rms * np.sqrt(prob.A.n)) < 0.02
+        prev = xs
+
+
+def test_capped_grading_keeps_the_spacing_range():
+    """Meshes up to 128^3 keep the ratio; finer ones get the ratio whose
+    largest/smallest z spacing matches the 128^3 mesh's (to 4 decimals)."""
+    assert W.capped_grading(64, 1.04) == 1.04 and W.capped_grading(128, 1.04) == 1.04
+    for N in (160, 192, 320):
+        r = W.capped_grading(N, 1.04)
+        assert r < 1.04
+        assert abs(np.log(r ** (N - 2)) - np.log(1.04 ** 126)) < 0.01 * np.log(1.04 ** 126) * 5
+        h = W.graded_spacing(N, r)
+        assert abs(h.max() / h.min() - r ** (N - 2)) < 1e-9 * r ** (N - 2)
