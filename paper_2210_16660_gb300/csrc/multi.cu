@@ -276,26 +276,35 @@ __global__ void __launch_bounds__(kMB) k_restrict_m(int nc, const int32_t *__res
     }
 }
 
-// x_L = A_L^{-1} b_L for K columns (float64, two columns per thread).
+// x_L = A_L^{-1} b_L for K columns (float64): one warp per (row, pair of
+// columns), lanes striding over the row with coalesced loads of A_L^{-1},
+// then the shuffle tree -- the order of k_coarse, per column.
 template <typename TO, int K>
 __global__ void __launch_bounds__(kMB) k_coarse_m(int nL, const double *__restrict__ ainv,
                                                  const double *__restrict__ bL, TO *__restrict__ xL,
                                                  const CtlM *__restrict__ ctl) {
     constexpr int V = 2;
     if (ctl->done) return;
-    MK_LIVE(V)
-    MK_FOR(live_ ? nL : 0, V) {
-        MK_IDX(V)
-        const double *a = ainv + (int64_t)i * nL;
-        double s0 = 0.0, s1 = 0.0;
-        for (int j = 0; j < nL; j++) {
-            double aj = ldg(a + j);
-            double2 bj = __ldg(reinterpret_cast<const double2 *>(bL + (int64_t)j * K + c0));
-            s0 += aj * bj.x;
-            s1 += aj * bj.y;
-        }
-        xL[e0] = (TO)s0;
-        xL[e0 + 1] = (TO)s1;
+    int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (warp >= nL * (K / V)) return;  // whole warps
+    int row = warp / (K / V), c0 = (warp % (K / V)) * V;
+    if (!group_live<V>(ctl, c0)) return;
+    const double *a = ainv + (int64_t)row * nL;
+    double s0 = 0.0, s1 = 0.0;
+    for (int j = lane; j < nL; j += 32) {
+        double aj = ldg(a + j);
+        double2 bj = __ldg(reinterpret_cast<const double2 *>(bL + (int64_t)j * K + c0));
+        s0 += aj * bj.x;
+        s1 += aj * bj.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) {
+        xL[(int64_t)row * K + c0] = (TO)s0;
+        xL[(int64_t)row * K + c0 + 1] = (TO)s1;
     }
 }
 
@@ -720,7 +729,8 @@ int launch_vcycle_m(amg_hier *h, MultiWS &W, cudaStream_t s) {
                 lv.nc, lv.rptr, lv.ridx, P::t(mv), P::b(W.lev[l + 1]), P::dinv(lev[l + 1]), P::xpre(W.lev[l + 1]),
                 ctl);
     }
-    k_coarse_m<T, K><<<grid_of((int64_t)h->nL * (K / 2)), kMB, 0, s>>>(h->nL, h->Ainv, W.bL, P::x(W.lev[L]), ctl);
+    k_coarse_m<T, K><<<grid_of((int64_t)h->nL * (K / 2) * 32), kMB, 0, s>>>(h->nL, h->Ainv, W.bL, P::x(W.lev[L]),
+                                                                            ctl);
     for (int l = L - 1; l >= 1; l--) {
         Level &lv = lev[l];
         MultiLevel &mv = W.lev[l];
