@@ -62,18 +62,20 @@ template <typename T>
 __global__ void __launch_bounds__(kTThreads, 1) k_tail_smem(SmemTailPlan plan, const unsigned char *__restrict__ blob,
                                                             const T *__restrict__ bF, const T *__restrict__ xpreF,
                                                             T *__restrict__ xF, const Ctl *__restrict__ ctl) {
-    pdl_enter();
     cg::cluster_group cl = cg::this_cluster();
-    if (ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x, nth = blockDim.x;
-    // 1. this CTA's static data (matrices, maps, coarsest rows) in one copy
+    // 1. this CTA's static data (matrices, maps, coarsest rows) in one copy.
+    // It is written once at setup, so the copy runs before the wait for the
+    // preceding kernel and overlaps that kernel's end.
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(blob + (size_t)rank * plan.static_bytes);
         uint4 *dst = reinterpret_cast<uint4 *>(smem);
         for (int k = tid; k < plan.static_bytes / 16; k += nth) dst[k] = __ldg(src + k);
     }
+    pdl_enter();
+    if (ctl->done) return;
     // ... and the entry level's b and xpre rows (written by the previous kernel)
     {
         const SmemTailLevel &F = plan.lev[0];
