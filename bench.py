@@ -65,6 +65,7 @@ def parse_args(argv=None):
     ap.add_argument("--serve-batch-min", type=int, default=3)
     ap.add_argument("--serve-no-solo", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the fixed sweep launch shapes")
+    ap.add_argument("--no-refresh", action="store_true", help="skip the partial-reuse (amg_refresh) measurement")
     return ap.parse_args(argv)
 
 
@@ -549,6 +550,39 @@ def run_ours(args):
             mm.amg.close()
         del meshes
 
+    # partial reuse (Sec. 4): the same mesh with new coefficients D A D; the
+    # hierarchy keeps its aggregates and rebuilds its coarse operators,
+    # smoothers and coarsest inverse, against a fresh setup of the new matrix
+    refresh = {}
+    if not args.no_refresh:
+        A2 = W.rescaled(prob.A, seed=args.seed + 2000)
+        b2 = torch.from_numpy(W.spmv(A2, W.normals(args.seed + 2001, prob.A.n))).to(device)
+        ra = B.AMG.from_csr(prob.A, mode="fcg32", stream=stream)
+        times = []
+        for k in range(3):
+            ra.refresh(A2 if k % 2 == 0 else prob.A, stream=stream)
+            times.append(ra.refresh_ms())
+        ra.refresh(A2, stream=stream)
+        times.append(ra.refresh_ms())
+        fresh = B.AMG.from_csr(A2, mode="fcg32", stream=stream)
+        row = {"workload": f"{prob.name} with coefficients (d_i d_j) a_ij, d = 1 + 0.5 u",
+               "refresh_ms": statistics.median(times), "setup_ms": fresh.setup_times()["total_ms"]}
+        for name, h in (("refreshed", ra), ("fresh", fresh)):
+            xr = torch.zeros_like(b2)
+            h.solve(b2, xr, rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)   # graph capture
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            xr.zero_()
+            e0.record(stream)
+            r = h.solve(b2, xr, rtol=args.rtol, maxit=args.maxit, stream=stream, hist=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r.status != 0:
+                raise RuntimeError(f"refresh check solve failed: {r.message}")
+            row[name] = {"iters": r.iters, "solve_ms": e0.elapsed_time(e1), "true_rel": r.true_rel}
+        refresh = row
+        ra.close()
+        fresh.close()
+
     # end to end through the C ABI with host buffers (pinned), copies inside the call
     pin_b = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
     pin_x = torch.zeros(prob.A.n, dtype=torch.float64).pin_memory().numpy()
@@ -660,6 +694,7 @@ def run_ours(args):
             "multi_rhs": multi,
             "batch": batch,
             "serving": serving,
+            "refresh": refresh,
             "fp64": {"value": solves / (f64_ms / 1e3), "unit": UNIT, "ms_per_step": f64_ms / args.steps,
                      "latency_ms": {"p50": pct(f64["lat_ms"], 50), "p99": pct(f64["lat_ms"], 99)},
                      "iters": statistics.median(f64["iters"]), "gpu_launches": f64["launches"]},

@@ -105,6 +105,28 @@ int amg_set_allocator(amg_alloc_fn alloc, amg_free_fn dealloc, void *ctx);
  * not SPD), AMG_ERR_COARSE, AMG_ERR_CUDA. *out is NULL on error. */
 int amg_setup(const amg_csr *A, const amg_params *p, void *stream, amg_handle *out);
 
+/* Partial reuse of the hierarchy (Sec. 4: when the mesh topology stays and
+ * only the coefficients change, the same prolongators/restrictors rebuild the
+ * hierarchy and its smoothers). A holds new values of the finest matrix on
+ * exactly the sparsity pattern h was built on (same n, nnz, row pointers and
+ * columns; host or device, as in amg_setup; copied, the caller keeps it).
+ * Every pass keeps its aggregates and tentative-prolongator weights (they do
+ * not depend on the values); the Galerkin products, the l1 diagonals, the
+ * float32 copies and the dense coarsest inverse are formed again, with the
+ * arithmetic of amg_setup, so amg_refresh(h, A0) with the values h was built
+ * on reproduces h bit for bit. Device arrays keep their addresses: solve
+ * graphs, batches and servers built on h stay valid. The call synchronises
+ * stream and must not overlap a solve on h.
+ * Errors: AMG_ERR_ARG (NULL, other sizes or pattern, invalid or not exactly
+ * symmetric values: h is unchanged), AMG_ERR_BREAKDOWN (coarsest matrix not
+ * SPD), AMG_ERR_OOM, AMG_ERR_CUDA. After an error other than AMG_ERR_ARG,
+ * solves on h (single, multi-column, batched, served) return AMG_ERR_ARG
+ * until a later amg_refresh succeeds. */
+int amg_refresh(amg_handle h, const amg_csr *A, void *stream);
+
+/* Host time (ms) of the last successful amg_refresh of h. */
+int amg_refresh_time(amg_handle h, double *ms);
+
 /* Select the solve mode of a handle (AMG_MODE_PCG64 / AMG_MODE_FCG32). */
 int amg_set_mode(amg_handle h, int mode);
 

@@ -64,6 +64,8 @@ def load():
     lib.or_chol_solve.argtypes = [I, _f64p, _f64p, _f64p]
     lib.or_setup.restype = I
     lib.or_setup.argtypes = [I, _i32p, _i32p, _f64p, I, I, I, C.POINTER(P)]
+    lib.or_refresh.restype = I
+    lib.or_refresh.argtypes = [P, I, _i32p, _i32p, _f64p]
     lib.or_free.restype = None
     lib.or_free.argtypes = [P]
     lib.or_nlevels.restype = I
@@ -182,6 +184,15 @@ class Hierarchy:
             raise RuntimeError(f"oracle setup status {st}")
         self._h = h
         self.n = n
+
+    def refresh(self, A) -> int:
+        """Partial reuse (Sec. 4): new values of the finest matrix on the same
+        pattern; the aggregates and prolongator weights are kept, the Galerkin
+        products, smoothers and coarsest factor are formed again. Returns the
+        status (ERR_ARG for another pattern; the hierarchy is then unchanged
+        unless a later level failed)."""
+        n, rp, ci, v = _csr_args(A)
+        return load().or_refresh(self._h, n, rp, ci, v)
 
     def close(self):
         if getattr(self, "_h", None):

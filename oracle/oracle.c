@@ -531,6 +531,100 @@ int or_setup(int n, const int32_t *rp, const int32_t *ci, const double *v,
     return OR_OK;
 }
 
+/* ------------------------------------------------- partial reuse (Sec. 4)
+ * When the mesh (the sparsity pattern) stays and only the coefficients
+ * change, the hierarchy can be rebuilt with the same prolongators: the
+ * aggregates of every pass and their weights are kept, and the Galerkin
+ * products, the l1 smoothers and the coarsest factor are formed again from
+ * the new values (Sec. 4, reuse of the prolongators/restrictors).
+ *
+ * The weights of a pass depend only on its aggregates and on w (w = 1 on
+ * level 0, then the aggregate norms), not on the matrix values, so they are
+ * restated here from the kept maps with the arithmetic of or_aggregate:
+ * pair {i < j}: p = w / ||(w_i, w_j)||, singleton: p = w / |w|, and a row
+ * left out of the coarse space (agg = -1) keeps p = 0.
+ */
+static void pass_weights(int m, const int32_t *agg, int nc, const double *w, double *p, double *wc) {
+    int32_t *first = (int32_t *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int32_t));
+    int32_t *second = (int32_t *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int32_t));
+    for (int I = 0; I < nc; I++) { first[I] = -1; second[I] = -1; }
+    for (int i = 0; i < m; i++) {
+        int I = agg[i];
+        if (I < 0) { p[i] = 0.0; continue; }
+        if (first[I] < 0) first[I] = i; else second[I] = i;
+    }
+    for (int I = 0; I < nc; I++) {
+        int i = first[I], j = second[I];
+        if (j >= 0) {
+            double nrm = sqrt(w[i] * w[i] + w[j] * w[j]);
+            p[i] = w[i] / nrm; p[j] = w[j] / nrm;
+            wc[I] = nrm;
+        } else {
+            p[i] = w[i] / fabs(w[i]);
+            wc[I] = fabs(w[i]);
+        }
+    }
+    free(first); free(second);
+}
+
+/* New values v for the finest matrix, whose pattern (rp, ci) must be the one
+ * the hierarchy was built on (else OR_ERR_ARG and the hierarchy is kept). */
+int or_refresh(hier_t *h, int n, const int32_t *rp, const int32_t *ci, const double *v) {
+    level_t *l0 = &h->lev[0];
+    if (n != l0->A.n || rp[n] != l0->A.nnz) return OR_ERR_ARG;
+    if (memcmp(rp, l0->A.rp, ((size_t)n + 1) * sizeof(int32_t)) != 0) return OR_ERR_ARG;
+    if (memcmp(ci, l0->A.ci, (size_t)l0->A.nnz * sizeof(int32_t)) != 0) return OR_ERR_ARG;
+    int st = csr_check(n, rp, ci, v);
+    if (st) return st;
+    memcpy(l0->A.v, v, (size_t)l0->A.nnz * sizeof(double));
+    for (int l = 0; l + 1 < h->nlev; l++) {
+        level_t *lv = &h->lev[l];
+        csr_t cur = lv->A;            /* borrowed on the first pass */
+        double *curw = lv->w;
+        int own = 0;
+        for (int ps = 0; ps < lv->npass; ps++) {
+            int m = lv->pass_n[ps], nc = lv->pass_n[ps + 1];
+            double *p = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+            double *wc = (double *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(double));
+            csr_t nxt = {0, 0, NULL, NULL, NULL};
+            if (!p || !wc) st = OR_ERR_OOM;
+            else {
+                pass_weights(m, lv->pass_agg[ps], nc, curw, p, wc);
+                st = rap(&cur, lv->pass_agg[ps], p, nc, &nxt);
+            }
+            free(p);
+            if (own) { csr_free(&cur); free(curw); }
+            if (st) { free(wc); return st; }
+            cur = nxt; curw = wc; own = 1;
+        }
+        /* the last pass gives A_{l+1}: same pattern, new values */
+        csr_t *An = &h->lev[l + 1].A;
+        int same = cur.n == An->n && cur.nnz == An->nnz &&
+                   memcmp(cur.rp, An->rp, ((size_t)cur.n + 1) * sizeof(int32_t)) == 0 &&
+                   memcmp(cur.ci, An->ci, (size_t)cur.nnz * sizeof(int32_t)) == 0;
+        if (same) memcpy(An->v, cur.v, (size_t)cur.nnz * sizeof(double));
+        csr_free(&cur); free(curw);
+        if (!same) return OR_ERR_ARG;
+    }
+    for (int l = 0; l < h->nlev; l++) {
+        level_t *lv = &h->lev[l];
+        free(lv->dinv); free(lv->dinv32); free(lv->v32);
+        lv->dinv = NULL; lv->dinv32 = NULL; lv->v32 = NULL;
+        st = level_finish(lv);
+        if (st) return st;
+    }
+    level_t *lc = &h->lev[h->nlev - 1];
+    int nL = lc->A.n;
+    double *Ad = (double *)calloc((size_t)nL * (size_t)nL, sizeof(double));
+    if (!Ad) return OR_ERR_OOM;
+    for (int i = 0; i < nL; i++)
+        for (int32_t k = lc->A.rp[i]; k < lc->A.rp[i + 1]; k++)
+            Ad[(size_t)i * nL + lc->A.ci[k]] = lc->A.v[k];
+    st = or_chol(nL, Ad, h->L);
+    free(Ad);
+    return st;
+}
+
 /* ------------------------------------------------------------ accessors */
 int or_nlevels(const hier_t *h) { return h->nlev; }
 

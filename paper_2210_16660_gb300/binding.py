@@ -28,7 +28,7 @@ EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode
            "amg_batch_create", "pcg_solve_batch", "amg_batch_destroy", "amg_server_default_params",
            "amg_serve_plan", "amg_server_create", "amg_server_mesh_info", "amg_server_info", "amg_server_submit",
            "amg_server_progress", "amg_server_result", "amg_server_destroy", "amg_autotune", "amg_level_shape",
-           "amg_set_level_shape", "amg_profile_levels")
+           "amg_set_level_shape", "amg_profile_levels", "amg_refresh", "amg_refresh_time")
 
 
 class AmgCsr(C.Structure):
@@ -87,6 +87,10 @@ def load(build_if_missing: bool = True):
     lib.amg_level_csr.restype = I
     lib.amg_setup_times.argtypes = [P, P]
     lib.amg_setup_times.restype = I
+    lib.amg_refresh.argtypes = [P, C.POINTER(AmgCsr), P]
+    lib.amg_refresh.restype = I
+    lib.amg_refresh_time.argtypes = [P, C.POINTER(C.c_double)]
+    lib.amg_refresh_time.restype = I
     lib.amg_profile.argtypes = [P, I]
     lib.amg_profile.restype = I
     lib.amg_profile_read.argtypes = [P, P, P, I]
@@ -405,6 +409,28 @@ class AMG:
         ms = np.zeros(4)
         load().amg_setup_times(self._h, ms.ctypes.data)
         return {"total_ms": ms[0], "matching_ms": ms[1], "galerkin_ms": ms[2], "other_ms": ms[3]}
+
+    def refresh(self, A, stream=None, check: bool = True) -> int:
+        """``amg_refresh``: new values of the finest matrix on the same pattern
+        (same aggregates and prolongator weights; coarse operators, smoothers
+        and the coarsest inverse formed again). Returns the status (raises
+        with ``check``)."""
+        lib = load()
+        rp, rp_dev = _ptr(A.row_ptr, np.int32)
+        ci, ci_dev = _ptr(A.col, np.int32)
+        v, v_dev = _ptr(A.val, np.float64)
+        if not (rp_dev == ci_dev == v_dev):
+            raise TypeError("CSR arrays must all be host or all device")
+        csr = AmgCsr(int(A.n), len(A.col), rp, ci, v, int(rp_dev))
+        st = lib.amg_refresh(self._h, C.byref(csr), _stream_ptr(stream))
+        if check and st:
+            raise AmgError(st, last_error())
+        return st
+
+    def refresh_ms(self) -> float:
+        ms = C.c_double(0.0)
+        load().amg_refresh_time(self._h, C.byref(ms))
+        return ms.value
 
 
 class Batch:

@@ -148,6 +148,10 @@ int pcg_solve_batch(amg_batch b, const double *const *B, double *const *X, doubl
             set_error("pcg_solve_batch: NULL vector for system %d", i);
             return AMG_ERR_ARG;
         }
+        if (h->invalid) {
+            set_error("pcg_solve_batch: the last amg_refresh of system %d failed", i);
+            return AMG_ERR_ARG;
+        }
         h->mem.stream = s;
         PCG_TRY(ensure_hist(h, maxit));
         if (b->modes[i] != h->mode || b->gens[i] != h->graph_gen) rebuild = true;

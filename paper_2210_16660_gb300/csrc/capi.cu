@@ -156,7 +156,31 @@ int pcg_solve(amg_handle h, const double *b, double *x, double rtol, int maxit, 
         set_error("pcg_solve: NULL handle");
         return AMG_ERR_ARG;
     }
+    if (h->invalid) {
+        set_error("pcg_solve: the handle's last amg_refresh failed; refresh it again first");
+        return AMG_ERR_ARG;
+    }
     return solve_impl(h, b, x, rtol, maxit, iters, res_hist, (cudaStream_t)stream);
+}
+
+int amg_refresh(amg_handle h, const amg_csr *A, void *stream) {
+    set_error("");
+    if (!h) {
+        set_error("amg_refresh: NULL handle");
+        return AMG_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamSynchronize(s);
+    return refresh_impl(h, A, s);
+}
+
+int amg_refresh_time(amg_handle h, double *ms) {
+    if (!h || !ms) {
+        set_error("amg_refresh_time: NULL argument");
+        return AMG_ERR_ARG;
+    }
+    *ms = h->refresh_ms;
+    return AMG_OK;
 }
 
 double amg_last_true_residual(amg_handle h) { return h ? h->last_true_rel : -1.0; }
@@ -205,8 +229,8 @@ int amg_level_shape(amg_handle h, int level, int *shape) {
 int pcg_solve_multi(amg_handle h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
                     double *res_hist, void *stream) {
     set_error("");
-    if (!h) {
-        set_error("pcg_solve_multi: NULL handle");
+    if (!h || h->invalid) {
+        set_error("pcg_solve_multi: NULL handle, or its last amg_refresh failed");
         return AMG_ERR_ARG;
     }
     return solve_multi_impl(h, k, B, X, rtol, maxit, iters, res_hist, (cudaStream_t)stream);

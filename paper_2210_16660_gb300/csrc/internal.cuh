@@ -251,6 +251,8 @@ struct amg_hier {
     cudaGraphExec_t gexec_nt[2] = {nullptr, nullptr};
     int graph_body_kernels_nt[2] = {0, 0};
     int no_tail = 0;  // set while capturing a solve that must not use the tail
+    int invalid = 0;  // set while a refresh is incomplete (or failed): solves are refused
+    double refresh_ms = 0;  // host time of the last amg_refresh
     int use_graph = 1;
     int no_col16 = 0;
     int pdl = 1;  // programmatic dependent launch between solve kernels
@@ -271,6 +273,8 @@ struct amg_hier {
 
 namespace pcgamg {
 int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_t s);
+int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s);
+int refresh_smem_tail(amg_hier *h);
 int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, int *iters,
                double *res_hist, cudaStream_t s);
 int alloc_solve_workspace(amg_hier *h);

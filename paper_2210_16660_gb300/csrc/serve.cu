@@ -489,6 +489,10 @@ int amg_server_submit(amg_server sv, int mesh, const double *b, const double *x0
                   mesh);
         return AMG_ERR_OOM;
     }
+    if (sv->meshes[mesh]->invalid) {
+        set_error("amg_server_submit: the last amg_refresh of mesh %d failed", mesh);
+        return AMG_ERR_ARG;
+    }
     if (sv->queued >= sv->prm.queue_cap) {
         set_error("amg_server_submit: queue full (%d requests waiting)", sv->queued);
         return AMG_ERR_BUSY;

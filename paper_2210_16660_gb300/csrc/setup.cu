@@ -546,6 +546,77 @@ __global__ void k_chol_inverse(int n, const double *__restrict__ L, double *__re
     for (int k = threadIdx.x; k < n; k += blockDim.x) ainv[(int64_t)k * n + c] = y[k];
 }
 
+// ------------------------------------------------------------ partial reuse
+// flag 16 where (rp, ci) differs from the pattern the hierarchy was built on.
+__global__ void k_same_pattern(int n, int64_t nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               const int32_t *__restrict__ rp0, const int32_t *__restrict__ ci0, int *flag) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= n && rp[k] != rp0[k]) atomicOr(flag, 16);
+    if (k < nnz && ci[k] != ci0[k]) atomicOr(flag, 16);
+}
+
+// Members of each aggregate of one kept pass map: smallest in first, largest
+// in second (equal for a singleton; a pass aggregate has one or two members).
+__global__ void k_pass_members(int m, const int32_t *__restrict__ agg, int32_t *__restrict__ first,
+                               int32_t *__restrict__ second) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int I = agg[i];
+    if (I < 0) return;
+    atomicMin(first + I, i);
+    atomicMax(second + I, i);
+}
+
+// Eq. (prolongator) weights of a kept pass from its map and w, with the
+// arithmetic of k_assign: pair w_e / ||w_e||, singleton w_s / |w_s|, 0 for a
+// row left out; the coarse w_c; members as mem0 < mem1 (-1 for a singleton).
+__global__ void k_pass_weights(int m, int nc, const int32_t *__restrict__ first, const int32_t *__restrict__ second,
+                               const double *__restrict__ w, double *__restrict__ p, double *__restrict__ wc,
+                               int32_t *__restrict__ mem0, int32_t *__restrict__ mem1, int *flag) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int i = first[I], j = second[I];
+    if (i < 0 || i >= m || j < 0 || j >= m) {  // an aggregate without members: not a kept map
+        atomicOr(flag, 1);
+        return;
+    }
+    double wi = w[i];
+    if (j != i) {
+        double wj = w[j];
+        double nrm = __dsqrt_rn(__dadd_rn(__dmul_rn(wi, wi), __dmul_rn(wj, wj)));
+        p[i] = __ddiv_rn(wi, nrm);
+        p[j] = __ddiv_rn(wj, nrm);
+        wc[I] = nrm;
+        mem0[I] = i;
+        mem1[I] = j;
+    } else {
+        double a = fabs(wi);
+        p[i] = __ddiv_rn(wi, a);
+        wc[I] = a;
+        mem0[I] = i;
+        mem1[I] = -1;
+    }
+}
+
+// Values only of the sliced-ELL copies (the layout and columns are those of
+// the same pattern, already in place).
+__global__ void k_sell_vals(int n, int nsl, const int32_t *__restrict__ rp, const double *__restrict__ v,
+                            const int32_t *__restrict__ sptr, double *__restrict__ v64, float *__restrict__ v32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nsl * kSlice) return;
+    int s = i / kSlice, lane = i % kSlice;
+    int32_t base = sptr[s];
+    int w = (sptr[s + 1] - base) / kSlice;
+    int len = i < n ? rp[i + 1] - rp[i] : 0;
+    int32_t r0 = i < n ? rp[i] : 0;
+    for (int k = 0; k < w; k++) {
+        int32_t e = base + k * kSlice + lane;
+        double a = k < len ? v[r0 + k] : 0.0;
+        v64[e] = a;
+        v32[e] = __double2float_rn(a);
+    }
+}
+
 double now_ms() {
     return std::chrono::duration<double, std::milli>(
                std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -561,6 +632,48 @@ void free_csr(Mem &M, DevCSR &a) {
     release(M, a.rp);
     release(M, a.ci);
     release(M, a.v);
+}
+
+// Galerkin product P^T cur P of one pairwise pass (aggregate members mem0 <
+// mem1, -1 = singleton; map agg; weights p) into a new CSR matrix c.
+int galerkin(amg_hier *h, const DevCSR &cur, const int32_t *agg, const double *p, const int32_t *mem0,
+             const int32_t *mem1, int nc, DevCSR *out, cudaStream_t s) {
+    Mem &M = h->mem;
+    int32_t *cnt = nullptr, *off = nullptr, *ucnt = nullptr, *tJ = nullptr;
+    unsigned long long *tK = nullptr;
+    double *tT = nullptr;
+    PCG_TRY(alloc(M, &cnt, nc));
+    PCG_TRY(alloc(M, &off, (size_t)nc + 1));
+    k_rap_count<<<grid_for(nc), kBlock, 0, s>>>(nc, mem0, mem1, cur.rp, cnt);
+    PCG_LAUNCH_CK();
+    int32_t nterm = 0;
+    PCG_TRY(scan_exclusive(M, cnt, off, nc, &nterm, s));
+    release(M, cnt);
+    PCG_TRY(alloc(M, &tJ, nterm));
+    PCG_TRY(alloc(M, &tK, nterm));
+    PCG_TRY(alloc(M, &tT, nterm));
+    PCG_TRY(alloc(M, &ucnt, nc));
+    k_rap_terms<<<grid_for(nc, 128), 128, 0, s>>>(nc, mem0, mem1, cur.rp, cur.ci, cur.v, agg, p, off, tJ,
+                                                   tK, tT, ucnt);
+    PCG_LAUNCH_CK();
+    DevCSR c;
+    c.n = nc;
+    PCG_TRY(alloc(M, &c.rp, (size_t)nc + 1));
+    int32_t nzc = 0;
+    PCG_TRY(scan_exclusive(M, ucnt, c.rp, nc, &nzc, s));
+    c.nnz = nzc;
+    PCG_TRY(alloc(M, &c.ci, nzc));
+    PCG_TRY(alloc(M, &c.v, nzc));
+    k_rap_copy<<<grid_for(nc), kBlock, 0, s>>>(nc, off, c.rp, tJ, tT, c.ci, c.v);
+    PCG_LAUNCH_CK();
+    PCG_CK(cudaStreamSynchronize(s));
+    release(M, tJ);
+    release(M, tK);
+    release(M, tT);
+    release(M, ucnt);
+    release(M, off);
+    *out = c;
+    return AMG_OK;
 }
 
 // One pairwise pass on cur (weights w): fills agg/p of the pass, the coarse
@@ -615,40 +728,8 @@ int pairwise_pass(amg_hier *h, const DevCSR &cur, const double *w, int32_t **agg
     release(M, idx);
     release(M, mate);
 
-    // Galerkin product
-    int32_t *cnt = nullptr, *off = nullptr, *ucnt = nullptr, *tJ = nullptr;
-    unsigned long long *tK = nullptr;
-    double *tT = nullptr;
-    PCG_TRY(alloc(M, &cnt, nc));
-    PCG_TRY(alloc(M, &off, (size_t)nc + 1));
-    k_rap_count<<<grid_for(nc), kBlock, 0, s>>>(nc, mem0, mem1, cur.rp, cnt);
-    PCG_LAUNCH_CK();
-    int32_t nterm = 0;
-    PCG_TRY(scan_exclusive(M, cnt, off, nc, &nterm, s));
-    release(M, cnt);
-    PCG_TRY(alloc(M, &tJ, nterm));
-    PCG_TRY(alloc(M, &tK, nterm));
-    PCG_TRY(alloc(M, &tT, nterm));
-    PCG_TRY(alloc(M, &ucnt, nc));
-    k_rap_terms<<<grid_for(nc, 128), 128, 0, s>>>(nc, mem0, mem1, cur.rp, cur.ci, cur.v, agg, p, off, tJ,
-                                                   tK, tT, ucnt);
-    PCG_LAUNCH_CK();
     DevCSR c;
-    c.n = nc;
-    PCG_TRY(alloc(M, &c.rp, (size_t)nc + 1));
-    int32_t nzc = 0;
-    PCG_TRY(scan_exclusive(M, ucnt, c.rp, nc, &nzc, s));
-    c.nnz = nzc;
-    PCG_TRY(alloc(M, &c.ci, nzc));
-    PCG_TRY(alloc(M, &c.v, nzc));
-    k_rap_copy<<<grid_for(nc), kBlock, 0, s>>>(nc, off, c.rp, tJ, tT, c.ci, c.v);
-    PCG_LAUNCH_CK();
-    PCG_CK(cudaStreamSynchronize(s));
-    release(M, tJ);
-    release(M, tK);
-    release(M, tT);
-    release(M, ucnt);
-    release(M, off);
+    PCG_TRY(galerkin(h, cur, agg, p, mem0, mem1, nc, &c, s));
     release(M, mem0);
     release(M, mem1);
     release(M, dflag);
@@ -908,6 +989,169 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
     h->setup_ms[1] = t_match;
     h->setup_ms[2] = t_rap;
     h->setup_ms[3] = h->setup_ms[0] - t_match - t_rap;
+    return AMG_OK;
+}
+
+// Partial reuse (Sec. 4): new values of the finest matrix on the pattern the
+// hierarchy was built on. Every pass keeps its aggregates; its weights are
+// formed again from the map and w (they do not depend on the values), then
+// the Galerkin products pass by pass, the l1 diagonals, the sliced-ELL values
+// and the coarsest inverse. Every array keeps its address, so captured solve
+// graphs, batch graphs and serving engines stay valid. Nothing is changed
+// when the input is rejected (AMG_ERR_ARG).
+int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s) {
+    double t_begin = now_ms();
+    Mem &M = h->mem;
+    M.stream = s;
+    Level &l0 = h->lev[0];
+    int n = l0.A.n;
+    int64_t nnz = l0.A.nnz;
+    if (!A || A->n != n || A->nnz != nnz || !A->row_ptr || !A->col || !A->val) {
+        set_error("amg_refresh: sizes differ from the hierarchy's matrix, or NULL arrays");
+        return AMG_ERR_ARG;
+    }
+    int32_t *rp = nullptr, *ci = nullptr;
+    double *v = nullptr;
+    int *dflag = nullptr;
+    PCG_TRY(alloc(M, &rp, (size_t)n + 1));
+    PCG_TRY(alloc(M, &ci, nnz));
+    PCG_TRY(alloc(M, &v, nnz));
+    PCG_TRY(alloc(M, &dflag, 1));
+    cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    PCG_CK(cudaMemcpyAsync(rp, A->row_ptr, sizeof(int32_t) * ((size_t)n + 1), kind, s));
+    PCG_CK(cudaMemcpyAsync(ci, A->col, sizeof(int32_t) * nnz, kind, s));
+    PCG_CK(cudaMemcpyAsync(v, A->val, sizeof(double) * nnz, kind, s));
+    PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+    k_same_pattern<<<grid_for(nnz > n ? nnz : (int64_t)n + 1), kBlock, 0, s>>>(n, nnz, rp, ci, l0.A.rp, l0.A.ci,
+                                                                               dflag);
+    PCG_LAUNCH_CK();
+    int flag = 0;
+    PCG_TRY(read_flag(dflag, s, &flag));
+    if (!flag) {
+        k_check_csr<<<grid_for(n), kBlock, 0, s>>>(n, rp, ci, v, nnz, dflag);
+        PCG_LAUNCH_CK();
+        PCG_TRY(read_flag(dflag, s, &flag));
+    }
+    if (!flag) {
+        k_check_sym<<<grid_for(n), kBlock, 0, s>>>(n, rp, ci, v, dflag);
+        PCG_LAUNCH_CK();
+        PCG_TRY(read_flag(dflag, s, &flag));
+    }
+    release(M, rp);
+    release(M, ci);
+    if (flag) {
+        release(M, v);
+        release(M, dflag);
+        set_error("amg_refresh: rejected (flags 0x%x: 16 another sparsity pattern, 1 column order/range, "
+                  "2 diagonal, 4 row pointers, 8 not exactly symmetric)", flag);
+        return AMG_ERR_ARG;
+    }
+    PCG_CK(cudaMemcpyAsync(l0.A.v, v, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
+    PCG_CK(cudaStreamSynchronize(s));
+    release(M, v);
+    h->invalid = 1;  // until every level and the coarsest inverse are rebuilt
+    int L = (int)h->lev.size() - 1;
+    for (int l = 0; l < L; l++) {
+        Level &lv = h->lev[l];
+        DevCSR cur = lv.A;
+        double *curw = lv.w;
+        bool own = false;
+        int npass = (int)lv.pass_agg.size();
+        for (int ps = 0; ps < npass; ps++) {
+            int m = lv.pass_n[ps], nc = lv.pass_n[ps + 1];
+            const int32_t *agg = lv.pass_agg[ps];
+            int32_t *first = nullptr, *second = nullptr, *mem0 = nullptr, *mem1 = nullptr;
+            double *p = nullptr, *wc = nullptr;
+            PCG_TRY(alloc(M, &first, nc));
+            PCG_TRY(alloc(M, &second, nc));
+            PCG_TRY(alloc(M, &mem0, nc));
+            PCG_TRY(alloc(M, &mem1, nc));
+            PCG_TRY(alloc(M, &p, m));
+            PCG_TRY(alloc(M, &wc, nc));
+            k_fill<int32_t><<<grid_for(nc), kBlock, 0, s>>>(first, nc, INT32_MAX);
+            k_fill<int32_t><<<grid_for(nc), kBlock, 0, s>>>(second, nc, -1);
+            k_fill<double><<<grid_for(m), kBlock, 0, s>>>(p, m, 0.0);
+            k_pass_members<<<grid_for(m), kBlock, 0, s>>>(m, agg, first, second);
+            PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+            k_pass_weights<<<grid_for(nc), kBlock, 0, s>>>(m, nc, first, second, curw, p, wc, mem0, mem1, dflag);
+            PCG_LAUNCH_CK();
+            PCG_TRY(read_flag(dflag, s, &flag));
+            if (flag) {
+                set_error("amg_refresh: level %d pass %d has an aggregate without members", l, ps);
+                return AMG_ERR_CUDA;
+            }
+            DevCSR nxt;
+            PCG_TRY(galerkin(h, cur, agg, p, mem0, mem1, nc, &nxt, s));
+            release(M, first);
+            release(M, second);
+            release(M, mem0);
+            release(M, mem1);
+            release(M, p);
+            if (own) {
+                free_csr(M, cur);
+                release(M, curw);
+            }
+            cur = nxt;
+            curw = wc;
+            own = true;
+        }
+        // the last pass gives A_{l+1} on its kept pattern
+        Level &nx = h->lev[l + 1];
+        flag = cur.n != nx.A.n || cur.nnz != nx.A.nnz;
+        if (!flag) {
+            PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+            k_same_pattern<<<grid_for(cur.nnz > cur.n ? cur.nnz : (int64_t)cur.n + 1), kBlock, 0, s>>>(
+                cur.n, cur.nnz, cur.rp, cur.ci, nx.A.rp, nx.A.ci, dflag);
+            PCG_LAUNCH_CK();
+            PCG_TRY(read_flag(dflag, s, &flag));
+        }
+        if (!flag)
+            PCG_CK(cudaMemcpyAsync(nx.A.v, cur.v, sizeof(double) * cur.nnz, cudaMemcpyDeviceToDevice, s));
+        PCG_CK(cudaStreamSynchronize(s));
+        if (own) {
+            free_csr(M, cur);
+            release(M, curw);
+        }
+        if (flag) {
+            release(M, dflag);
+            set_error("amg_refresh: level %d came out with another pattern", l + 1);
+            return AMG_ERR_CUDA;
+        }
+    }
+    for (int l = 0; l <= L; l++) {
+        Level &lv = h->lev[l];
+        Sell &S = lv.S;
+        int nl = lv.A.n;
+        k_l1diag<<<grid_for(nl), kBlock, 0, s>>>(nl, lv.A.rp, lv.A.v, lv.dinv, lv.dinv32);
+        k_sell_vals<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(nl, S.nslices, lv.A.rp, lv.A.v,
+                                                                             S.sptr, S.v64, S.v32);
+        PCG_LAUNCH_CK();
+    }
+    // dense inverse of the coarsest matrix, in place
+    Level &lc = h->lev[L];
+    int nL = lc.A.n;
+    double *ad = nullptr;
+    PCG_TRY(alloc(M, &ad, (size_t)nL * nL));
+    PCG_CK(cudaMemsetAsync(ad, 0, sizeof(double) * (size_t)nL * nL, s));
+    PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+    k_dense<<<grid_for(nL), kBlock, 0, s>>>(nL, lc.A.rp, lc.A.ci, lc.A.v, ad);
+    k_chol<<<1, 256, 0, s>>>(nL, ad, dflag);
+    PCG_LAUNCH_CK();
+    PCG_TRY(read_flag(dflag, s, &flag));
+    release(M, dflag);
+    if (flag) {
+        release(M, ad);
+        set_error("amg_refresh: coarsest matrix is not SPD (Cholesky pivot <= 0); the handle refuses "
+                  "solves until a refresh succeeds");
+        return AMG_ERR_BREAKDOWN;
+    }
+    k_chol_inverse<<<nL, 256, sizeof(double) * nL, s>>>(nL, ad, h->Ainv);
+    PCG_LAUNCH_CK();
+    PCG_CK(cudaStreamSynchronize(s));
+    release(M, ad);
+    PCG_TRY(refresh_smem_tail(h));
+    h->invalid = 0;
+    h->refresh_ms = now_ms() - t_begin;
     return AMG_OK;
 }
 

@@ -230,6 +230,31 @@ int cluster_fits(int ctas, size_t smem, int smem_max) {
 // whose tail's data fit the cluster's shared memory, if at least one level
 // lies between it and the coarsest; otherwise no tail for that precision
 // (tail_first[p] = 0).
+// Host copies of what the tail levels F..L need.
+int fetch_tail_levels(amg_hier *h, int F, std::vector<HostLevel> &hl) {
+    int L = (int)h->lev.size() - 1;
+    int nt = L - F + 1;
+    hl.assign(nt, HostLevel());
+    for (int k = 0; k < nt; k++) {
+        Level &lv = h->lev[F + k];
+        HostLevel &H = hl[k];
+        H.n = lv.A.n;
+        PCG_TRY(fetch(H.dinv, lv.dinv, H.n));
+        PCG_TRY(fetch(H.dinv32, lv.dinv32, H.n));
+        if (k + 1 < nt) {
+            PCG_TRY(fetch(H.rp, lv.A.rp, H.n + 1));
+            PCG_TRY(fetch(H.ci, lv.A.ci, (size_t)lv.A.nnz));
+            PCG_TRY(fetch(H.v, lv.A.v, (size_t)lv.A.nnz));
+            PCG_TRY(fetch(H.p, lv.p, H.n));
+            PCG_TRY(fetch(H.p32, lv.p32, H.n));
+            PCG_TRY(fetch(H.agg, lv.agg, H.n));
+            PCG_TRY(fetch(H.rptr, lv.rptr, lv.nc + 1));
+            PCG_TRY(fetch(H.ridx, lv.ridx, (size_t)H.rptr[lv.nc]));
+        }
+    }
+    return AMG_OK;
+}
+
 template <typename T>
 int plan_precision(amg_hier *h, int smem_max) {
     const int pi = sizeof(T) == 4 ? 0 : 1;
@@ -241,24 +266,8 @@ int plan_precision(amg_hier *h, int smem_max) {
         if (h->lev[F].A.n > kSmemTailRows) continue;
         int nt = L - F + 1;
         if (nt > kMaxTailLevels) continue;
-        std::vector<HostLevel> hl(nt);
-        for (int k = 0; k < nt; k++) {
-            Level &lv = h->lev[F + k];
-            HostLevel &H = hl[k];
-            H.n = lv.A.n;
-            PCG_TRY(fetch(H.dinv, lv.dinv, H.n));
-            PCG_TRY(fetch(H.dinv32, lv.dinv32, H.n));
-            if (k + 1 < nt) {
-                PCG_TRY(fetch(H.rp, lv.A.rp, H.n + 1));
-                PCG_TRY(fetch(H.ci, lv.A.ci, (size_t)lv.A.nnz));
-                PCG_TRY(fetch(H.v, lv.A.v, (size_t)lv.A.nnz));
-                PCG_TRY(fetch(H.p, lv.p, H.n));
-                PCG_TRY(fetch(H.p32, lv.p32, H.n));
-                PCG_TRY(fetch(H.agg, lv.agg, H.n));
-                PCG_TRY(fetch(H.rptr, lv.rptr, lv.nc + 1));
-                PCG_TRY(fetch(H.ridx, lv.ridx, (size_t)H.rptr[lv.nc]));
-            }
-        }
+        std::vector<HostLevel> hl;
+        PCG_TRY(fetch_tail_levels(h, F, hl));
         for (int ctas : {16, 8}) {
             SmemTailPlan plan = {};
             std::vector<unsigned char> blob;
@@ -277,6 +286,29 @@ int plan_precision(amg_hier *h, int smem_max) {
     return AMG_OK;
 }
 
+// The static blob of a planned tail formed again from the hierarchy's
+// current values (same levels, same layout) and written over the old one, so
+// captured launches keep their arguments.
+template <typename T>
+int refresh_precision(amg_hier *h) {
+    const int pi = sizeof(T) == 4 ? 0 : 1;
+    int F = h->tail_first[pi];
+    if (F <= 0) return AMG_OK;
+    std::vector<double> ainv;
+    PCG_TRY(fetch(ainv, h->Ainv, (size_t)h->nL * h->nL));
+    std::vector<HostLevel> hl;
+    PCG_TRY(fetch_tail_levels(h, F, hl));
+    SmemTailPlan plan = {};
+    std::vector<unsigned char> blob;
+    size_t bytes = build_plan<T>(hl, ainv, h->tail_ctas[pi], plan, blob);
+    if (bytes != h->tail_smem[pi] || plan.static_bytes != h->tail_plan[pi].static_bytes) {
+        set_error("amg_refresh: the shared-memory tail changed its layout");
+        return AMG_ERR_CUDA;
+    }
+    PCG_CK(cudaMemcpy(h->tail_blob[pi], blob.data(), blob.size(), cudaMemcpyHostToDevice));
+    return AMG_OK;
+}
+
 int setup_smem_tail(amg_hier *h) {
     h->tail_first[0] = h->tail_first[1] = 0;
     if ((int)h->lev.size() < 3) return AMG_OK;
@@ -284,6 +316,12 @@ int setup_smem_tail(amg_hier *h) {
     PCG_CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     PCG_TRY(plan_precision<float>(h, smem_max));
     PCG_TRY(plan_precision<double>(h, smem_max));
+    return AMG_OK;
+}
+
+int refresh_smem_tail(amg_hier *h) {
+    PCG_TRY(refresh_precision<float>(h));
+    PCG_TRY(refresh_precision<double>(h));
     return AMG_OK;
 }
 

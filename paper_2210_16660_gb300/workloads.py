@@ -221,6 +221,19 @@ def make_problem(N: int, ratio: float = 1.0, seed: int = 1, lx: float = 1.0,
     return Problem(name or f"q1_{N}^3_r{ratio}", N, A, b, xs, wall, sp)
 
 
+def rescaled(A: CSR, seed: int, spread: float = 0.5) -> CSR:
+    """New coefficients on the same pattern: ``a'_ij = (d_i d_j) a_ij`` with
+    ``d = 1 + spread * u``, ``u`` uniform on [0, 1) from SplitMix64 words.
+
+    ``D A D`` stays SPD, and ``d_i d_j == d_j d_i`` exactly, so a bitwise
+    symmetric ``A`` gives a bitwise symmetric ``A'``.
+    """
+    u = (splitmix64(seed, A.n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    d = 1.0 + spread * u
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    return CSR(A.n, A.row_ptr.copy(), A.col.copy(), (d[rows] * d[A.col]) * A.val)
+
+
 def make_rhs(problem: Problem, k: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
     """``k`` further right-hand sides: columns of ``X*`` and ``B = A X*``.
 

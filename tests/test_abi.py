@@ -76,6 +76,10 @@ def test_host_side_checks_of_the_batched_serving_and_tuning_calls():
     assert lib.amg_set_level_shape(None, 1, shape) == E
     assert lib.amg_profile_levels(None, 1, None, None) == E
     assert lib.amg_residual_noalloc(None, None, None, None, None, None) == E
+    assert lib.amg_refresh(None, None, None) == E
+    assert b"NULL handle" in lib.amg_last_error()
+    d = ctypes.c_double()
+    assert lib.amg_refresh_time(None, ctypes.byref(d)) == E
     p = binding.ServerParams()
     lib.amg_server_default_params(ctypes.byref(p))
     assert (p.mode, p.slots, p.max_engines, p.chunk, p.solo, p.batch_min) == (binding.MODE_FCG32, 4, 2, 4, 1, 3)
