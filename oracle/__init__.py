@@ -64,6 +64,8 @@ def load():
     lib.or_chol_solve.argtypes = [I, _f64p, _f64p, _f64p]
     lib.or_setup.restype = I
     lib.or_setup.argtypes = [I, _i32p, _i32p, _f64p, I, I, I, C.POINTER(P)]
+    lib.or_set_smoother.restype = I
+    lib.or_set_smoother.argtypes = [P, I, I]
     lib.or_refresh.restype = I
     lib.or_refresh.argtypes = [P, I, _i32p, _i32p, _f64p]
     lib.or_free.restype = None
@@ -184,6 +186,12 @@ class Hierarchy:
             raise RuntimeError(f"oracle setup status {st}")
         self._h = h
         self.n = n
+
+    def set_smoother(self, nu: int, nblocks: int = 0) -> int:
+        """nu = 0: the setup's one-sweep l1-Jacobi; nu >= 1: nu sweeps of l1
+        hybrid Gauss-Seidel (forward before, backward after the coarse
+        correction) over ``nblocks`` row blocks per level (0: one row each)."""
+        return load().or_set_smoother(self._h, nu, nblocks)
 
     def refresh(self, A) -> int:
         """Partial reuse (Sec. 4): new values of the finest matrix on the same

@@ -61,6 +61,10 @@ typedef struct {
     level_t lev[OR_MAX_LEVELS];
     double *L;          /* dense Cholesky factor of the coarsest A (row-major, lower) */
     int nL;
+    /* smoother: nu = 0 is the one-sweep l1-Jacobi of the setup; otherwise nu
+     * sweeps of the l1 hybrid Gauss-Seidel method over nblocks row blocks per
+     * level (or_set_smoother) */
+    int nu, nblocks;
 } hier_t;
 
 /* ---------------------------------------------------------------- helpers */
@@ -118,6 +122,80 @@ void or_l1_diag(int n, const int32_t *rp, const int32_t *ci, const double *v, do
         double s = 0.0;
         for (int32_t k = rp[i]; k < rp[i + 1]; k++) s += fabs(v[k]);
         d[i] = s;
+    }
+}
+
+/* ------------------------------------- hybrid Gauss-Seidel smoother (Sec. 3.1)
+ * The paper smooths with nu = 4 sweeps of hybrid forward/backward
+ * Gauss-Seidel: block Jacobi over the row blocks of the parallel distribution,
+ * each block solved by one forward (pre-smoothing) or backward (post-
+ * smoothing) Gauss-Seidel pass, M_pp = omega (L_pp + D_pp). Reading: the l1
+ * form of the same method (the l1 family the paper cites), which needs no
+ * damping: omega = 1 and D_pp augmented by the off-block row sums,
+ * d_i = a_ii + sum_{j outside i's block} |a_ij|. The blocks are nblocks
+ * contiguous row ranges per level ("processes"), ceil(n_l / nblocks) rows
+ * each, so they shrink on coarser levels as a fixed distribution's do. One
+ * row per block is the l1-Jacobi smoother.
+ */
+static int gs_rows(const hier_t *h, int n) {
+    if (h->nblocks <= 0) return 1;
+    int nb = (int)(((int64_t)n + h->nblocks - 1) / h->nblocks);
+    return nb < 1 ? 1 : nb;
+}
+
+/* d_i summed in storage order; in-block off-diagonal entries are skipped */
+static void hybrid_l1(const csr_t *a, int nb, double *dinv, float *dinv32) {
+    for (int i = 0; i < a->n; i++) {
+        int lo = (i / nb) * nb, hi = lo + nb;
+        double s = 0.0;
+        for (int32_t k = a->rp[i]; k < a->rp[i + 1]; k++) {
+            int j = a->ci[k];
+            if (j == i || j < lo || j >= hi) s += fabs(a->v[k]);
+        }
+        dinv[i] = 1.0 / s;
+        dinv32[i] = (float)dinv[i];
+    }
+}
+
+/* One sweep x_new = x_old + M^{-1} (b - A x_old), M = blockdiag(L_pp + D_l1)
+ * (forward) or its transpose (backward), rows of a block in increasing
+ * (forward) or decreasing (backward) order; within a block the updated
+ * values are used, outside it the values of x_old (xo = NULL: x_old = 0). */
+static void sweep64(const csr_t *a, const double *dinv, int nb, const double *b, const double *xo, double *xn,
+                    int fwd) {
+    int n = a->n;
+    for (int lo = 0; lo < n; lo += nb) {
+        int hi = lo + nb < n ? lo + nb : n;
+        for (int r = lo; r < hi; r++) xn[r] = xo ? xo[r] : 0.0;
+        for (int q = 0; q < hi - lo; q++) {
+            int r = fwd ? lo + q : hi - 1 - q;
+            double acc = 0.0;
+            for (int32_t k = a->rp[r]; k < a->rp[r + 1]; k++) {
+                int j = a->ci[k];
+                double xj = (j >= lo && j < hi) ? xn[j] : (xo ? xo[j] : 0.0);
+                acc += a->v[k] * xj;
+            }
+            xn[r] = xo ? xn[r] + dinv[r] * (b[r] - acc) : dinv[r] * (b[r] - acc);
+        }
+    }
+}
+
+static void sweep32(const csr_t *a, const float *v32, const float *dinv, int nb, const float *b, const float *xo,
+                    float *xn, int fwd) {
+    int n = a->n;
+    for (int lo = 0; lo < n; lo += nb) {
+        int hi = lo + nb < n ? lo + nb : n;
+        for (int r = lo; r < hi; r++) xn[r] = xo ? xo[r] : 0.0f;
+        for (int q = 0; q < hi - lo; q++) {
+            int r = fwd ? lo + q : hi - 1 - q;
+            float acc = 0.0f;
+            for (int32_t k = a->rp[r]; k < a->rp[r + 1]; k++) {
+                int j = a->ci[k];
+                float xj = (j >= lo && j < hi) ? xn[j] : (xo ? xo[j] : 0.0f);
+                acc += v32[k] * xj;
+            }
+            xn[r] = xo ? xn[r] + dinv[r] * (b[r] - acc) : dinv[r] * (b[r] - acc);
+        }
     }
 }
 
@@ -531,6 +609,28 @@ int or_setup(int n, const int32_t *rp, const int32_t *ci, const double *v,
     return OR_OK;
 }
 
+/* Select the smoother: nu = 0 restores the l1-Jacobi sweep of the setup;
+ * nu >= 1 sweeps of l1 hybrid Gauss-Seidel over nblocks row blocks per level
+ * (nblocks = 0: one row per block). Re-forms D^-1 with the block rule. */
+int or_set_smoother(hier_t *h, int nu, int nblocks) {
+    if (nu < 0 || nu > 64 || nblocks < 0) return OR_ERR_ARG;
+    h->nu = nu;
+    h->nblocks = nblocks;
+    for (int l = 0; l < h->nlev; l++) {
+        level_t *lv = &h->lev[l];
+        if (nu > 0) {
+            hybrid_l1(&lv->A, gs_rows(h, lv->A.n), lv->dinv, lv->dinv32);
+        } else {
+            or_l1_diag(lv->A.n, lv->A.rp, lv->A.ci, lv->A.v, lv->dinv);
+            for (int i = 0; i < lv->A.n; i++) {
+                lv->dinv[i] = 1.0 / lv->dinv[i];
+                lv->dinv32[i] = (float)lv->dinv[i];
+            }
+        }
+    }
+    return OR_OK;
+}
+
 /* ------------------------------------------------- partial reuse (Sec. 4)
  * When the mesh (the sparsity pattern) stays and only the coefficients
  * change, the hierarchy can be rebuilt with the same prolongators: the
@@ -612,6 +712,7 @@ int or_refresh(hier_t *h, int n, const int32_t *rp, const int32_t *ci, const dou
         lv->dinv = NULL; lv->dinv32 = NULL; lv->v32 = NULL;
         st = level_finish(lv);
         if (st) return st;
+        if (h->nu > 0) hybrid_l1(&lv->A, gs_rows(h, lv->A.n), lv->dinv, lv->dinv32);
     }
     level_t *lc = &h->lev[h->nlev - 1];
     int nL = lc->A.n;
@@ -676,23 +777,34 @@ void or_coarse_factor(const hier_t *h, double *L) {
  */
 static int vcycle64(const hier_t *h, const double *r, double *z) {
     int L = h->nlev - 1;
-    double *bl[OR_MAX_LEVELS] = {0}, *xl[OR_MAX_LEVELS] = {0}, *t = NULL;
+    double *bl[OR_MAX_LEVELS] = {0}, *xl[OR_MAX_LEVELS] = {0}, *t = NULL, *u = NULL;
     int st = OR_OK;
     int nmax = h->lev[0].A.n;
     t = (double *)malloc((size_t)nmax * sizeof(double));
+    u = (double *)malloc((size_t)nmax * sizeof(double));
     for (int l = 0; l <= L; l++) {
         int n = h->lev[l].A.n;
         bl[l] = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
         xl[l] = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
         if (!bl[l] || !xl[l]) st = OR_ERR_OOM;
     }
-    if (!t) st = OR_ERR_OOM;
+    if (!t || !u) st = OR_ERR_OOM;
     if (st) goto done;
     memcpy(bl[0], r, (size_t)nmax * sizeof(double));
     for (int l = 0; l < L; l++) {
         const level_t *lv = &h->lev[l];
         int n = lv->A.n, nc = h->lev[l + 1].A.n;
-        for (int i = 0; i < n; i++) xl[l][i] = lv->dinv[i] * bl[l][i];
+        if (h->nu > 0) {
+            /* nu forward sweeps from zero */
+            int nb = gs_rows(h, n);
+            sweep64(&lv->A, lv->dinv, nb, bl[l], NULL, xl[l], 1);
+            for (int s = 1; s < h->nu; s++) {
+                memcpy(u, xl[l], (size_t)n * sizeof(double));
+                sweep64(&lv->A, lv->dinv, nb, bl[l], u, xl[l], 1);
+            }
+        } else {
+            for (int i = 0; i < n; i++) xl[l][i] = lv->dinv[i] * bl[l][i];
+        }
         or_spmv(n, lv->A.rp, lv->A.ci, lv->A.v, xl[l], t);
         for (int I = 0; I < nc; I++) bl[l + 1][I] = 0.0;
         for (int i = 0; i < n; i++)
@@ -704,13 +816,22 @@ static int vcycle64(const hier_t *h, const double *r, double *z) {
         int n = lv->A.n;
         for (int i = 0; i < n; i++)
             if (lv->agg[i] >= 0) xl[l][i] += lv->p[i] * xl[l + 1][lv->agg[i]];
-        or_spmv(n, lv->A.rp, lv->A.ci, lv->A.v, xl[l], t);
-        for (int i = 0; i < n; i++) xl[l][i] = xl[l][i] + lv->dinv[i] * (bl[l][i] - t[i]);
+        if (h->nu > 0) {
+            /* nu backward sweeps (M^T: the symmetric counterpart) */
+            int nb = gs_rows(h, n);
+            for (int s = 0; s < h->nu; s++) {
+                memcpy(u, xl[l], (size_t)n * sizeof(double));
+                sweep64(&lv->A, lv->dinv, nb, bl[l], u, xl[l], 0);
+            }
+        } else {
+            or_spmv(n, lv->A.rp, lv->A.ci, lv->A.v, xl[l], t);
+            for (int i = 0; i < n; i++) xl[l][i] = xl[l][i] + lv->dinv[i] * (bl[l][i] - t[i]);
+        }
     }
     memcpy(z, xl[0], (size_t)nmax * sizeof(double));
 done:
     for (int l = 0; l <= L; l++) { free(bl[l]); free(xl[l]); }
-    free(t);
+    free(t); free(u);
     return st;
 }
 
@@ -728,11 +849,12 @@ static void spmv32(const csr_t *a, const float *v32, const float *x, float *y) {
 
 static int vcycle32(const hier_t *h, const double *r, double *z) {
     int L = h->nlev - 1;
-    float *bl[OR_MAX_LEVELS] = {0}, *xl[OR_MAX_LEVELS] = {0}, *t = NULL;
+    float *bl[OR_MAX_LEVELS] = {0}, *xl[OR_MAX_LEVELS] = {0}, *t = NULL, *u = NULL;
     double *b64 = NULL, *x64 = NULL;
     int st = OR_OK;
     int nmax = h->lev[0].A.n;
     t = (float *)malloc((size_t)nmax * sizeof(float));
+    u = (float *)malloc((size_t)nmax * sizeof(float));
     b64 = (double *)malloc((size_t)h->nL * sizeof(double) + 8);
     x64 = (double *)malloc((size_t)h->nL * sizeof(double) + 8);
     for (int l = 0; l <= L; l++) {
@@ -741,13 +863,22 @@ static int vcycle32(const hier_t *h, const double *r, double *z) {
         xl[l] = (float *)malloc((size_t)(n > 0 ? n : 1) * sizeof(float));
         if (!bl[l] || !xl[l]) st = OR_ERR_OOM;
     }
-    if (!t || !b64 || !x64) st = OR_ERR_OOM;
+    if (!t || !u || !b64 || !x64) st = OR_ERR_OOM;
     if (st) goto done;
     for (int i = 0; i < nmax; i++) bl[0][i] = (float)r[i];
     for (int l = 0; l < L; l++) {
         const level_t *lv = &h->lev[l];
         int n = lv->A.n, nc = h->lev[l + 1].A.n;
-        for (int i = 0; i < n; i++) xl[l][i] = lv->dinv32[i] * bl[l][i];
+        if (h->nu > 0) {
+            int nb = gs_rows(h, n);
+            sweep32(&lv->A, lv->v32, lv->dinv32, nb, bl[l], NULL, xl[l], 1);
+            for (int s = 1; s < h->nu; s++) {
+                memcpy(u, xl[l], (size_t)n * sizeof(float));
+                sweep32(&lv->A, lv->v32, lv->dinv32, nb, bl[l], u, xl[l], 1);
+            }
+        } else {
+            for (int i = 0; i < n; i++) xl[l][i] = lv->dinv32[i] * bl[l][i];
+        }
         spmv32(&lv->A, lv->v32, xl[l], t);
         for (int I = 0; I < nc; I++) bl[l + 1][I] = 0.0f;
         for (int i = 0; i < n; i++)
@@ -761,13 +892,21 @@ static int vcycle32(const hier_t *h, const double *r, double *z) {
         int n = lv->A.n;
         for (int i = 0; i < n; i++)
             if (lv->agg[i] >= 0) xl[l][i] += lv->p32[i] * xl[l + 1][lv->agg[i]];
-        spmv32(&lv->A, lv->v32, xl[l], t);
-        for (int i = 0; i < n; i++) xl[l][i] = xl[l][i] + lv->dinv32[i] * (bl[l][i] - t[i]);
+        if (h->nu > 0) {
+            int nb = gs_rows(h, n);
+            for (int s = 0; s < h->nu; s++) {
+                memcpy(u, xl[l], (size_t)n * sizeof(float));
+                sweep32(&lv->A, lv->v32, lv->dinv32, nb, bl[l], u, xl[l], 0);
+            }
+        } else {
+            spmv32(&lv->A, lv->v32, xl[l], t);
+            for (int i = 0; i < n; i++) xl[l][i] = xl[l][i] + lv->dinv32[i] * (bl[l][i] - t[i]);
+        }
     }
     for (int i = 0; i < nmax; i++) z[i] = (double)xl[0][i];
 done:
     for (int l = 0; l <= L; l++) { free(bl[l]); free(xl[l]); }
-    free(t); free(b64); free(x64);
+    free(t); free(u); free(b64); free(x64);
     return st;
 }
 
