@@ -66,6 +66,8 @@ def parse_args(argv=None):
     ap.add_argument("--serve-no-solo", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the fixed sweep launch shapes")
     ap.add_argument("--no-refresh", action="store_true", help="skip the partial-reuse (amg_refresh) measurement")
+    ap.add_argument("--gs-nu", type=int, default=4, help="sweeps of the hybrid Gauss-Seidel comparison (0: skip)")
+    ap.add_argument("--gs-blocks", type=int, default=65536, help="row blocks per level of the Gauss-Seidel smoother")
     return ap.parse_args(argv)
 
 
@@ -583,6 +585,25 @@ def run_ours(args):
         ra.close()
         fresh.close()
 
+    # the paper's smoother (Sec. 3.1): nu = 4 sweeps of l1 hybrid Gauss-Seidel
+    # over 65,536 row blocks per level, against the default one-sweep l1-Jacobi
+    smoother = {}
+    if args.gs_nu > 0:
+        ga = B.AMG.from_csr(prob.A, mode="fcg32", stream=stream)
+        smoother = {"workload": prob.name, "nu": args.gs_nu, "blocks_per_level": args.gs_blocks,
+                    "rows_per_block_level0": -(-prob.A.n // args.gs_blocks)}
+        for sm in ("l1_jacobi", "hybrid_gs"):
+            if sm == "hybrid_gs":
+                ga.set_smoother(args.gs_nu, args.gs_blocks, stream=stream)
+            row = {}
+            for mode in ("fcg32", "pcg64"):
+                ga.set_mode(mode)
+                m = timed_solves(ga, bs, x, 3, 1, args.rtol, args.maxit, torch, stream, None, device)
+                row[mode] = {"iters": statistics.median(m["iters"]), "ms_per_solve": m["total_ms"] / 3,
+                             "solves_per_s": 3e3 / m["total_ms"], "kernels_per_solve": m["launches"] / 3}
+            smoother[sm] = row
+        ga.close()
+
     # end to end through the C ABI with host buffers (pinned), copies inside the call
     pin_b = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
     pin_x = torch.zeros(prob.A.n, dtype=torch.float64).pin_memory().numpy()
@@ -695,6 +716,7 @@ def run_ours(args):
             "batch": batch,
             "serving": serving,
             "refresh": refresh,
+            "smoother": smoother,
             "fp64": {"value": solves / (f64_ms / 1e3), "unit": UNIT, "ms_per_step": f64_ms / args.steps,
                      "latency_ms": {"p50": pct(f64["lat_ms"], 50), "p99": pct(f64["lat_ms"], 99)},
                      "iters": statistics.median(f64["iters"]), "gpu_launches": f64["launches"]},

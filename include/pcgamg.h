@@ -124,6 +124,24 @@ int amg_setup(const amg_csr *A, const amg_params *p, void *stream, amg_handle *o
  * until a later amg_refresh succeeds. */
 int amg_refresh(amg_handle h, const amg_csr *A, void *stream);
 
+/* Smoother of h's V-cycle (Sec. 3.1). nu = 0: one l1-Jacobi sweep before and
+ * after the coarse correction (the setup's default, M = diag(sum_j |a_ij|)).
+ * nu in 1..64: nu sweeps of the l1 hybrid Gauss-Seidel method the paper
+ * smooths with (it uses nu = 4): block Jacobi over nblocks contiguous row
+ * blocks per level, ceil(n_l / nblocks) rows each (nblocks = 0: one row per
+ * block), each block solved by a forward Gauss-Seidel pass before and a
+ * backward pass after the coarse correction; d_i = a_ii + sum of |a_ij| over
+ * j outside i's block (the l1 form, no damping). One row per block and one
+ * sweep give the values of the default. Re-forms every level's smoother
+ * diagonal (and a float32 CSR copy of the level matrices for the sweeps);
+ * the next solve recaptures its graph; the shared-memory cluster tail is not
+ * used while nu > 0. Multi-column, batched and served solves run the l1-Jacobi
+ * kernels only and return AMG_ERR_ARG for a handle with nu > 0; amg_autotune
+ * returns AMG_OK without changes for it. Synchronises stream.
+ * Errors: AMG_ERR_ARG (NULL, nu or nblocks out of range), AMG_ERR_OOM,
+ * AMG_ERR_CUDA. */
+int amg_set_smoother(amg_handle h, int nu, int nblocks, void *stream);
+
 /* Host time (ms) of the last successful amg_refresh of h. */
 int amg_refresh_time(amg_handle h, double *ms);
 

@@ -28,7 +28,7 @@ EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode
            "amg_batch_create", "pcg_solve_batch", "amg_batch_destroy", "amg_server_default_params",
            "amg_serve_plan", "amg_server_create", "amg_server_mesh_info", "amg_server_info", "amg_server_submit",
            "amg_server_progress", "amg_server_result", "amg_server_destroy", "amg_autotune", "amg_level_shape",
-           "amg_set_level_shape", "amg_profile_levels", "amg_refresh", "amg_refresh_time")
+           "amg_set_level_shape", "amg_profile_levels", "amg_refresh", "amg_refresh_time", "amg_set_smoother")
 
 
 class AmgCsr(C.Structure):
@@ -91,6 +91,8 @@ def load(build_if_missing: bool = True):
     lib.amg_refresh.restype = I
     lib.amg_refresh_time.argtypes = [P, C.POINTER(C.c_double)]
     lib.amg_refresh_time.restype = I
+    lib.amg_set_smoother.argtypes = [P, I, I, P]
+    lib.amg_set_smoother.restype = I
     lib.amg_profile.argtypes = [P, I]
     lib.amg_profile.restype = I
     lib.amg_profile_read.argtypes = [P, P, P, I]
@@ -426,6 +428,13 @@ class AMG:
         if check and st:
             raise AmgError(st, last_error())
         return st
+
+    def set_smoother(self, nu: int, nblocks: int = 0, stream=None):
+        """``amg_set_smoother``: nu = 0 the one-sweep l1-Jacobi default; nu >= 1
+        sweeps of l1 hybrid Gauss-Seidel over ``nblocks`` row blocks per level."""
+        st = load().amg_set_smoother(self._h, nu, nblocks, _stream_ptr(stream))
+        if st:
+            raise AmgError(st, last_error())
 
     def refresh_ms(self) -> float:
         ms = C.c_double(0.0)

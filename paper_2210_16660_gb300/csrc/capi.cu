@@ -174,6 +174,15 @@ int amg_refresh(amg_handle h, const amg_csr *A, void *stream) {
     return refresh_impl(h, A, s);
 }
 
+int amg_set_smoother(amg_handle h, int nu, int nblocks, void *stream) {
+    set_error("");
+    if (!h || nu < 0 || nu > 64 || nblocks < 0) {
+        set_error("amg_set_smoother: NULL handle, or nu outside 0..64, or nblocks < 0");
+        return AMG_ERR_ARG;
+    }
+    return set_smoother_impl(h, nu, nblocks, (cudaStream_t)stream);
+}
+
 int amg_refresh_time(amg_handle h, double *ms) {
     if (!h || !ms) {
         set_error("amg_refresh_time: NULL argument");
@@ -229,8 +238,9 @@ int amg_level_shape(amg_handle h, int level, int *shape) {
 int pcg_solve_multi(amg_handle h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
                     double *res_hist, void *stream) {
     set_error("");
-    if (!h || h->invalid) {
-        set_error("pcg_solve_multi: NULL handle, or its last amg_refresh failed");
+    if (!h || h->invalid || h->gs_nu) {
+        set_error("pcg_solve_multi: NULL handle, its last amg_refresh failed, or it smooths by Gauss-Seidel "
+                  "(the multi-column kernels implement the l1-Jacobi sweeps only)");
         return AMG_ERR_ARG;
     }
     return solve_multi_impl(h, k, B, X, rtol, maxit, iters, res_hist, (cudaStream_t)stream);

@@ -121,6 +121,7 @@ struct Level {
     float *p32 = nullptr;
     int32_t *rptr = nullptr;  // members of each coarse row: rptr[nc+1], ridx[...]
     int32_t *ridx = nullptr;
+    float *v32csr = nullptr;  // float32 copy of A.v (CSR order), for the Gauss-Seidel sweeps
     std::vector<int32_t *> pass_agg;
     std::vector<int> pass_n;  // rows entering pass k; pass_n[npass] = nc
     // V-cycle work vectors: right-hand side, solution, restriction input,
@@ -252,6 +253,10 @@ struct amg_hier {
     int graph_body_kernels_nt[2] = {0, 0};
     int no_tail = 0;  // set while capturing a solve that must not use the tail
     int invalid = 0;  // set while a refresh is incomplete (or failed): solves are refused
+    // smoother: gs_nu = 0 is the one-sweep l1-Jacobi of the setup; otherwise
+    // gs_nu sweeps of l1 hybrid Gauss-Seidel over gs_blocks row blocks per
+    // level (amg_set_smoother)
+    int gs_nu = 0, gs_blocks = 0;
     double refresh_ms = 0;  // host time of the last amg_refresh
     int use_graph = 1;
     int no_col16 = 0;
@@ -274,6 +279,8 @@ struct amg_hier {
 namespace pcgamg {
 int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_t s);
 int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s);
+int set_smoother_impl(amg_hier *h, int nu, int nblocks, cudaStream_t s);
+int gs_rows(int n, int nblocks);
 int refresh_smem_tail(amg_hier *h);
 int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, int *iters,
                double *res_hist, cudaStream_t s);

@@ -386,6 +386,10 @@ int amg_server_create(const amg_server_params *p, int m, const amg_handle *meshe
             set_error("amg_server_create: mesh %d is NULL", i);
             return AMG_ERR_ARG;
         }
+        if (meshes[i]->gs_nu) {
+            set_error("amg_server_create: mesh %d smooths by Gauss-Seidel (engines run the l1-Jacobi sweeps)", i);
+            return AMG_ERR_ARG;
+        }
         if (meshes[i]->lev.size() < 2) {
             set_error("amg_server_create: mesh %d has a single level (serving needs a coarse level)", i);
             return AMG_ERR_ARG;
@@ -489,8 +493,8 @@ int amg_server_submit(amg_server sv, int mesh, const double *b, const double *x0
                   mesh);
         return AMG_ERR_OOM;
     }
-    if (sv->meshes[mesh]->invalid) {
-        set_error("amg_server_submit: the last amg_refresh of mesh %d failed", mesh);
+    if (sv->meshes[mesh]->invalid || sv->meshes[mesh]->gs_nu) {
+        set_error("amg_server_submit: mesh %d: its last amg_refresh failed, or it smooths by Gauss-Seidel", mesh);
         return AMG_ERR_ARG;
     }
     if (sv->queued >= sv->prm.queue_cap) {

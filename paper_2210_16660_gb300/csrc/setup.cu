@@ -388,6 +388,24 @@ __global__ void k_l1diag(int n, const int32_t *__restrict__ rp, const double *__
     dinv32[i] = __double2float_rn(d);
 }
 
+// l1 diagonal of the hybrid Gauss-Seidel smoother, blocks of nb rows:
+// d_i = a_ii + sum of |a_ij| over j outside i's block (row order; in-block
+// off-diagonal entries skipped), stored inverted. nb = 1 is k_l1diag.
+__global__ void k_hybrid_l1(int n, int nb, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, double *__restrict__ dinv, float *__restrict__ dinv32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = (i / nb) * nb, hi = lo + nb;
+    double s = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+        int j = ci[k];
+        if (j == i || j < lo || j >= hi) s = __dadd_rn(s, fabs(v[k]));
+    }
+    double d = __ddiv_rn(1.0, s);
+    dinv[i] = d;
+    dinv32[i] = __double2float_rn(d);
+}
+
 __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = __double2float_rn(a[i]);
@@ -1122,9 +1140,14 @@ int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s) {
         Level &lv = h->lev[l];
         Sell &S = lv.S;
         int nl = lv.A.n;
-        k_l1diag<<<grid_for(nl), kBlock, 0, s>>>(nl, lv.A.rp, lv.A.v, lv.dinv, lv.dinv32);
+        if (h->gs_nu > 0)
+            k_hybrid_l1<<<grid_for(nl), kBlock, 0, s>>>(nl, gs_rows(nl, h->gs_blocks), lv.A.rp, lv.A.ci, lv.A.v,
+                                                        lv.dinv, lv.dinv32);
+        else
+            k_l1diag<<<grid_for(nl), kBlock, 0, s>>>(nl, lv.A.rp, lv.A.v, lv.dinv, lv.dinv32);
         k_sell_vals<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(nl, S.nslices, lv.A.rp, lv.A.v,
                                                                              S.sptr, S.v64, S.v32);
+        if (lv.v32csr) k_to_f32<<<grid_for(lv.A.nnz), kBlock, 0, s>>>(lv.A.v, lv.v32csr, lv.A.nnz);
         PCG_LAUNCH_CK();
     }
     // dense inverse of the coarsest matrix, in place
@@ -1152,6 +1175,45 @@ int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s) {
     PCG_TRY(refresh_smem_tail(h));
     h->invalid = 0;
     h->refresh_ms = now_ms() - t_begin;
+    return AMG_OK;
+}
+
+// Rows per Gauss-Seidel block of a level with n rows: nblocks contiguous
+// blocks per level ("processes", Sec. 3.1), so blocks shrink on coarser
+// levels; nblocks = 0 gives one row per block.
+int gs_rows(int n, int nblocks) {
+    if (nblocks <= 0) return 1;
+    int64_t nb = ((int64_t)n + nblocks - 1) / nblocks;
+    return nb < 1 ? 1 : (int)nb;
+}
+
+// Smoother of the V-cycle: nu = 0 restores the setup's one-sweep l1-Jacobi;
+// nu >= 1 selects nu sweeps of l1 hybrid Gauss-Seidel over nblocks row blocks
+// per level (Sec. 3.1 with the l1 reading). Forms D^-1 by the block rule and
+// the float32 CSR values the sweeps read; captured graphs are dropped.
+int set_smoother_impl(amg_hier *h, int nu, int nblocks, cudaStream_t s) {
+    Mem &M = h->mem;
+    M.stream = s;
+    PCG_CK(cudaStreamSynchronize(s));
+    drop_graphs(h);
+    h->gs_nu = 0;  // the Jacobi diagonals until the new ones are in place
+    for (Level &lv : h->lev) {
+        int nl = lv.A.n;
+        if (nu > 0) {
+            if (!lv.v32csr) {
+                PCG_TRY(alloc(M, &lv.v32csr, lv.A.nnz));
+                k_to_f32<<<grid_for(lv.A.nnz), kBlock, 0, s>>>(lv.A.v, lv.v32csr, lv.A.nnz);
+            }
+            k_hybrid_l1<<<grid_for(nl), kBlock, 0, s>>>(nl, gs_rows(nl, nblocks), lv.A.rp, lv.A.ci, lv.A.v, lv.dinv,
+                                                        lv.dinv32);
+        } else {
+            k_l1diag<<<grid_for(nl), kBlock, 0, s>>>(nl, lv.A.rp, lv.A.v, lv.dinv, lv.dinv32);
+        }
+        PCG_LAUNCH_CK();
+    }
+    PCG_CK(cudaStreamSynchronize(s));
+    h->gs_nu = nu;
+    h->gs_blocks = nu > 0 ? nblocks : 0;
     return AMG_OK;
 }
 

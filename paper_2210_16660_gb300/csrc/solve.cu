@@ -263,6 +263,68 @@ __global__ void __launch_bounds__(kBlock) k_prolong_post(int n, const int32_t *_
     }
 }
 
+// ------------------------------------------------------------ hybrid Gauss-Seidel
+// One sweep of the l1 hybrid Gauss-Seidel smoother (Sec. 3.1, l1 reading):
+// xn = xo + M^{-1} (b - A xo), M = blockdiag(L_pp + D_l1) for FWD (rows of a
+// block in increasing order) or its transpose (decreasing order). One thread
+// per block of nb contiguous rows: it first copies its rows of xo into xn,
+// then updates them in order, reading its own block's values from xn (the
+// ones already updated) and every other block's from xo (block Jacobi).
+// ZERO: xo = 0 (the first pre-smoothing sweep), x_r = d_r (b_r - acc).
+// Entries are summed in storage order; with one row per block and one sweep
+// the values are those of the l1-Jacobi sweeps (k_down's xpre, k_post).
+template <typename T, bool FWD, bool ZERO>
+__global__ void __launch_bounds__(kBlock) k_gs_sweep(int n, int nb, const int32_t *__restrict__ rp,
+                                                     const int32_t *__restrict__ ci, const T *__restrict__ v,
+                                                     const T *__restrict__ dinv, const T *__restrict__ b,
+                                                     const T *__restrict__ xo, T *xn, const Ctl *__restrict__ ctl) {
+    pdl_enter();
+    if (ctl->done) return;
+    int64_t lo64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * nb;
+    if (lo64 >= n) return;
+    const int lo = (int)lo64, hi = (int)min((int64_t)n, lo64 + nb);
+    for (int r = lo; r < hi; r++) xn[r] = ZERO ? T(0) : ldg(xo + r);
+    for (int q = 0; q < hi - lo; q++) {
+        const int r = FWD ? lo + q : hi - 1 - q;
+        T acc = 0;
+        const int32_t e = ldg(rp + r + 1);
+        for (int32_t k = ldg(rp + r); k < e; k++) {
+            const int j = ldg(ci + k);
+            T xj = (j >= lo && j < hi) ? xn[j] : (ZERO ? T(0) : ldg(xo + j));
+            acc += ldg(v + k) * xj;
+        }
+        if (ZERO)
+            xn[r] = ldg(dinv + r) * (ldg(b + r) - acc);
+        else
+            xn[r] = xn[r] + ldg(dinv + r) * (ldg(b + r) - acc);
+    }
+}
+
+// Level 0 after the Gauss-Seidel post-smoothing: z = x (widened), r.z and,
+// for FCG(1), z.q_old; the last block forms rho and beta. Same grid and row
+// order as the level-0 k_post, so the sums are formed in the same order.
+template <typename T, bool FCG>
+__global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_gs_finish0(int n, const T *__restrict__ x,
+                                                                           const double *__restrict__ r64,
+                                                                           const double *__restrict__ qold,
+                                                                           double *__restrict__ z, double *partials,
+                                                                           Ctl *ctl) {
+    pdl_enter();
+    if (ctl->done) return;
+    double rz = 0.0, zq = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double zo = (double)ldg(x + i);
+        z[i] = zo;
+        rz += ldg(r64 + i) * zo;
+        if (FCG) zq += zo * ldg(qold + i);
+    }
+    if (publish_partials(rz, zq, partials, &ctl->counter[0])) {
+        double a, bb;
+        final_sum2(partials, a, bb);
+        if (threadIdx.x == 0) finish_rho(ctl, a, bb);
+    }
+}
+
 // x_L = A_L^{-1} b_L, one warp per row; TO = float rounds the float64 result.
 template <typename TO>
 __global__ void __launch_bounds__(kBlock) k_coarse(int nL, const double *__restrict__ ainv,
@@ -550,6 +612,7 @@ struct LP<float> {
     static float *xpre(Level &l) { return l.xpre32; }
     static float *xp(Level &l) { return l.xp32; }
     static const float *r0(const amg_hier *h) { return h->r32; }
+    static const float *csr(const Level &l) { return l.v32csr; }
 };
 template <>
 struct LP<double> {
@@ -562,6 +625,7 @@ struct LP<double> {
     static double *xpre(Level &l) { return l.xpre64; }
     static double *xp(Level &l) { return l.xp64; }
     static const double *r0(const amg_hier *h) { return h->r; }
+    static const double *csr(const Level &l) { return l.A.v; }
 };
 
 REmit remit(amg_hier *h) {
@@ -763,6 +827,95 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     return AMG_OK;
 }
 
+// gs_nu Gauss-Seidel sweeps on level l: pre-smoothing (forward, from zero,
+// into xpre) or post-smoothing (backward, from xp, into x). Successive sweeps
+// alternate between the target and t (free at both points), arranged so the
+// last one writes the target. Returns the kernels launched.
+template <typename T>
+int launch_gs(amg_hier *h, int l, bool pre, const T *b, T *target, cudaStream_t s) {
+    using P = LP<T>;
+    Level &lv = h->lev[l];
+    const int n = lv.A.n, nu = h->gs_nu, nb = gs_rows(n, h->gs_blocks);
+    const unsigned g = (unsigned)((((int64_t)n + nb - 1) / nb + kBlock - 1) / kBlock);
+    const Ctl *ctl = h->ctl;
+    const T *src = pre ? nullptr : (const T *)P::xp(lv);
+    for (int sw = 1; sw <= nu; sw++) {
+        T *dst = (nu - sw) % 2 == 0 ? target : P::t(lv);
+        if (pre && sw == 1)
+            launch_k(h->pdl, k_gs_sweep<T, true, true>, g, kBlock, s, n, nb, (const int32_t *)lv.A.rp,
+                     (const int32_t *)lv.A.ci, P::csr(lv), P::dinv(lv), b, (const T *)nullptr, dst, ctl);
+        else if (pre)
+            launch_k(h->pdl, k_gs_sweep<T, true, false>, g, kBlock, s, n, nb, (const int32_t *)lv.A.rp,
+                     (const int32_t *)lv.A.ci, P::csr(lv), P::dinv(lv), b, src, dst, ctl);
+        else
+            launch_k(h->pdl, k_gs_sweep<T, false, false>, g, kBlock, s, n, nb, (const int32_t *)lv.A.rp,
+                     (const int32_t *)lv.A.ci, P::csr(lv), P::dinv(lv), b, src, dst, ctl);
+        src = dst;
+    }
+    return nu;
+}
+
+// z = B r with the hybrid Gauss-Seidel smoother (gs_nu sweeps each side):
+// the l1-Jacobi V-cycle with its smoothing steps replaced, the coarsest solve
+// by k_coarse (no cluster tail), rho and beta by k_gs_finish0.
+template <typename T, bool FCG>
+int launch_vcycle_gs(amg_hier *h, cudaStream_t s) {
+    using P = LP<T>;
+    auto &lev = h->lev;
+    int L = (int)lev.size() - 1;
+    Ctl *ctl = h->ctl;
+    Level &l0 = lev[0];
+    const T *b0 = P::r0(h);
+    const bool pdl = h->pdl;
+    int g0 = sizeof(T) == 4 ? h->grid32 : h->grid64;
+    int kernels = 0;
+    int sp1 = prof_begin(h, 0, s);
+    kernels += launch_gs<T>(h, 0, true, b0, P::xpre(l0), s);
+    WITH_COLS(l0.S, (launch_k(pdl, k_down<T, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n, l0.S.sptr, cols,
+                              P::val(l0), (const T *)P::xpre(l0), b0, P::p(l0), P::t(l0), (const Ctl *)ctl)));
+    kernels += 1;
+    prof_end(h, sp1, s);
+    int sp2 = prof_begin(h, 5, s);
+    for (int l = 0; l < L; l++) {
+        int spl = prof_begin(h, kLevelSpan + 3 * l, s);
+        unsigned char sh = lev[l].shape[prec_index<T>()][0];
+        if (l == 0) {
+            launch_restrict<T>(h, 0, s);
+            kernels += 1;
+        } else {
+            kernels += launch_gs<T>(h, l, true, P::b(lev[l]), P::xpre(lev[l]), s);
+            launch_down_phase<T>(h, l, sh, s);
+            kernels += (sh & 4) ? 1 : 2;
+        }
+        prof_end(h, spl, s);
+    }
+    int spc = prof_begin(h, kLevelSpan + 3 * L + 2, s);
+    launch_k(pdl, k_coarse<T>, (h->nL * 32 + kBlock - 1) / kBlock, kBlock, s, h->nL, h->Ainv, h->bL, P::x(lev[L]),
+             (const Ctl *)ctl);
+    kernels += 1;
+    prof_end(h, spc, s);
+    for (int l = L - 1; l >= 1; l--) {
+        Level &lv = lev[l];
+        int spl = prof_begin(h, kLevelSpan + 3 * l + 1, s);
+        launch_k(pdl, k_prolong<T>, grid_rows(lv.A.n), kBlock, s, lv.A.n, (const T *)P::xpre(lv), P::p(lv), lv.agg,
+                 (const T *)P::x(lev[l + 1]), P::xp(lv), (const Ctl *)ctl);
+        kernels += 1 + launch_gs<T>(h, l, false, P::b(lv), P::x(lv), s);
+        prof_end(h, spl, s);
+    }
+    prof_end(h, sp2, s);
+    int sp3 = prof_begin(h, 1, s);
+    launch_k(pdl, k_prolong<T>, h->gridv, kBlock, s, l0.A.n, (const T *)P::xpre(l0), P::p(l0), l0.agg,
+             (const T *)P::x(lev[1]), P::xp(l0), (const Ctl *)ctl);
+    kernels += 1 + launch_gs<T>(h, 0, false, b0, P::x(l0), s);
+    launch_k(pdl, k_gs_finish0<T, FCG>, g0, kBlock, s, l0.A.n, (const T *)P::x(l0), (const double *)h->r,
+             (const double *)h->q, h->z, h->partials, ctl);
+    kernels += 1;
+    prof_end(h, sp3, s);
+    h->launches += kernels;
+    PCG_LAUNCH_CK();
+    return AMG_OK;
+}
+
 template <int MODE>
 int launch_iteration_t(amg_hier *h, cudaStream_t s) {
     int L = (int)h->lev.size() - 1;
@@ -774,9 +927,11 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
                  h->Ainv, h->r, h->z, h->q, h->partials, h->ctl);
         h->launches += 1;
     } else if (MODE == AMG_MODE_FCG32) {
-        PCG_TRY((launch_vcycle<float, true>(h, s)));
+        if (h->gs_nu) PCG_TRY((launch_vcycle_gs<float, true>(h, s)));
+        else PCG_TRY((launch_vcycle<float, true>(h, s)));
     } else {
-        PCG_TRY((launch_vcycle<double, false>(h, s)));
+        if (h->gs_nu) PCG_TRY((launch_vcycle_gs<double, false>(h, s)));
+        else PCG_TRY((launch_vcycle<double, false>(h, s)));
     }
     int sp4 = prof_begin(h, 6, s);
     launch_k(pdl, k_axpy_p, h->gridv, kBlock, s, n, h->z, h->p, h->ctl);
@@ -1066,6 +1221,7 @@ int tune_level(amg_hier *h, int l, cudaStream_t s, int reps, cudaEvent_t e0, cud
 int autotune_impl(amg_hier *h, cudaStream_t s, int reps, int *changed) {
     int L = (int)h->lev.size() - 1;
     *changed = 0;
+    if (h->gs_nu) return AMG_OK;  // the shapes tune the l1-Jacobi sweeps only
     if (reps < 1) reps = 1;
     PCG_CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
     for (int l = 1; l <= L; l++) {
