@@ -122,6 +122,17 @@ struct Level {
     int32_t *rptr = nullptr;  // members of each coarse row: rptr[nc+1], ridx[...]
     int32_t *ridx = nullptr;
     float *v32csr = nullptr;  // float32 copy of A.v (CSR order), for the Gauss-Seidel sweeps
+    // two-phase Gauss-Seidel sweeps (blocks of at most 32 rows): for the
+    // forward [0] and backward [1] pass, each row's in-block entries that the
+    // pass has already updated (j < r in the block, resp. j > r), width
+    // gs_w[d] per row (column -1 pads), storage order; gs_w[d] < 0: the level
+    // sweeps with one thread per block instead. gs_acc: per-row sums of the
+    // other entries (phase one of a sweep).
+    int gs_w[2] = {-1, -1};
+    int32_t *gs_ci[2] = {nullptr, nullptr};
+    double *gs_v64[2] = {nullptr, nullptr};
+    float *gs_v32[2] = {nullptr, nullptr};
+    double *gs_acc = nullptr;
     std::vector<int32_t *> pass_agg;
     std::vector<int> pass_n;  // rows entering pass k; pass_n[npass] = nc
     // V-cycle work vectors: right-hand side, solution, restriction input,
@@ -281,6 +292,7 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
 int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s);
 int set_smoother_impl(amg_hier *h, int nu, int nblocks, cudaStream_t s);
 int gs_rows(int n, int nblocks);
+int fill_gs_parts(Level &lv, int nblocks, cudaStream_t s);
 int refresh_smem_tail(amg_hier *h);
 int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, int *iters,
                double *res_hist, cudaStream_t s);

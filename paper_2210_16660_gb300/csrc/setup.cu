@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 
 #include "internal.cuh"
 
@@ -404,6 +405,48 @@ __global__ void k_hybrid_l1(int n, int nb, const int32_t *__restrict__ rp, const
     double d = __ddiv_rn(1.0, s);
     dinv[i] = d;
     dinv32[i] = __double2float_rn(d);
+}
+
+// In-block entries a pass has already updated when it reaches row i (LOWER:
+// j in [lo, i), the forward pass; else j in (i, hi), the backward pass):
+// count, then fill a width-w table in storage order (column -1, value 0 pad).
+template <bool LOWER>
+__global__ void k_part_count(int n, int nb, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             int32_t *__restrict__ cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = (i / nb) * nb, hi = min(n, lo + nb);
+    int c = 0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+        int j = ci[k];
+        if (LOWER ? (j >= lo && j < i) : (j > i && j < hi)) c++;
+    }
+    cnt[i] = c;
+}
+
+template <bool LOWER>
+__global__ void k_part_fill(int n, int nb, int w, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, int32_t *__restrict__ pci, double *__restrict__ pv64,
+                            float *__restrict__ pv32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = (i / nb) * nb, hi = min(n, lo + nb);
+    int64_t base = (int64_t)i * w;
+    int c = 0;
+    for (int32_t k = rp[i]; k < rp[i + 1] && c < w; k++) {
+        int j = ci[k];
+        if (LOWER ? (j >= lo && j < i) : (j > i && j < hi)) {
+            pci[base + c] = j;
+            pv64[base + c] = v[k];
+            pv32[base + c] = __double2float_rn(v[k]);
+            c++;
+        }
+    }
+    for (; c < w; c++) {
+        pci[base + c] = -1;
+        pv64[base + c] = 0.0;
+        pv32[base + c] = 0.0f;
+    }
 }
 
 __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
@@ -1149,6 +1192,7 @@ int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s) {
                                                                              S.sptr, S.v64, S.v32);
         if (lv.v32csr) k_to_f32<<<grid_for(lv.A.nnz), kBlock, 0, s>>>(lv.A.v, lv.v32csr, lv.A.nnz);
         PCG_LAUNCH_CK();
+        if (h->gs_nu) PCG_TRY(fill_gs_parts(lv, h->gs_blocks, s));
     }
     // dense inverse of the coarsest matrix, in place
     Level &lc = h->lev[L];
@@ -1187,6 +1231,61 @@ int gs_rows(int n, int nblocks) {
     return nb < 1 ? 1 : (int)nb;
 }
 
+// The two-phase sweep tables of a level (values of its current matrix): for
+// blocks of at most 32 rows whose rows have at most kGsPart already-updated
+// in-block entries; other levels keep gs_w = -1 (one thread per block).
+constexpr int kGsPart = 8;
+int build_gs_parts(amg_hier *h, Level &lv, int nblocks, cudaStream_t s) {
+    Mem &M = h->mem;
+    int n = lv.A.n, nb = gs_rows(n, nblocks);
+    for (int d = 0; d < 2; d++) {
+        release(M, lv.gs_ci[d]);
+        release(M, lv.gs_v64[d]);
+        release(M, lv.gs_v32[d]);
+        lv.gs_w[d] = -1;
+    }
+    if (nb > 32) return AMG_OK;
+    int32_t *cnt = nullptr;
+    PCG_TRY(alloc(M, &cnt, n));
+    std::vector<int32_t> hc(n);
+    for (int d = 0; d < 2; d++) {
+        if (d == 0) k_part_count<true><<<grid_for(n), kBlock, 0, s>>>(n, nb, lv.A.rp, lv.A.ci, cnt);
+        else k_part_count<false><<<grid_for(n), kBlock, 0, s>>>(n, nb, lv.A.rp, lv.A.ci, cnt);
+        PCG_LAUNCH_CK();
+        PCG_CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaStreamSynchronize(s));
+        int w = 0;
+        for (int i = 0; i < n; i++) w = std::max(w, (int)hc[i]);
+        if (w > kGsPart) continue;
+        lv.gs_w[d] = w;
+        if (w > 0) {
+            PCG_TRY(alloc(M, &lv.gs_ci[d], (size_t)n * w));
+            PCG_TRY(alloc(M, &lv.gs_v64[d], (size_t)n * w));
+            PCG_TRY(alloc(M, &lv.gs_v32[d], (size_t)n * w));
+        }
+    }
+    release(M, cnt);
+    if (!lv.gs_acc) PCG_TRY(alloc(M, &lv.gs_acc, n));
+    return fill_gs_parts(lv, nblocks, s);
+}
+
+// Values of the tables (after a setup of the smoother or a refresh).
+int fill_gs_parts(Level &lv, int nblocks, cudaStream_t s) {
+    int n = lv.A.n, nb = gs_rows(n, nblocks);
+    for (int d = 0; d < 2; d++) {
+        int w = lv.gs_w[d];
+        if (w <= 0) continue;
+        if (d == 0)
+            k_part_fill<true><<<grid_for(n), kBlock, 0, s>>>(n, nb, w, lv.A.rp, lv.A.ci, lv.A.v, lv.gs_ci[d],
+                                                             lv.gs_v64[d], lv.gs_v32[d]);
+        else
+            k_part_fill<false><<<grid_for(n), kBlock, 0, s>>>(n, nb, w, lv.A.rp, lv.A.ci, lv.A.v, lv.gs_ci[d],
+                                                              lv.gs_v64[d], lv.gs_v32[d]);
+        PCG_LAUNCH_CK();
+    }
+    return AMG_OK;
+}
+
 // Smoother of the V-cycle: nu = 0 restores the setup's one-sweep l1-Jacobi;
 // nu >= 1 selects nu sweeps of l1 hybrid Gauss-Seidel over nblocks row blocks
 // per level (Sec. 3.1 with the l1 reading). Forms D^-1 by the block rule and
@@ -1206,6 +1305,7 @@ int set_smoother_impl(amg_hier *h, int nu, int nblocks, cudaStream_t s) {
             }
             k_hybrid_l1<<<grid_for(nl), kBlock, 0, s>>>(nl, gs_rows(nl, nblocks), lv.A.rp, lv.A.ci, lv.A.v, lv.dinv,
                                                         lv.dinv32);
+            PCG_TRY(build_gs_parts(h, lv, nblocks, s));
         } else {
             k_l1diag<<<grid_for(nl), kBlock, 0, s>>>(nl, lv.A.rp, lv.A.v, lv.dinv, lv.dinv32);
         }

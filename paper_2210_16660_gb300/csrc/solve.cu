@@ -300,6 +300,69 @@ __global__ void __launch_bounds__(kBlock) k_gs_sweep(int n, int nb, const int32_
     }
 }
 
+// Two-phase form of the same sweep, for blocks of at most 32 rows. Phase one,
+// one thread per row over the sliced-ELL layout: acc_r = sum of a_rj x_old_j
+// over every entry of row r except the in-block ones the pass has already
+// updated when it reaches r (FWD: j in [lo, r); backward: j in (r, hi)),
+// which contribute 0 here. Phase two, one thread per block: the recurrence
+// over those entries alone (k_gs_block). Same values as k_gs_sweep up to the
+// order of the sums; with one row per block the sums are k_post's.
+template <typename T, typename IDX, int U, bool FWD, bool STREAM>
+__global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_gs_offsum(
+    int n, int nb, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
+    const T *__restrict__ xo, T *__restrict__ acc, const Ctl *__restrict__ ctl) {
+    pdl_enter();
+    if (ctl->done) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        SELL_ROW_BEGIN
+        const int lo = (i / nb) * nb, hi = min(n, lo + nb);
+        T a = sell_row<U, STREAM>(c_, a_, w_, i, [&](int j) {
+            bool done = FWD ? (j >= lo && j < i) : (j > i && j < hi);
+            return done ? T(0) : ldg(xo + j);
+        });
+        acc[i] = a;
+    }
+}
+
+constexpr int kGsThreads = 128;  // threads per CTA of k_gs_block (window: 33 values each)
+
+// Phase two: one thread per block of nb <= 32 rows, rows in pass order. The
+// block's new values live in a shared-memory window (33-value stride per
+// thread, so threads at the same row offset use different banks);
+// x_r = x_old_r + d_r (b_r - (acc_r + sum over the row's part entries of
+// a_rj x_new_j)). ZERO (first pre-smoothing pass, x_old = 0): acc = 0 and
+// x_r = d_r (b_r - sum).
+template <typename T, bool FWD, bool ZERO>
+__global__ void __launch_bounds__(kGsThreads) k_gs_block(int n, int nb, int w, const int32_t *__restrict__ pci,
+                                                         const T *__restrict__ pv, const T *__restrict__ dinv,
+                                                         const T *__restrict__ b, const T *__restrict__ xo,
+                                                         const T *__restrict__ acc, T *__restrict__ xn,
+                                                         const Ctl *__restrict__ ctl) {
+    __shared__ T win[kGsThreads * 33];
+    pdl_enter();
+    if (ctl->done) return;
+    int64_t lo64 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * nb;
+    if (lo64 >= n) return;
+    const int lo = (int)lo64, hi = (int)min((int64_t)n, lo64 + nb);
+    T *wv = win + threadIdx.x * 33;
+    for (int q = 0; q < hi - lo; q++) {
+        const int r = FWD ? lo + q : hi - 1 - q;
+        T sum = ZERO ? T(0) : ldg(acc + r);
+        const int64_t e = (int64_t)r * w;
+        for (int k = 0; k < w; k++) {
+            const int j = ldg(pci + e + k);
+            if (j >= 0) sum += ldg(pv + e + k) * wv[j - lo];
+        }
+        T x;
+        if (ZERO)
+            x = ldg(dinv + r) * (ldg(b + r) - sum);
+        else
+            x = ldg(xo + r) + ldg(dinv + r) * (ldg(b + r) - sum);
+        wv[r - lo] = x;
+        xn[r] = x;
+    }
+}
+
 // Level 0 after the Gauss-Seidel post-smoothing: z = x (widened), r.z and,
 // for FCG(1), z.q_old; the last block forms rho and beta. Same grid and row
 // order as the level-0 k_post, so the sums are formed in the same order.
@@ -613,6 +676,8 @@ struct LP<float> {
     static float *xp(Level &l) { return l.xp32; }
     static const float *r0(const amg_hier *h) { return h->r32; }
     static const float *csr(const Level &l) { return l.v32csr; }
+    static const float *part(const Level &l, int d) { return l.gs_v32[d]; }
+    static float *acc(const Level &l) { return reinterpret_cast<float *>(l.gs_acc); }
 };
 template <>
 struct LP<double> {
@@ -626,6 +691,8 @@ struct LP<double> {
     static double *xp(Level &l) { return l.xp64; }
     static const double *r0(const amg_hier *h) { return h->r; }
     static const double *csr(const Level &l) { return l.A.v; }
+    static const double *part(const Level &l, int d) { return l.gs_v64[d]; }
+    static double *acc(const Level &l) { return l.gs_acc; }
 };
 
 REmit remit(amg_hier *h) {
@@ -839,6 +906,53 @@ int launch_gs(amg_hier *h, int l, bool pre, const T *b, T *target, cudaStream_t 
     const unsigned g = (unsigned)((((int64_t)n + nb - 1) / nb + kBlock - 1) / kBlock);
     const Ctl *ctl = h->ctl;
     const T *src = pre ? nullptr : (const T *)P::xp(lv);
+    const int d = pre ? 0 : 1;  // the forward (pre) or backward (post) pass
+    if (lv.gs_w[d] >= 0) {
+        // two-phase sweeps
+        const int w = lv.gs_w[d];
+        const unsigned gb = (unsigned)((((int64_t)n + nb - 1) / nb + kGsThreads - 1) / kGsThreads);
+        const int gr = grid_rows(n);
+        const bool big = n > kSmallRows;
+        int kernels = 0;
+        for (int sw = 1; sw <= nu; sw++) {
+            T *dst = (nu - sw) % 2 == 0 ? target : P::t(lv);
+            const bool zero = pre && sw == 1;
+            if (!zero) {
+#define PCG_OFFSUM(UU, ST)                                                                                          \
+    WITH_COLS(lv.S, (launch_k(h->pdl, k_gs_offsum<T, IDX, UU, true, ST>, gr, kBlock, s, n, nb, lv.S.sptr, cols,     \
+                              P::val(lv), src, P::acc(lv), ctl)))
+#define PCG_OFFSUM_B(UU, ST)                                                                                        \
+    WITH_COLS(lv.S, (launch_k(h->pdl, k_gs_offsum<T, IDX, UU, false, ST>, gr, kBlock, s, n, nb, lv.S.sptr, cols,    \
+                              P::val(lv), src, P::acc(lv), ctl)))
+                if (pre) {
+                    if (l == 0) PCG_OFFSUM(kUnroll, true);
+                    else if (big) PCG_OFFSUM(kUnroll, false);
+                    else PCG_OFFSUM(kUnrollSmall, false);
+                } else {
+                    if (l == 0) PCG_OFFSUM_B(kUnroll, true);
+                    else if (big) PCG_OFFSUM_B(kUnroll, false);
+                    else PCG_OFFSUM_B(kUnrollSmall, false);
+                }
+#undef PCG_OFFSUM
+#undef PCG_OFFSUM_B
+                kernels++;
+            }
+            const int32_t *pci = lv.gs_ci[d];
+            const T *pv = P::part(lv, d);
+            if (zero)
+                launch_k(h->pdl, k_gs_block<T, true, true>, gb, kGsThreads, s, n, nb, w, pci, pv, P::dinv(lv), b,
+                         (const T *)nullptr, (const T *)nullptr, dst, ctl);
+            else if (pre)
+                launch_k(h->pdl, k_gs_block<T, true, false>, gb, kGsThreads, s, n, nb, w, pci, pv, P::dinv(lv), b,
+                         src, (const T *)P::acc(lv), dst, ctl);
+            else
+                launch_k(h->pdl, k_gs_block<T, false, false>, gb, kGsThreads, s, n, nb, w, pci, pv, P::dinv(lv), b,
+                         src, (const T *)P::acc(lv), dst, ctl);
+            kernels++;
+            src = dst;
+        }
+        return kernels;
+    }
     for (int sw = 1; sw <= nu; sw++) {
         T *dst = (nu - sw) % 2 == 0 ? target : P::t(lv);
         if (pre && sw == 1)
