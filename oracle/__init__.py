@@ -64,6 +64,12 @@ def load():
     lib.or_chol_solve.argtypes = [I, _f64p, _f64p, _f64p]
     lib.or_setup.restype = I
     lib.or_setup.argtypes = [I, _i32p, _i32p, _f64p, I, I, I, C.POINTER(P)]
+    lib.or_setup_ex.restype = I
+    lib.or_setup_ex.argtypes = [I, _i32p, _i32p, _f64p, I, I, I, I, C.POINTER(P)]
+    lib.or_level_P_nnz.restype = C.c_int64
+    lib.or_level_P_nnz.argtypes = [P, I]
+    lib.or_level_P.restype = None
+    lib.or_level_P.argtypes = [P, I, _i32p, _i32p, _f64p]
     lib.or_set_smoother.restype = I
     lib.or_set_smoother.argtypes = [P, I, I]
     lib.or_refresh.restype = I
@@ -176,11 +182,13 @@ def chol_solve(L, b):
 class Hierarchy:
     """Oracle AMG hierarchy (aggregation by matching, tentative prolongator)."""
 
-    def __init__(self, A, coarse_max: int = 200, n_pass: int = 3, max_levels: int = 30):
+    def __init__(self, A, coarse_max: int = 200, n_pass: int = 3, max_levels: int = 30, smoothed: bool = False):
+        """``smoothed``: prolongators P = (I - omega D^-1 A) P_hat (smoothed
+        aggregation, Sec. 3.1) instead of the tentative P_hat."""
         lib = load()
         n, rp, ci, v = _csr_args(A)
         h = C.c_void_p()
-        st = lib.or_setup(n, rp, ci, v, coarse_max, n_pass, max_levels, C.byref(h))
+        st = lib.or_setup_ex(n, rp, ci, v, coarse_max, n_pass, max_levels, int(smoothed), C.byref(h))
         self.status = st
         if st:
             raise RuntimeError(f"oracle setup status {st}")
@@ -245,6 +253,20 @@ class Hierarchy:
         agg = np.empty(max(m, 1), np.int32)
         nc = lib.or_pass_agg(self._h, l, ps, agg)
         return agg[:m], nc
+
+    def prolongator(self, l: int):
+        """Explicit (smoothed) prolongator of level l as CSR parts, or None
+        for the tentative one (use level_agg)."""
+        lib = load()
+        nz = lib.or_level_P_nnz(self._h, l)
+        if nz < 0:
+            return None
+        n, _, _ = self.level_size(l)
+        rp = np.empty(n + 1, np.int32)
+        ci = np.empty(max(nz, 1), np.int32)
+        v = np.empty(max(nz, 1))
+        lib.or_level_P(self._h, l, rp, ci, v)
+        return rp, ci[:nz], v[:nz]
 
     def coarse_factor(self):
         n, _, _ = self.level_size(self.nlevels - 1)

@@ -54,6 +54,10 @@ typedef struct {
     int pass_n[OR_MAX_PASS + 1];
     /* single-precision copies for the FP32 V-cycle */
     float *v32, *dinv32, *p32;
+    /* smoothed aggregation: the explicit prolongator P (n_l x n_{l+1}) and
+     * its float32 values; empty (P.rp == NULL) for the tentative one */
+    csr_t P;
+    float *P32;
 } level_t;
 
 typedef struct {
@@ -65,6 +69,7 @@ typedef struct {
      * sweeps of the l1 hybrid Gauss-Seidel method over nblocks row blocks per
      * level (or_set_smoother) */
     int nu, nblocks;
+    int smoothed;       /* 1: P = (I - omega D^-1 A) P_hat on every level */
 } hier_t;
 
 /* ---------------------------------------------------------------- helpers */
@@ -476,10 +481,235 @@ void or_free(hier_t *h) {
         csr_free(&lv->A);
         free(lv->dinv); free(lv->w); free(lv->agg); free(lv->p);
         free(lv->v32); free(lv->dinv32); free(lv->p32);
+        csr_free(&lv->P); free(lv->P32);
         for (int k = 0; k < OR_MAX_PASS; k++) free(lv->pass_agg[k]);
     }
     free(h->L);
     free(h);
+}
+
+/* ------------------------------------------------- smoothed aggregation
+ * Sec. 3.1: the prolongator actually used is P = (I - omega D^-1 A) P_hat,
+ * D = diag(A), omega = 1 / ||D^-1 A||_inf (~ 1 / rho(D^-1 A)). Aggregates of
+ * more than two come from multiplying the pass prolongators; reading: the
+ * tentative pass prolongators are multiplied into the level's P_hat (the
+ * composed map and weight), which is then smoothed once with the level's A.
+ *
+ * Row i of P: the tentative entry p_i at column agg(i), then, for each stored
+ * a_ij with agg(j) >= 0, -omega (a_ij / a_ii) p_j added to column agg(j);
+ * contributions to one column are added in increasing j, starting from the
+ * tentative entry. Columns sorted; every column that receives a contribution
+ * is kept (exact zeros included), so the pattern depends on A's pattern only.
+ */
+static double smoothing_omega(const csr_t *a) {
+    double mx = 0.0;
+    for (int i = 0; i < a->n; i++) {
+        double d = diag_of(a, i), s = 0.0;
+        for (int32_t k = a->rp[i]; k < a->rp[i + 1]; k++) s += fabs(a->v[k]) / d;
+        if (s > mx) mx = s;
+    }
+    return 1.0 / mx;
+}
+
+typedef struct { int32_t J, j; double t; } pterm_t;
+
+static int pterm_cmp(const void *pa, const void *pb) {
+    const pterm_t *a = (const pterm_t *)pa, *b = (const pterm_t *)pb;
+    if (a->J != b->J) return a->J < b->J ? -1 : 1;
+    if (a->j != b->j) return a->j < b->j ? -1 : 1;
+    return 0;
+}
+
+static int smooth_prolongator(const csr_t *a, const int32_t *agg, const double *p, int nc, double omega,
+                              csr_t *P) {
+    int n = a->n;
+    P->n = n;
+    P->rp = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int64_t cap = a->nnz + n + 16;
+    P->ci = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    P->v = (double *)malloc((size_t)cap * sizeof(double));
+    int64_t tcap = 64;
+    pterm_t *tm = (pterm_t *)malloc((size_t)tcap * sizeof(pterm_t));
+    if (!P->rp || !P->ci || !P->v || !tm) { free(tm); csr_free(P); return OR_ERR_OOM; }
+    (void)nc;
+    int64_t nz = 0;
+    P->rp[0] = 0;
+    for (int i = 0; i < n; i++) {
+        int64_t nt = 0;
+        double s = omega / diag_of(a, i);
+        /* the tentative entry sorts first within its column (j = -1) */
+        if (agg[i] >= 0) { tm[nt].J = agg[i]; tm[nt].j = -1; tm[nt].t = p[i]; nt++; }
+        for (int32_t k = a->rp[i]; k < a->rp[i + 1]; k++) {
+            int j = a->ci[k];
+            if (agg[j] < 0) continue;
+            if (nt == tcap) {
+                tcap *= 2;
+                pterm_t *t2 = (pterm_t *)realloc(tm, (size_t)tcap * sizeof(pterm_t));
+                if (!t2) { free(tm); csr_free(P); return OR_ERR_OOM; }
+                tm = t2;
+            }
+            tm[nt].J = agg[j]; tm[nt].j = j; tm[nt].t = -(s * a->v[k]) * p[j];
+            nt++;
+        }
+        qsort(tm, (size_t)nt, sizeof(pterm_t), pterm_cmp);
+        for (int64_t t = 0; t < nt; t++) {
+            if (t == 0 || tm[t].J != tm[t - 1].J) {
+                P->ci[nz] = tm[t].J;
+                P->v[nz] = tm[t].t;
+                nz++;
+            } else {
+                P->v[nz - 1] = P->v[nz - 1] + tm[t].t;
+            }
+        }
+        P->rp[i + 1] = (int32_t)nz;
+    }
+    P->nnz = nz;
+    free(tm);
+    return OR_OK;
+}
+
+/* A_c = P^T A P for an explicit P. Row I of A_c for columns J >= I:
+ * acc_J = sum over the rows i of P's column I (increasing i) of
+ * p_iI * (A P)_iJ, with (A P)_iJ = sum over a_ik (storage order) of
+ * a_ik p_kJ; the entries below the diagonal are mirrored from above, so A_c
+ * is bitwise symmetric (the next level's matching reads one copy of each
+ * coupling). */
+static int rap_explicit(const csr_t *a, const csr_t *P, int nc, csr_t *out) {
+    int n = a->n;
+    /* A P, row by row, columns sorted */
+    double *acc = (double *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(double));
+    int32_t *mark = (int32_t *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int32_t));
+    int32_t *list = (int32_t *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int32_t));
+    csr_t AP = {n, 0, NULL, NULL, NULL};
+    AP.rp = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int64_t cap = 1024;
+    AP.ci = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    AP.v = (double *)malloc((size_t)cap * sizeof(double));
+    if (!acc || !mark || !list || !AP.rp || !AP.ci || !AP.v) {
+        free(acc); free(mark); free(list); csr_free(&AP); return OR_ERR_OOM;
+    }
+    for (int J = 0; J < nc; J++) mark[J] = -1;
+    int64_t nz = 0;
+    AP.rp[0] = 0;
+    for (int i = 0; i < n; i++) {
+        int m = 0;
+        for (int32_t k = a->rp[i]; k < a->rp[i + 1]; k++) {
+            int c = a->ci[k];
+            for (int32_t q = P->rp[c]; q < P->rp[c + 1]; q++) {
+                int J = P->ci[q];
+                if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; list[m++] = J; }
+                acc[J] = acc[J] + a->v[k] * P->v[q];
+            }
+        }
+        /* sort the touched columns (insertion sort: rows are short) */
+        for (int x = 1; x < m; x++) {
+            int y = list[x], z = x;
+            while (z > 0 && list[z - 1] > y) { list[z] = list[z - 1]; z--; }
+            list[z] = y;
+        }
+        if (nz + m > cap) {
+            while (nz + m > cap) cap *= 2;
+            int32_t *c2 = (int32_t *)realloc(AP.ci, (size_t)cap * sizeof(int32_t));
+            if (c2) AP.ci = c2;
+            double *v2 = (double *)realloc(AP.v, (size_t)cap * sizeof(double));
+            if (v2) AP.v = v2;
+            if (!c2 || !v2) { free(acc); free(mark); free(list); csr_free(&AP); return OR_ERR_OOM; }
+        }
+        for (int x = 0; x < m; x++) { AP.ci[nz] = list[x]; AP.v[nz] = acc[list[x]]; nz++; }
+        AP.rp[i + 1] = (int32_t)nz;
+    }
+    AP.nnz = nz;
+    /* P^T by columns: for each coarse I, the rows i with p_iI != stored */
+    int32_t *tc = (int32_t *)calloc((size_t)nc + 1, sizeof(int32_t));
+    int32_t *ti = (int32_t *)malloc((size_t)(P->nnz > 0 ? P->nnz : 1) * sizeof(int32_t));
+    double *tv = (double *)malloc((size_t)(P->nnz > 0 ? P->nnz : 1) * sizeof(double));
+    int32_t *fill = (int32_t *)malloc(((size_t)nc + 1) * sizeof(int32_t));
+    if (!tc || !ti || !tv || !fill) {
+        free(tc); free(ti); free(tv); free(fill); free(acc); free(mark); free(list); csr_free(&AP);
+        return OR_ERR_OOM;
+    }
+    for (int64_t q = 0; q < P->nnz; q++) tc[P->ci[q] + 1]++;
+    for (int I = 0; I < nc; I++) tc[I + 1] += tc[I];
+    memcpy(fill, tc, ((size_t)nc + 1) * sizeof(int32_t));
+    for (int i = 0; i < n; i++)
+        for (int32_t q = P->rp[i]; q < P->rp[i + 1]; q++) {
+            int32_t pos = fill[P->ci[q]]++;
+            ti[pos] = i;
+            tv[pos] = P->v[q];
+        }
+    free(fill);
+    /* upper part of each coarse row */
+    int32_t *ucnt = (int32_t *)calloc((size_t)nc + 1, sizeof(int32_t));
+    int64_t ucap = 1024, unz = 0;
+    int32_t *uJ = (int32_t *)malloc((size_t)ucap * sizeof(int32_t));
+    double *uV = (double *)malloc((size_t)ucap * sizeof(double));
+    int32_t *urp = (int32_t *)malloc(((size_t)nc + 1) * sizeof(int32_t));
+    int st = OR_OK;
+    if (!ucnt || !uJ || !uV || !urp) st = OR_ERR_OOM;
+    for (int J = 0; J < nc; J++) mark[J] = -1;
+    if (!st) urp[0] = 0;
+    for (int I = 0; I < nc && !st; I++) {
+        int m = 0;
+        for (int32_t q = tc[I]; q < tc[I + 1]; q++) {
+            int i = ti[q];
+            double pv = tv[q];
+            for (int32_t r = AP.rp[i]; r < AP.rp[i + 1]; r++) {
+                int J = AP.ci[r];
+                if (J < I) continue;
+                if (mark[J] != I) { mark[J] = I; acc[J] = 0.0; list[m++] = J; }
+                acc[J] = acc[J] + pv * AP.v[r];
+            }
+        }
+        for (int x = 1; x < m; x++) {
+            int y = list[x], z = x;
+            while (z > 0 && list[z - 1] > y) { list[z] = list[z - 1]; z--; }
+            list[z] = y;
+        }
+        if (unz + m > ucap) {
+            while (unz + m > ucap) ucap *= 2;
+            int32_t *c2 = (int32_t *)realloc(uJ, (size_t)ucap * sizeof(int32_t));
+            if (c2) uJ = c2;
+            double *v2 = (double *)realloc(uV, (size_t)ucap * sizeof(double));
+            if (v2) uV = v2;
+            if (!c2 || !v2) { st = OR_ERR_OOM; break; }
+        }
+        for (int x = 0; x < m; x++) {
+            uJ[unz] = list[x]; uV[unz] = acc[list[x]]; unz++;
+            if (list[x] != I) ucnt[list[x] + 1]++;   /* mirrored entry in row J */
+        }
+        urp[I + 1] = (int32_t)unz;
+    }
+    if (!st) {
+        /* full rows: mirrored lower entries (increasing I) then the upper part */
+        out->n = nc;
+        out->rp = (int32_t *)malloc(((size_t)nc + 1) * sizeof(int32_t));
+        int64_t tot = 0;
+        for (int I = 0; I < nc; I++) tot += (urp[I + 1] - urp[I]) + ucnt[I + 1];
+        out->ci = (int32_t *)malloc((size_t)(tot > 0 ? tot : 1) * sizeof(int32_t));
+        out->v = (double *)malloc((size_t)(tot > 0 ? tot : 1) * sizeof(double));
+        int32_t *lf = (int32_t *)malloc(((size_t)nc + 1) * sizeof(int32_t));
+        if (!out->rp || !out->ci || !out->v || !lf) { free(lf); csr_free(out); st = OR_ERR_OOM; }
+        else {
+            out->rp[0] = 0;
+            for (int I = 0; I < nc; I++) out->rp[I + 1] = out->rp[I] + ucnt[I + 1] + (urp[I + 1] - urp[I]);
+            for (int I = 0; I < nc; I++) lf[I] = out->rp[I];
+            for (int I = 0; I < nc; I++)
+                for (int32_t q = urp[I]; q < urp[I + 1]; q++) {
+                    int J = uJ[q];
+                    if (J == I) continue;
+                    out->ci[lf[J]] = I; out->v[lf[J]] = uV[q]; lf[J]++;
+                }
+            for (int I = 0; I < nc; I++)
+                for (int32_t q = urp[I]; q < urp[I + 1]; q++) {
+                    out->ci[lf[I]] = uJ[q]; out->v[lf[I]] = uV[q]; lf[I]++;
+                }
+            out->nnz = tot;
+            free(lf);
+        }
+    }
+    free(ucnt); free(uJ); free(uV); free(urp);
+    free(tc); free(ti); free(tv); free(acc); free(mark); free(list); csr_free(&AP);
+    return st;
 }
 
 static int level_finish(level_t *lv) {
@@ -498,8 +728,8 @@ static int level_finish(level_t *lv) {
     return OR_OK;
 }
 
-int or_setup(int n, const int32_t *rp, const int32_t *ci, const double *v,
-             int coarse_max, int n_pass, int max_levels, hier_t **out) {
+int or_setup_ex(int n, const int32_t *rp, const int32_t *ci, const double *v,
+                int coarse_max, int n_pass, int max_levels, int smoothed, hier_t **out) {
     *out = NULL;
     if (n <= 0 || n_pass < 1 || n_pass > OR_MAX_PASS || max_levels < 1 || coarse_max < 1)
         return OR_ERR_ARG;
@@ -508,6 +738,7 @@ int or_setup(int n, const int32_t *rp, const int32_t *ci, const double *v,
     if (st) return st;
     hier_t *h = (hier_t *)calloc(1, sizeof(hier_t));
     if (!h) return OR_ERR_OOM;
+    h->smoothed = smoothed ? 1 : 0;
     level_t *l0 = &h->lev[0];
     int64_t z = rp[n];
     l0->A.n = n; l0->A.nnz = z;
@@ -583,6 +814,20 @@ int or_setup(int n, const int32_t *rp, const int32_t *ci, const double *v,
         lv->p32 = (float *)malloc((size_t)nl * sizeof(float));
         if (!lv->p32) { csr_free(&cur); free(curw); or_free(h); return OR_ERR_OOM; }
         for (int i = 0; i < nl; i++) lv->p32[i] = (float)cp[i];
+        if (h->smoothed) {
+            /* P = (I - omega D^-1 A) P_hat and A_c = P^T A P replace the
+             * tentative product of the passes */
+            csr_t Pm = {0, 0, NULL, NULL, NULL}, Ac = {0, 0, NULL, NULL, NULL};
+            st = smooth_prolongator(&lv->A, cagg, cp, nc, smoothing_omega(&lv->A), &Pm);
+            if (!st) st = rap_explicit(&lv->A, &Pm, nc, &Ac);
+            csr_free(&cur);
+            if (st) { csr_free(&Pm); free(curw); or_free(h); return st; }
+            cur = Ac;
+            lv->P = Pm;
+            lv->P32 = (float *)malloc((size_t)(Pm.nnz > 0 ? Pm.nnz : 1) * sizeof(float));
+            if (!lv->P32) { csr_free(&cur); free(curw); or_free(h); return OR_ERR_OOM; }
+            for (int64_t q = 0; q < Pm.nnz; q++) lv->P32[q] = (float)Pm.v[q];
+        }
         level_t *nx = &h->lev[l + 1];
         nx->A = cur; nx->w = curw;
         h->nlev = l + 2;
@@ -607,6 +852,11 @@ int or_setup(int n, const int32_t *rp, const int32_t *ci, const double *v,
     if (st) { or_free(h); return st; }
     *out = h;
     return OR_OK;
+}
+
+int or_setup(int n, const int32_t *rp, const int32_t *ci, const double *v,
+             int coarse_max, int n_pass, int max_levels, hier_t **out) {
+    return or_setup_ex(n, rp, ci, v, coarse_max, n_pass, max_levels, 0, out);
 }
 
 /* Select the smoother: nu = 0 restores the l1-Jacobi sweep of the setup;
@@ -679,6 +929,28 @@ int or_refresh(hier_t *h, int n, const int32_t *rp, const int32_t *ci, const dou
     memcpy(l0->A.v, v, (size_t)l0->A.nnz * sizeof(double));
     for (int l = 0; l + 1 < h->nlev; l++) {
         level_t *lv = &h->lev[l];
+        if (h->smoothed) {
+            /* P and A_{l+1} = P^T A_l P formed again; both keep their patterns */
+            int nc = h->lev[l + 1].A.n;
+            csr_t Pm = {0, 0, NULL, NULL, NULL}, Ac = {0, 0, NULL, NULL, NULL};
+            st = smooth_prolongator(&lv->A, lv->agg, lv->p, nc, smoothing_omega(&lv->A), &Pm);
+            if (!st) st = rap_explicit(&lv->A, &Pm, nc, &Ac);
+            csr_t *An = &h->lev[l + 1].A;
+            int same = !st && Pm.nnz == lv->P.nnz &&
+                       memcmp(Pm.rp, lv->P.rp, ((size_t)Pm.n + 1) * sizeof(int32_t)) == 0 &&
+                       memcmp(Pm.ci, lv->P.ci, (size_t)Pm.nnz * sizeof(int32_t)) == 0 && Ac.nnz == An->nnz &&
+                       memcmp(Ac.rp, An->rp, ((size_t)Ac.n + 1) * sizeof(int32_t)) == 0 &&
+                       memcmp(Ac.ci, An->ci, (size_t)Ac.nnz * sizeof(int32_t)) == 0;
+            if (same) {
+                memcpy(lv->P.v, Pm.v, (size_t)Pm.nnz * sizeof(double));
+                for (int64_t q = 0; q < Pm.nnz; q++) lv->P32[q] = (float)Pm.v[q];
+                memcpy(An->v, Ac.v, (size_t)Ac.nnz * sizeof(double));
+            }
+            csr_free(&Pm); csr_free(&Ac);
+            if (st) return st;
+            if (!same) return OR_ERR_ARG;
+            continue;
+        }
         csr_t cur = lv->A;            /* borrowed on the first pass */
         double *curw = lv->w;
         int own = 0;
@@ -761,6 +1033,16 @@ int or_pass_agg(const hier_t *h, int l, int ps, int32_t *agg) {
 
 int or_pass_n(const hier_t *h, int l, int ps) { return h->lev[l].pass_n[ps]; }
 
+/* explicit (smoothed) prolongator of level l: nnz, or -1 when tentative */
+int64_t or_level_P_nnz(const hier_t *h, int l) { return h->lev[l].P.rp ? h->lev[l].P.nnz : -1; }
+
+void or_level_P(const hier_t *h, int l, int32_t *rp, int32_t *ci, double *v) {
+    const csr_t *P = &h->lev[l].P;
+    memcpy(rp, P->rp, ((size_t)P->n + 1) * sizeof(int32_t));
+    memcpy(ci, P->ci, (size_t)P->nnz * sizeof(int32_t));
+    memcpy(v, P->v, (size_t)P->nnz * sizeof(double));
+}
+
 void or_coarse_factor(const hier_t *h, double *L) {
     memcpy(L, h->L, (size_t)h->nL * (size_t)h->nL * sizeof(double));
 }
@@ -807,15 +1089,30 @@ static int vcycle64(const hier_t *h, const double *r, double *z) {
         }
         or_spmv(n, lv->A.rp, lv->A.ci, lv->A.v, xl[l], t);
         for (int I = 0; I < nc; I++) bl[l + 1][I] = 0.0;
-        for (int i = 0; i < n; i++)
-            if (lv->agg[i] >= 0) bl[l + 1][lv->agg[i]] += lv->p[i] * (bl[l][i] - t[i]);
+        if (lv->P.rp) {
+            for (int i = 0; i < n; i++) {
+                double res = bl[l][i] - t[i];
+                for (int32_t q = lv->P.rp[i]; q < lv->P.rp[i + 1]; q++) bl[l + 1][lv->P.ci[q]] += lv->P.v[q] * res;
+            }
+        } else {
+            for (int i = 0; i < n; i++)
+                if (lv->agg[i] >= 0) bl[l + 1][lv->agg[i]] += lv->p[i] * (bl[l][i] - t[i]);
+        }
     }
     or_chol_solve(h->nL, h->L, bl[L], xl[L]);
     for (int l = L - 1; l >= 0; l--) {
         const level_t *lv = &h->lev[l];
         int n = lv->A.n;
-        for (int i = 0; i < n; i++)
-            if (lv->agg[i] >= 0) xl[l][i] += lv->p[i] * xl[l + 1][lv->agg[i]];
+        if (lv->P.rp) {
+            for (int i = 0; i < n; i++) {
+                double s = 0.0;
+                for (int32_t q = lv->P.rp[i]; q < lv->P.rp[i + 1]; q++) s += lv->P.v[q] * xl[l + 1][lv->P.ci[q]];
+                xl[l][i] = xl[l][i] + s;
+            }
+        } else {
+            for (int i = 0; i < n; i++)
+                if (lv->agg[i] >= 0) xl[l][i] += lv->p[i] * xl[l + 1][lv->agg[i]];
+        }
         if (h->nu > 0) {
             /* nu backward sweeps (M^T: the symmetric counterpart) */
             int nb = gs_rows(h, n);
@@ -881,8 +1178,15 @@ static int vcycle32(const hier_t *h, const double *r, double *z) {
         }
         spmv32(&lv->A, lv->v32, xl[l], t);
         for (int I = 0; I < nc; I++) bl[l + 1][I] = 0.0f;
-        for (int i = 0; i < n; i++)
-            if (lv->agg[i] >= 0) bl[l + 1][lv->agg[i]] += lv->p32[i] * (bl[l][i] - t[i]);
+        if (lv->P.rp) {
+            for (int i = 0; i < n; i++) {
+                float res = bl[l][i] - t[i];
+                for (int32_t q = lv->P.rp[i]; q < lv->P.rp[i + 1]; q++) bl[l + 1][lv->P.ci[q]] += lv->P32[q] * res;
+            }
+        } else {
+            for (int i = 0; i < n; i++)
+                if (lv->agg[i] >= 0) bl[l + 1][lv->agg[i]] += lv->p32[i] * (bl[l][i] - t[i]);
+        }
     }
     for (int i = 0; i < h->nL; i++) b64[i] = (double)bl[L][i];
     or_chol_solve(h->nL, h->L, b64, x64);
@@ -890,8 +1194,16 @@ static int vcycle32(const hier_t *h, const double *r, double *z) {
     for (int l = L - 1; l >= 0; l--) {
         const level_t *lv = &h->lev[l];
         int n = lv->A.n;
-        for (int i = 0; i < n; i++)
-            if (lv->agg[i] >= 0) xl[l][i] += lv->p32[i] * xl[l + 1][lv->agg[i]];
+        if (lv->P.rp) {
+            for (int i = 0; i < n; i++) {
+                float s = 0.0f;
+                for (int32_t q = lv->P.rp[i]; q < lv->P.rp[i + 1]; q++) s += lv->P32[q] * xl[l + 1][lv->P.ci[q]];
+                xl[l][i] = xl[l][i] + s;
+            }
+        } else {
+            for (int i = 0; i < n; i++)
+                if (lv->agg[i] >= 0) xl[l][i] += lv->p32[i] * xl[l + 1][lv->agg[i]];
+        }
         if (h->nu > 0) {
             int nb = gs_rows(h, n);
             for (int s = 0; s < h->nu; s++) {
