@@ -1312,6 +1312,9 @@ int set_smoother_impl(amg_hier *h, int nu, int nblocks, cudaStream_t s) {
         PCG_LAUNCH_CK();
     }
     PCG_CK(cudaStreamSynchronize(s));
+    // the cluster tail's shared-memory image holds the small levels' D^-1:
+    // form it again from the diagonals now in place (used while nu = 0)
+    PCG_TRY(refresh_smem_tail(h));
     h->gs_nu = nu;
     h->gs_blocks = nu > 0 ? nblocks : 0;
     return AMG_OK;

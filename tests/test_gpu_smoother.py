@@ -113,6 +113,25 @@ def test_refresh_with_gauss_seidel_matches_the_oracle():
     assert np.linalg.norm(xs - ref["x"]) <= X_TOL * np.linalg.norm(ref["x"])
 
 
+def test_back_to_jacobi_after_a_refresh_under_gauss_seidel():
+    """A refresh while Gauss-Seidel is active re-forms the cluster tail's image
+    with the Gauss-Seidel diagonals; returning to the default must re-form it
+    with the l1-Jacobi ones (same bits as a handle refreshed under Jacobi)."""
+    prob = W.make_problem(48, 1.04, seed=19)
+    A2 = W.rescaled(prob.A, seed=20)
+    b = torch.from_numpy(W.spmv(A2, W.normals(21, A2.n))).cuda()
+    a1 = B.AMG.from_csr(prob.A, mode="fcg32")
+    a1.set_smoother(2, 4096)
+    a1.refresh(A2)
+    a1.set_smoother(0)
+    a2 = B.AMG.from_csr(prob.A, mode="fcg32")
+    a2.refresh(A2)
+    r1, x1 = _solve(a1, b)
+    r2, x2 = _solve(a2, b)
+    assert r1.status == r2.status == 0 and r1.iters == r2.iters
+    assert torch.equal(x1, x2)
+
+
 def test_full_size_128_nu4():
     """The paper's nu = 4 on the benchmarked system, 65,536 row blocks per
     level (32 rows per block on level 0)."""
