@@ -122,3 +122,37 @@ def test_refresh_of_2A_equals_a_fresh_smoothed_setup_of_2A():
         if l + 1 < h.nlevels:
             for x, y in zip(h.prolongator(l), fresh.prolongator(l)):
                 assert np.array_equal(x, y)
+
+
+def test_smoothed_prolongator_with_hybrid_gauss_seidel():
+    """Both of the paper's choices at once (smoothed P, nu = 4 hybrid GS): the
+    V-cycle is the dense composition with the explicit P and M = blockdiag(L + D_l1)."""
+    A, _, _ = W.q1_laplacian(7, 1.04)
+    h = O.Hierarchy(A, coarse_max=8, n_pass=2, smoothed=True)
+    nu, nblocks = 4, 5
+    assert h.set_smoother(nu, nblocks) == O.OK
+    L = h.nlevels - 1
+    dense = [_level_dense(h, l) for l in range(L + 1)]
+    B = np.linalg.inv(dense[L])
+    for l in range(L - 1, -1, -1):
+        a = dense[l]
+        n = a.shape[0]
+        nb = max(1, -(-n // nblocks))
+        M = np.zeros_like(a)
+        for lo in range(0, n, nb):
+            hi = min(n, lo + nb)
+            M[lo:hi, lo:hi] = np.tril(a[lo:hi, lo:hi], -1)
+            for i in range(lo, hi):
+                M[i, i] = a[i, i] + np.abs(a[i]).sum() - np.abs(a[i, lo:hi]).sum()
+        P = _dense(h.prolongator(l), n, dense[l + 1].shape[0])
+        I = np.eye(n)
+        pre = np.linalg.matrix_power(I - np.linalg.solve(M, a), nu)
+        post = np.linalg.matrix_power(I - np.linalg.solve(M.T, a), nu)
+        E = post @ (I - P @ B @ P.T @ a) @ pre
+        B = (I - E) @ np.linalg.inv(a)
+    Bo = np.stack([h.vcycle(e) for e in np.eye(A.n)], axis=1)
+    assert np.allclose(Bo, B, rtol=1e-9, atol=1e-11 * np.abs(B).max())
+    prob_b = W.spmv(A, W.normals(3, A.n))
+    res = h.solve(prob_b, rtol=1e-10, mode="pcg64")
+    assert res["status"] == O.OK
+    assert np.linalg.norm(res["x"] - np.linalg.solve(A.to_dense(), prob_b)) <= 1e-8 * np.linalg.norm(res["x"])
