@@ -897,7 +897,10 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
 // gs_nu Gauss-Seidel sweeps on level l: pre-smoothing (forward, from zero,
 // into xpre) or post-smoothing (backward, from xp, into x). Successive sweeps
 // alternate between the target and t (free at both points), arranged so the
-// last one writes the target. Returns the kernels launched.
+// last one writes the target. A level with a two-phase table for the pass
+// (blocks of at most 32 rows) sweeps with k_gs_offsum + k_gs_block (the first
+// pre-smoothing pass with k_gs_block alone); any other with k_gs_sweep.
+// Returns the kernels launched.
 template <typename T>
 int launch_gs(amg_hier *h, int l, bool pre, const T *b, T *target, cudaStream_t s) {
     using P = LP<T>;
