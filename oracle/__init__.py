@@ -23,6 +23,16 @@ OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_NAN, ERR_COARSE = 0, 1, 2, 
 
 _lib = None
 
+
+class _Cfg(C.Structure):
+    """or_cfg_t: hierarchy and coarsest-solver options."""
+    _fields_ = [("coarse_max", C.c_int), ("n_pass", C.c_int), ("max_levels", C.c_int),
+                ("smoothed", C.c_int), ("csolver", C.c_int), ("cb", C.c_int), ("cmaxit", C.c_int),
+                ("ctol", C.c_double)]
+
+
+COARSE = {"auto": 0, "dense": 1, "iter": 2}
+
 _i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
 
@@ -66,6 +76,20 @@ def load():
     lib.or_setup.argtypes = [I, _i32p, _i32p, _f64p, I, I, I, C.POINTER(P)]
     lib.or_setup_ex.restype = I
     lib.or_setup_ex.argtypes = [I, _i32p, _i32p, _f64p, I, I, I, I, C.POINTER(P)]
+    lib.or_setup_cfg.restype = I
+    lib.or_setup_cfg.argtypes = [I, _i32p, _i32p, _f64p, C.POINTER(_Cfg), C.POINTER(P)]
+    lib.or_coarse_kind.restype = I
+    lib.or_coarse_kind.argtypes = [P]
+    lib.or_coarse_ilu_nnz.restype = C.c_int64
+    lib.or_coarse_ilu_nnz.argtypes = [P]
+    lib.or_coarse_ilu.restype = None
+    lib.or_coarse_ilu.argtypes = [P, _i32p, _i32p, _f64p, _i32p]
+    lib.or_coarse_solve.restype = I
+    lib.or_coarse_solve.argtypes = [P, _f64p, _f64p]
+    lib.or_coarse_prec.restype = None
+    lib.or_coarse_prec.argtypes = [P, _f64p, _f64p]
+    lib.or_coarse_stats.restype = None
+    lib.or_coarse_stats.argtypes = [P, C.POINTER(C.c_int64)]
     lib.or_level_P_nnz.restype = C.c_int64
     lib.or_level_P_nnz.argtypes = [P, I]
     lib.or_level_P.restype = None
@@ -182,13 +206,23 @@ def chol_solve(L, b):
 class Hierarchy:
     """Oracle AMG hierarchy (aggregation by matching, tentative prolongator)."""
 
-    def __init__(self, A, coarse_max: int = 200, n_pass: int = 3, max_levels: int = 30, smoothed: bool = False):
+    def __init__(self, A, coarse_max: int = 200, n_pass: int = 3, max_levels: int = 30, smoothed: bool = False,
+                 coarse: str = "dense", coarse_block: int = 32, coarse_tol: float = 1e-3,
+                 coarse_maxit: int = 30):
         """``smoothed``: prolongators P = (I - omega D^-1 A) P_hat (smoothed
-        aggregation, Sec. 3.1) instead of the tentative P_hat."""
+        aggregation, Sec. 3.1) instead of the tentative P_hat.
+
+        ``coarse``: the coarsest solver (Sec. 3.1). "dense": Cholesky (the
+        setup fails above 4096 rows); "iter": flexible CG preconditioned by
+        block-Jacobi with ILU(1) blocks of ``coarse_block`` rows, stopped at
+        ``||r|| <= coarse_tol ||b||`` or after ``coarse_maxit`` iterations;
+        "auto": dense up to 4096 rows, else iterative."""
         lib = load()
         n, rp, ci, v = _csr_args(A)
         h = C.c_void_p()
-        st = lib.or_setup_ex(n, rp, ci, v, coarse_max, n_pass, max_levels, int(smoothed), C.byref(h))
+        cfg = _Cfg(coarse_max, n_pass, max_levels, int(smoothed), COARSE[coarse], coarse_block, coarse_maxit,
+                   coarse_tol)
+        st = lib.or_setup_cfg(n, rp, ci, v, C.byref(cfg), C.byref(h))
         self.status = st
         if st:
             raise RuntimeError(f"oracle setup status {st}")
@@ -273,6 +307,49 @@ class Hierarchy:
         L = np.empty((n, n))
         load().or_coarse_factor(self._h, L)
         return L
+
+    @property
+    def coarse_kind(self) -> str:
+        """The coarsest solver in use: "dense" or "iter"."""
+        return ("dense", "iter")[load().or_coarse_kind(self._h)]
+
+    def coarse_ilu(self):
+        """ILU(1) factors of the coarsest level's blocks as CSR parts plus the
+        position of each row's diagonal (L strictly below it, with a unit
+        diagonal not stored; U from it on)."""
+        lib = load()
+        nz = lib.or_coarse_ilu_nnz(self._h)
+        if nz < 0:
+            return None
+        n, _, _ = self.level_size(self.nlevels - 1)
+        rp = np.empty(n + 1, np.int32)
+        ci = np.empty(max(nz, 1), np.int32)
+        v = np.empty(max(nz, 1))
+        dg = np.empty(max(n, 1), np.int32)
+        lib.or_coarse_ilu(self._h, rp, ci, v, dg)
+        return rp, ci[:nz], v[:nz], dg[:n]
+
+    def coarse_solve(self, b):
+        """The coarsest solver alone: (x, inner iterations)."""
+        n, _, _ = self.level_size(self.nlevels - 1)
+        x = np.empty(n)
+        its = load().or_coarse_solve(self._h, np.ascontiguousarray(b, np.float64), x)
+        if its < 0:
+            raise MemoryError("oracle coarse solve")
+        return x, its
+
+    def coarse_prec(self, r):
+        """The block-Jacobi ILU(1) preconditioner of the coarsest level."""
+        n, _, _ = self.level_size(self.nlevels - 1)
+        z = np.empty(n)
+        load().or_coarse_prec(self._h, np.ascontiguousarray(r, np.float64), z)
+        return z
+
+    def coarse_stats(self):
+        """(calls, inner iterations in total, inner iterations of the last call)"""
+        out = (C.c_int64 * 3)()
+        load().or_coarse_stats(self._h, out)
+        return tuple(int(v) for v in out)
 
     def vcycle(self, r, fp32: bool = False) -> np.ndarray:
         z = np.empty(self.n)

@@ -17,7 +17,8 @@
  *
  * Status codes: 0 ok, 1 bad argument, 2 out of memory, 3 breakdown
  * (rho <= 0 or p'Ap <= 0: not SPD), 4 no convergence within maxit,
- * 5 NaN/Inf met, 8 coarsening stalled above the dense-solve limit.
+ * 5 NaN/Inf met, 8 coarsening stalled above the dense-solve limit (only when
+ * the dense coarsest solver is requested).
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,7 +71,28 @@ typedef struct {
      * level (or_set_smoother) */
     int nu, nblocks;
     int smoothed;       /* 1: P = (I - omega D^-1 A) P_hat on every level */
+    /* coarsest solver: csolver = 0 dense Cholesky (L above), 1 flexible CG
+     * preconditioned by block-Jacobi with ILU(1) blocks of cb rows, stopped
+     * at ||r|| <= ctol ||b|| or after cmaxit iterations */
+    int csolver, cb, cmaxit;
+    double ctol;
+    int32_t *frp, *fci, *fdg;   /* ILU(1) factors of the blocks: row i holds its
+                                   in-block entries of L (unit diagonal not
+                                   stored) and U, columns ascending; fdg[i] is
+                                   the position of u_ii */
+    double *fv;
+    unsigned char *flev;        /* level of fill of each kept entry (0 or 1) */
+    int64_t *cstat;             /* calls, inner iterations in total, last count */
 } hier_t;
+
+/* Options of or_setup_cfg. csolver: 0 = dense when the coarsest level has at
+ * most OR_DENSE_MAX rows, else iterative; 1 = dense (OR_ERR_COARSE above the
+ * limit); 2 = iterative. */
+typedef struct {
+    int coarse_max, n_pass, max_levels, smoothed;
+    int csolver, cb, cmaxit;
+    double ctol;
+} or_cfg_t;
 
 /* ---------------------------------------------------------------- helpers */
 
@@ -460,6 +482,159 @@ void or_chol_solve(int n, const double *L, const double *b, double *x) {
     }
 }
 
+/* ------------------------------------------- iterative coarsest solver
+ * Sec. 3.1, coarsest solver: flexible CG preconditioned by block-Jacobi,
+ * each block solved approximately by an incomplete LU factorization with one
+ * level of fill-in, ILU(1); the iteration stops once the residual has fallen
+ * by three orders of magnitude or after 30 iterations.
+ *
+ * Readings: a block is a contiguous range of cb rows of the coarsest matrix
+ * (the last one ragged), the rows one parallel worker owns, as the paper's
+ * blocks are the rows one process owns; its matrix is A restricted to the
+ * block's rows and columns. ILU(1) is the level-of-fill ILU(p) with p = 1 in
+ * row (IKJ) order: stored entries have level 0; row i is eliminated with the
+ * earlier rows k of its block in increasing k, using only entries (i,k) of
+ * level <= 1: l_ik = a_ik / u_kk, then for every kept upper entry u_kj of
+ * row k, a_ij -= l_ik u_kj and lev_ij = min(lev_ij, lev_ik + lev_kj + 1);
+ * row i keeps its entries of level <= 1. A pivot u_ii that is not a positive
+ * finite number is a breakdown (status 3). The solve starts from x = 0 and
+ * stops when ||r_k|| <= ctol ||b|| (ctol = 1e-3) or after cmaxit (30)
+ * iterations; its recurrence is the FCG(1) of the outer loop. An r.z or
+ * p.Ap that is not positive ends it with the current x.
+ */
+static int ilu1_build(hier_t *h) {
+    const csr_t *a = &h->lev[h->nlev - 1].A;
+    int n = a->n, cb = h->cb;
+    if (cb < 1) return OR_ERR_ARG;
+    int64_t cap = (int64_t)n * (cb < n ? cb : n);
+    free(h->frp); free(h->fci); free(h->fdg); free(h->fv); free(h->flev);
+    h->frp = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    h->fdg = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    h->fci = (int32_t *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(int32_t));
+    h->fv = (double *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(double));
+    h->flev = (unsigned char *)malloc((size_t)(cap > 0 ? cap : 1));
+    double *wv = (double *)malloc((size_t)cb * sizeof(double));
+    int *wl = (int *)malloc((size_t)cb * sizeof(int));
+    if (!h->frp || !h->fdg || !h->fci || !h->fv || !h->flev || !wv || !wl) {
+        free(wv); free(wl);
+        return OR_ERR_OOM;
+    }
+    const int absent = 1 << 20;
+    int32_t cnt = 0;
+    int st = OR_OK;
+    h->frp[0] = 0;
+    for (int s = 0; s < n && !st; s += cb) {
+        int e = s + cb < n ? s + cb : n, m = e - s;
+        for (int i = s; i < e; i++) {
+            for (int j = 0; j < m; j++) { wv[j] = 0.0; wl[j] = absent; }
+            for (int32_t q = a->rp[i]; q < a->rp[i + 1]; q++) {
+                int j = a->ci[q];
+                if (j >= s && j < e) { wv[j - s] = a->v[q]; wl[j - s] = 0; }
+            }
+            for (int k = s; k < i; k++) {
+                if (wl[k - s] > 1) continue;
+                double lik = wv[k - s] / h->fv[h->fdg[k]];
+                wv[k - s] = lik;
+                for (int32_t q = h->fdg[k] + 1; q < h->frp[k + 1]; q++) {
+                    int j = h->fci[q] - s;
+                    wv[j] = wv[j] - lik * h->fv[q];
+                    int nl = wl[k - s] + (int)h->flev[q] + 1;
+                    if (nl < wl[j]) wl[j] = nl;
+                }
+            }
+            for (int j = 0; j < m; j++) {
+                if (wl[j] > 1) continue;
+                if (s + j == i) h->fdg[i] = cnt;
+                h->fci[cnt] = s + j;
+                h->fv[cnt] = wv[j];
+                h->flev[cnt] = (unsigned char)wl[j];
+                cnt++;
+            }
+            h->frp[i + 1] = cnt;
+            double piv = h->fv[h->fdg[i]];
+            if (!(piv > 0.0) || !isfinite(piv)) { st = OR_ERR_BREAKDOWN; break; }
+        }
+    }
+    free(wv); free(wl);
+    return st;
+}
+
+/* z = M^{-1} r, M = blockdiag(L_b U_b): per block, L y = r (forward, the
+ * row's lower entries in increasing column order), then U z = y (backward,
+ * rows from the last, the row's upper entries in decreasing column order,
+ * then the division by u_ii). */
+static void bj_apply(const hier_t *h, const double *r, double *z) {
+    int n = h->lev[h->nlev - 1].A.n, cb = h->cb;
+    for (int s = 0; s < n; s += cb) {
+        int e = s + cb < n ? s + cb : n;
+        for (int i = s; i < e; i++) {
+            double acc = r[i];
+            for (int32_t q = h->frp[i]; q < h->fdg[i]; q++) acc = acc - h->fv[q] * z[h->fci[q]];
+            z[i] = acc;
+        }
+        for (int i = e - 1; i >= s; i--) {
+            double acc = z[i];
+            for (int32_t q = h->frp[i + 1] - 1; q > h->fdg[i]; q--) acc = acc - h->fv[q] * z[h->fci[q]];
+            z[i] = acc / h->fv[h->fdg[i]];
+        }
+    }
+}
+
+/* x = approximate solution of A_L x = b (x0 = 0); returns the iterations
+ * run. ws: 4 n_L doubles. */
+static int coarse_fcg(const hier_t *h, const double *b, double *x, double *ws) {
+    const csr_t *A = &h->lev[h->nlev - 1].A;
+    int n = A->n;
+    double *r = ws, *z = ws + n, *p = ws + 2 * (size_t)n, *q = ws + 3 * (size_t)n;
+    for (int i = 0; i < n; i++) { x[i] = 0.0; r[i] = b[i]; }
+    double bn = sqrt(dot(n, b, b));
+    int its = 0;
+    if (!(bn > 0.0) || !isfinite(bn)) goto out;
+    double pq_old = 0.0;
+    for (int k = 1; k <= h->cmaxit; k++) {
+        bj_apply(h, r, z);
+        double rho = dot(n, r, z);
+        if (!(rho > 0.0) || !isfinite(rho)) break;
+        if (k == 1) {
+            for (int i = 0; i < n; i++) p[i] = z[i];
+        } else {
+            double beta = -dot(n, z, q) / pq_old;
+            for (int i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
+        }
+        or_spmv(n, A->rp, A->ci, A->v, p, q);
+        double pq = dot(n, p, q);
+        if (!(pq > 0.0) || !isfinite(pq)) break;
+        double alpha = rho / pq;
+        for (int i = 0; i < n; i++) x[i] = x[i] + alpha * p[i];
+        for (int i = 0; i < n; i++) r[i] = r[i] - alpha * q[i];
+        pq_old = pq;
+        its = k;
+        if (sqrt(dot(n, r, r)) <= h->ctol * bn) break;
+    }
+out:
+    if (h->cstat) { h->cstat[0] += 1; h->cstat[1] += its; h->cstat[2] = its; }
+    return its;
+}
+
+/* Factor of the coarsest level for the chosen solver: the dense Cholesky
+ * factor, or the blocks' ILU(1) factors. */
+static int coarse_build(hier_t *h) {
+    level_t *lc = &h->lev[h->nlev - 1];
+    int nL = lc->A.n;
+    h->nL = nL;
+    if (h->csolver == 1) return ilu1_build(h);
+    if (nL > OR_DENSE_MAX) return OR_ERR_COARSE;
+    double *Ad = (double *)calloc((size_t)nL * (size_t)nL, sizeof(double));
+    if (!h->L) h->L = (double *)malloc((size_t)nL * (size_t)nL * sizeof(double));
+    if (!Ad || !h->L) { free(Ad); return OR_ERR_OOM; }
+    for (int i = 0; i < nL; i++)
+        for (int32_t k = lc->A.rp[i]; k < lc->A.rp[i + 1]; k++)
+            Ad[(size_t)i * nL + lc->A.ci[k]] = lc->A.v[k];
+    int st = or_chol(nL, Ad, h->L);
+    free(Ad);
+    return st;
+}
+
 /* ------------------------------------------------------------ hierarchy
  * Sec. 3.1: A_{l+1} = P_l^T A_l P_l; aggregates larger than pairs come from
  * multiplying pairwise prolongators (the aggregate size is an input
@@ -485,6 +660,7 @@ void or_free(hier_t *h) {
         for (int k = 0; k < OR_MAX_PASS; k++) free(lv->pass_agg[k]);
     }
     free(h->L);
+    free(h->frp); free(h->fci); free(h->fdg); free(h->fv); free(h->flev); free(h->cstat);
     free(h);
 }
 
@@ -728,10 +904,14 @@ static int level_finish(level_t *lv) {
     return OR_OK;
 }
 
-int or_setup_ex(int n, const int32_t *rp, const int32_t *ci, const double *v,
-                int coarse_max, int n_pass, int max_levels, int smoothed, hier_t **out) {
+int or_setup_cfg(int n, const int32_t *rp, const int32_t *ci, const double *v, const or_cfg_t *cfg,
+                 hier_t **out) {
     *out = NULL;
+    int coarse_max = cfg->coarse_max, n_pass = cfg->n_pass, max_levels = cfg->max_levels;
+    int smoothed = cfg->smoothed;
     if (n <= 0 || n_pass < 1 || n_pass > OR_MAX_PASS || max_levels < 1 || coarse_max < 1)
+        return OR_ERR_ARG;
+    if (cfg->csolver < 0 || cfg->csolver > 2 || cfg->cb < 1 || cfg->cmaxit < 1 || !(cfg->ctol > 0.0))
         return OR_ERR_ARG;
     if (max_levels > OR_MAX_LEVELS) max_levels = OR_MAX_LEVELS;
     int st = csr_check(n, rp, ci, v);
@@ -739,6 +919,9 @@ int or_setup_ex(int n, const int32_t *rp, const int32_t *ci, const double *v,
     hier_t *h = (hier_t *)calloc(1, sizeof(hier_t));
     if (!h) return OR_ERR_OOM;
     h->smoothed = smoothed ? 1 : 0;
+    h->cb = cfg->cb; h->cmaxit = cfg->cmaxit; h->ctol = cfg->ctol;
+    h->cstat = (int64_t *)calloc(3, sizeof(int64_t));
+    if (!h->cstat) { free(h); return OR_ERR_OOM; }
     level_t *l0 = &h->lev[0];
     int64_t z = rp[n];
     l0->A.n = n; l0->A.nnz = z;
@@ -836,22 +1019,19 @@ int or_setup_ex(int n, const int32_t *rp, const int32_t *ci, const double *v,
         st = level_finish(&h->lev[l]);
         if (st) { or_free(h); return st; }
     }
-    /* dense factor of the coarsest level */
-    level_t *lc = &h->lev[h->nlev - 1];
-    int nL = lc->A.n;
-    if (nL > OR_DENSE_MAX) { or_free(h); return OR_ERR_COARSE; }
-    double *Ad = (double *)calloc((size_t)nL * (size_t)nL, sizeof(double));
-    h->L = (double *)malloc((size_t)nL * (size_t)nL * sizeof(double));
-    h->nL = nL;
-    if (!Ad || !h->L) { free(Ad); or_free(h); return OR_ERR_OOM; }
-    for (int i = 0; i < nL; i++)
-        for (int32_t k = lc->A.rp[i]; k < lc->A.rp[i + 1]; k++)
-            Ad[(size_t)i * nL + lc->A.ci[k]] = lc->A.v[k];
-    st = or_chol(nL, Ad, h->L);
-    free(Ad);
+    /* the coarsest level's solver and its factor */
+    int nL = h->lev[h->nlev - 1].A.n;
+    h->csolver = cfg->csolver == 2 || (cfg->csolver == 0 && nL > OR_DENSE_MAX) ? 1 : 0;
+    st = coarse_build(h);
     if (st) { or_free(h); return st; }
     *out = h;
     return OR_OK;
+}
+
+int or_setup_ex(int n, const int32_t *rp, const int32_t *ci, const double *v,
+                int coarse_max, int n_pass, int max_levels, int smoothed, hier_t **out) {
+    or_cfg_t cfg = {coarse_max, n_pass, max_levels, smoothed, 1, 32, 30, 1e-3};
+    return or_setup_cfg(n, rp, ci, v, &cfg, out);
 }
 
 int or_setup(int n, const int32_t *rp, const int32_t *ci, const double *v,
@@ -986,16 +1166,7 @@ int or_refresh(hier_t *h, int n, const int32_t *rp, const int32_t *ci, const dou
         if (st) return st;
         if (h->nu > 0) hybrid_l1(&lv->A, gs_rows(h, lv->A.n), lv->dinv, lv->dinv32);
     }
-    level_t *lc = &h->lev[h->nlev - 1];
-    int nL = lc->A.n;
-    double *Ad = (double *)calloc((size_t)nL * (size_t)nL, sizeof(double));
-    if (!Ad) return OR_ERR_OOM;
-    for (int i = 0; i < nL; i++)
-        for (int32_t k = lc->A.rp[i]; k < lc->A.rp[i + 1]; k++)
-            Ad[(size_t)i * nL + lc->A.ci[k]] = lc->A.v[k];
-    st = or_chol(nL, Ad, h->L);
-    free(Ad);
-    return st;
+    return coarse_build(h);
 }
 
 /* ------------------------------------------------------------ accessors */
@@ -1045,6 +1216,43 @@ void or_level_P(const hier_t *h, int l, int32_t *rp, int32_t *ci, double *v) {
 
 void or_coarse_factor(const hier_t *h, double *L) {
     memcpy(L, h->L, (size_t)h->nL * (size_t)h->nL * sizeof(double));
+}
+
+/* coarsest solver: 0 dense, 1 iterative (block-Jacobi ILU(1) + FCG) */
+int or_coarse_kind(const hier_t *h) { return h->csolver; }
+
+/* stored entries of the ILU(1) factors (-1 with the dense solver) */
+int64_t or_coarse_ilu_nnz(const hier_t *h) { return h->csolver ? (int64_t)h->frp[h->nL] : -1; }
+
+void or_coarse_ilu(const hier_t *h, int32_t *rp, int32_t *ci, double *v, int32_t *dg) {
+    int n = h->nL;
+    memcpy(rp, h->frp, ((size_t)n + 1) * sizeof(int32_t));
+    memcpy(ci, h->fci, (size_t)h->frp[n] * sizeof(int32_t));
+    memcpy(v, h->fv, (size_t)h->frp[n] * sizeof(double));
+    memcpy(dg, h->fdg, (size_t)n * sizeof(int32_t));
+}
+
+/* The coarsest solver alone: x ~ A_L^{-1} b. Returns the inner iterations
+ * (0 with the dense solver), or -2 when out of memory. */
+int or_coarse_solve(const hier_t *h, const double *b, double *x) {
+    if (!h->csolver) {
+        or_chol_solve(h->nL, h->L, b, x);
+        return 0;
+    }
+    double *ws = (double *)malloc(4 * (size_t)(h->nL > 0 ? h->nL : 1) * sizeof(double));
+    if (!ws) return -2;
+    int its = coarse_fcg(h, b, x, ws);
+    free(ws);
+    return its;
+}
+
+/* z = M^{-1} r with the block-Jacobi ILU(1) preconditioner alone */
+void or_coarse_prec(const hier_t *h, const double *r, double *z) { bj_apply(h, r, z); }
+
+/* calls of the iterative coarsest solver, inner iterations in total, and the
+ * count of the last call */
+void or_coarse_stats(const hier_t *h, int64_t *out) {
+    out[0] = h->cstat[0]; out[1] = h->cstat[1]; out[2] = h->cstat[2];
 }
 
 /* -------------------------------------------------------------- V-cycle
@@ -1099,7 +1307,14 @@ static int vcycle64(const hier_t *h, const double *r, double *z) {
                 if (lv->agg[i] >= 0) bl[l + 1][lv->agg[i]] += lv->p[i] * (bl[l][i] - t[i]);
         }
     }
-    or_chol_solve(h->nL, h->L, bl[L], xl[L]);
+    if (h->csolver) {
+        double *ws = (double *)malloc(4 * (size_t)(h->nL > 0 ? h->nL : 1) * sizeof(double));
+        if (!ws) { st = OR_ERR_OOM; goto done; }
+        coarse_fcg(h, bl[L], xl[L], ws);
+        free(ws);
+    } else {
+        or_chol_solve(h->nL, h->L, bl[L], xl[L]);
+    }
     for (int l = L - 1; l >= 0; l--) {
         const level_t *lv = &h->lev[l];
         int n = lv->A.n;
@@ -1189,7 +1404,14 @@ static int vcycle32(const hier_t *h, const double *r, double *z) {
         }
     }
     for (int i = 0; i < h->nL; i++) b64[i] = (double)bl[L][i];
-    or_chol_solve(h->nL, h->L, b64, x64);
+    if (h->csolver) {
+        double *ws = (double *)malloc(4 * (size_t)(h->nL > 0 ? h->nL : 1) * sizeof(double));
+        if (!ws) { st = OR_ERR_OOM; goto done; }
+        coarse_fcg(h, b64, x64, ws);
+        free(ws);
+    } else {
+        or_chol_solve(h->nL, h->L, b64, x64);
+    }
     for (int i = 0; i < h->nL; i++) xl[L][i] = (float)x64[i];
     for (int l = L - 1; l >= 0; l--) {
         const level_t *lv = &h->lev[l];
@@ -1236,6 +1458,8 @@ int or_vcycle(const hier_t *h, const double *r, double *z, int fp32) {
  *         V-cycle: beta = -(z_k . q_{k-1}) / (p_{k-1} . q_{k-1}), where
  *         q = A p (Notay's truncated flexible CG; equal to the Polak-Ribiere
  *         form z_k.(r_k - r_{k-1}) / rho_{k-1} in exact arithmetic).
+ * With the iterative coarsest solver the V-cycle is not a fixed operator,
+ * and mode 0 uses the FCG(1) beta too (with the float64 V-cycle).
  * Both: rho_k = r_k . z_k, alpha = rho_k / (p_k . q_k).
  * Readings: "relative residual" is ||r_k|| / ||b||; when the recursive
  * residual meets rtol the true residual b - A x is formed and must meet it
@@ -1270,6 +1494,9 @@ int or_solve(const hier_t *h, const double *b, double *x, double rtol, int maxit
     if (!isfinite(rn)) { st = OR_ERR_NAN; goto done; }
     if (rn / bn <= rtol) goto done;
     int restart = 1;
+    /* an iterative coarsest solve makes the V-cycle vary from one application
+     * to the next, so the flexible recurrence is used in both precisions */
+    int flexible = mode == 1 || h->csolver;
     double rho_old = 0.0, pq_old = 0.0;
     for (int k = 1; k <= maxit; k++) {
         st = or_vcycle(h, r, z, mode == 1);
@@ -1282,7 +1509,7 @@ int or_solve(const hier_t *h, const double *b, double *x, double rtol, int maxit
             for (int i = 0; i < n; i++) p[i] = z[i];
             restart = 0;
         } else {
-            double beta = mode == 1 ? -dot(n, z, q) / pq_old : rho / rho_old;
+            double beta = flexible ? -dot(n, z, q) / pq_old : rho / rho_old;
             for (int i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
         }
         or_spmv(n, A->rp, A->ci, A->v, p, q);
