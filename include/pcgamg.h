@@ -13,9 +13,12 @@
  * the Krylov driver through a single call.
  *
  * Variant implemented (fixed by the library, not by the paper): l1-Jacobi
- * smoothing, one pre- and one post-sweep (M = diag(sum_j |a_ij|)); the
- * tentative prolongator without the smoothing step; a dense float64
- * direct solve on the coarsest level.
+ * smoothing, one pre- and one post-sweep (M = diag(sum_j |a_ij|)) by default
+ * (the paper's hybrid Gauss-Seidel on request, amg_set_smoother); the
+ * tentative prolongator without the smoothing step; on the coarsest level a
+ * dense float64 direct solve up to 4096 rows, and above that (or on request)
+ * the paper's own coarsest solver, flexible CG preconditioned by
+ * block-Jacobi with ILU(1) blocks.
  *
  * Conventions for every entry point:
  *  - All functions return an int status (AMG_OK = 0 or an AMG_ERR_* code);
@@ -50,8 +53,22 @@ extern "C" {
 #define AMG_ERR_NAN 5       /* NaN or Inf in the iteration */
 #define AMG_ERR_CUDA 6      /* a CUDA runtime call failed */
 #define AMG_ERR_TIMEOUT 7   /* reserved: no kernel waits on another, no call returns it */
-#define AMG_ERR_COARSE 8    /* coarsening stalled with more than 4096 rows left */
+#define AMG_ERR_COARSE 8    /* the dense coarsest solve was asked for (or a single level
+                               was left) with more than 4096 rows */
 #define AMG_ERR_BUSY 9      /* serving: the request queue is full */
+
+/* Coarsest solver (Sec. 3.1). AUTO: the dense direct solve when the coarsest
+ * level has at most 4096 rows, else the iterative one. DENSE: the dense
+ * direct solve (AMG_ERR_COARSE above 4096 rows). ITER: flexible CG
+ * preconditioned by block-Jacobi over blocks of 32 consecutive rows, each
+ * block solved by its ILU(1) factorization (level-of-fill 1), started from
+ * x = 0 and stopped when ||r|| <= coarse_tol ||b|| or after coarse_maxit
+ * iterations (the paper: a reduction of three orders of magnitude or 30
+ * iterations). With ITER in use the V-cycle is no longer a fixed linear
+ * operator, so both modes run the flexible FCG(1) recurrence. */
+#define AMG_COARSE_AUTO 0
+#define AMG_COARSE_DENSE 1
+#define AMG_COARSE_ITER 2
 
 /* Precision of the V-cycle (Sec. 5 uses flexible CG around the preconditioner). */
 #define AMG_MODE_PCG64 0    /* float64 V-cycle, plain PCG */
@@ -82,6 +99,11 @@ typedef struct {
     int max_levels;   /* at most this many levels, coarsest included (30) */
     int mode;         /* AMG_MODE_PCG64 or AMG_MODE_FCG32 for pcg_solve (PCG64) */
     size_t hbm_budget;/* bytes the handle may allocate; 0 = no limit */
+    int coarse_solver;/* AMG_COARSE_AUTO, _DENSE or _ITER (AUTO) */
+    int coarse_maxit; /* iterative coarsest solve: at most this many iterations, 1..1000
+                         (30; 0 = 30) */
+    double coarse_tol;/* iterative coarsest solve: stop at ||r|| <= coarse_tol ||b||, in
+                         [0, 1) (1e-3; 0 = 1e-3) */
 } amg_params;
 
 /* Fill p with the defaults listed above. */
@@ -99,10 +121,13 @@ int amg_set_allocator(amg_alloc_fn alloc, amg_free_fn dealloc, void *ctx);
  * (locally-dominant, equal to the greedy matching under a strict total
  * order), aggregates and tentative prolongator weights, pairwise Galerkin
  * products P^T A P, sliced-ELL copies in float64 and float32, and the dense
- * coarsest inverse. The level sizes are read back once per pass.
+ * coarsest inverse, or the ILU(1) factors of the coarsest level's blocks and
+ * their dense inverses (iterative coarsest solve). The level sizes are read
+ * back once per pass.
  * A is copied; the caller may free it after the call returns.
- * Errors: AMG_ERR_ARG (bad CSR), AMG_ERR_OOM, AMG_ERR_BREAKDOWN (coarsest
- * not SPD), AMG_ERR_COARSE, AMG_ERR_CUDA. *out is NULL on error. */
+ * Errors: AMG_ERR_ARG (bad CSR or parameters; ITER with a single level),
+ * AMG_ERR_OOM, AMG_ERR_BREAKDOWN (coarsest not SPD, or an ILU(1) pivot that
+ * is not positive), AMG_ERR_COARSE, AMG_ERR_CUDA. *out is NULL on error. */
 int amg_setup(const amg_csr *A, const amg_params *p, void *stream, amg_handle *out);
 
 /* Partial reuse of the hierarchy (Sec. 4: when the mesh topology stays and
@@ -406,6 +431,28 @@ int64_t amg_launch_count(amg_handle h);
  * the caller. Calls no cudaMalloc, cudaFree or allocating library routine. */
 int amg_residual_noalloc(amg_handle h, const double *b, const double *x, double *r, double *norms,
                          void *stream);
+
+/* Coarsest solver of h: *kind = AMG_COARSE_DENSE or AMG_COARSE_ITER (the
+ * one in use), *rows = rows of the coarsest level, *blocks = its 32-row
+ * ILU(1) blocks (0 for the dense solve). Any pointer may be NULL. */
+int amg_coarse_info(amg_handle h, int *kind, int *rows, int *blocks);
+
+/* ILU(1) factors of the coarsest level's blocks (iterative coarsest solve;
+ * AMG_ERR_ARG otherwise), copied to the host buffer F of blocks * 1024
+ * doubles: block b's local row i, column j at F[b*1024 + 32 i + j]; L
+ * strictly below the diagonal (unit diagonal not stored), U on and above;
+ * 0 outside the kept level-1 pattern and on rows past the last row. The
+ * factorization is the level-of-fill ILU(1) in row order with every
+ * operation rounded on its own, so equal inputs give these bits on any
+ * device. */
+int amg_coarse_factors(amg_handle h, double *F);
+
+/* The iterative coarsest solve alone (AMG_ERR_ARG when h uses the dense
+ * one): x ~ A_L^{-1} b for the coarsest matrix A_L, from x = 0, with h's
+ * coarse_tol and coarse_maxit. b, x: n_L values, host or device. *iters
+ * (may be NULL): iterations run. Synchronises stream; must not overlap a
+ * solve on h. */
+int amg_coarse_solve(amg_handle h, const double *b, double *x, int *iters, void *stream);
 
 /* Release every device allocation of the handle (NULL is ignored). */
 void amg_destroy(amg_handle h);

@@ -19,6 +19,8 @@ from . import build as _build
 OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_NAN, ERR_CUDA, ERR_TIMEOUT, ERR_COARSE, ERR_BUSY = range(10)
 MODE_PCG64, MODE_FCG32 = 0, 1
 _MODES = {"pcg64": MODE_PCG64, "fcg32": MODE_FCG32}
+COARSE_AUTO, COARSE_DENSE, COARSE_ITER = 0, 1, 2
+_COARSE = {"auto": COARSE_AUTO, "dense": COARSE_DENSE, "iter": COARSE_ITER}
 
 # Every symbol the header declares (checked by the CPU tests).
 EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode", "pcg_solve",
@@ -28,7 +30,8 @@ EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode
            "amg_batch_create", "pcg_solve_batch", "amg_batch_destroy", "amg_server_default_params",
            "amg_serve_plan", "amg_server_create", "amg_server_mesh_info", "amg_server_info", "amg_server_submit",
            "amg_server_progress", "amg_server_result", "amg_server_destroy", "amg_autotune", "amg_level_shape",
-           "amg_set_level_shape", "amg_profile_levels", "amg_refresh", "amg_refresh_time", "amg_set_smoother")
+           "amg_set_level_shape", "amg_profile_levels", "amg_refresh", "amg_refresh_time", "amg_set_smoother",
+           "amg_coarse_info", "amg_coarse_factors", "amg_coarse_solve")
 
 
 class AmgCsr(C.Structure):
@@ -38,7 +41,8 @@ class AmgCsr(C.Structure):
 
 class AmgParams(C.Structure):
     _fields_ = [("coarse_max", C.c_int), ("n_pass", C.c_int), ("max_levels", C.c_int), ("mode", C.c_int),
-                ("hbm_budget", C.c_size_t)]
+                ("hbm_budget", C.c_size_t), ("coarse_solver", C.c_int), ("coarse_maxit", C.c_int),
+                ("coarse_tol", C.c_double)]
 
 
 class ServerParams(C.Structure):
@@ -93,6 +97,12 @@ def load(build_if_missing: bool = True):
     lib.amg_refresh_time.restype = I
     lib.amg_set_smoother.argtypes = [P, I, I, P]
     lib.amg_set_smoother.restype = I
+    lib.amg_coarse_info.argtypes = [P, C.POINTER(I), C.POINTER(I), C.POINTER(I)]
+    lib.amg_coarse_info.restype = I
+    lib.amg_coarse_factors.argtypes = [P, P]
+    lib.amg_coarse_factors.restype = I
+    lib.amg_coarse_solve.argtypes = [P, P, P, C.POINTER(I), P]
+    lib.amg_coarse_solve.restype = I
     lib.amg_profile.argtypes = [P, I]
     lib.amg_profile.restype = I
     lib.amg_profile_read.argtypes = [P, P, P, I]
@@ -231,7 +241,8 @@ class AMG:
     """A resident AMG hierarchy (``amg_setup``) and its solves (``pcg_solve``)."""
 
     def __init__(self, row_ptr, col, val, n: int | None = None, coarse_max: int = 200, n_pass: int = 2,
-                 max_levels: int = 30, mode: str = "pcg64", hbm_budget: int = 0, stream=None):
+                 max_levels: int = 30, mode: str = "pcg64", hbm_budget: int = 0, stream=None,
+                 coarse: str = "auto", coarse_maxit: int = 30, coarse_tol: float = 1e-3):
         lib = load()
         rp, rp_dev = _ptr(row_ptr, np.int32)
         ci, ci_dev = _ptr(col, np.int32)
@@ -245,6 +256,7 @@ class AMG:
         lib.amg_default_params(C.byref(prm))
         prm.coarse_max, prm.n_pass, prm.max_levels = coarse_max, n_pass, max_levels
         prm.mode, prm.hbm_budget = _MODES[mode], hbm_budget
+        prm.coarse_solver, prm.coarse_maxit, prm.coarse_tol = _COARSE[coarse], coarse_maxit, coarse_tol
         h = C.c_void_p()
         st = lib.amg_setup(C.byref(csr), C.byref(prm), _stream_ptr(stream), C.byref(h))
         if st:
@@ -406,6 +418,36 @@ class AMG:
         if st:
             raise AmgError(st, last_error())
         return float(norms[0]), float(norms[1])
+
+    def coarse_info(self) -> dict:
+        """``amg_coarse_info``: the coarsest solver in use ("dense"/"iter"),
+        its rows and its ILU(1) blocks."""
+        k, r, b = C.c_int(), C.c_int(), C.c_int()
+        st = load().amg_coarse_info(self._h, C.byref(k), C.byref(r), C.byref(b))
+        if st:
+            raise AmgError(st, last_error())
+        return {"kind": "iter" if k.value == COARSE_ITER else "dense", "rows": r.value, "blocks": b.value}
+
+    def coarse_factors(self) -> np.ndarray:
+        """``amg_coarse_factors``: (blocks, 32, 32) ILU(1) factors, L below
+        the diagonal (unit diagonal implied), U on and above."""
+        nb = self.coarse_info()["blocks"]
+        F = np.empty((nb, 32, 32))
+        st = load().amg_coarse_factors(self._h, F.ctypes.data)
+        if st:
+            raise AmgError(st, last_error())
+        return F
+
+    def coarse_solve(self, b, x, stream=None) -> int:
+        """``amg_coarse_solve``: the iterative coarsest solve alone; returns
+        the iterations run (x written in place)."""
+        bp, _ = _ptr(b, np.float64)
+        xp, _ = _ptr(x, np.float64)
+        it = C.c_int(0)
+        st = load().amg_coarse_solve(self._h, bp, xp, C.byref(it), _stream_ptr(stream))
+        if st:
+            raise AmgError(st, last_error())
+        return it.value
 
     def setup_times(self):
         ms = np.zeros(4)

@@ -176,6 +176,7 @@ int pcg_solve_batch(amg_batch b, const double *const *B, double *const *X, doubl
         c0.rtol = rtol;
         c0.maxit = maxit;
         c0.mode = h->mode;
+        c0.flex = h->coarse_iter;
         c0.restart = 1;
         *h->ctl_host = c0;
         PCG_CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));

@@ -96,6 +96,9 @@ void amg_default_params(amg_params *p) {
     p->max_levels = 30;
     p->mode = AMG_MODE_PCG64;
     p->hbm_budget = 0;
+    p->coarse_solver = AMG_COARSE_AUTO;
+    p->coarse_maxit = 30;
+    p->coarse_tol = 1e-3;
 }
 
 int amg_set_allocator(amg_alloc_fn alloc, amg_free_fn dealloc, void *ctx) {

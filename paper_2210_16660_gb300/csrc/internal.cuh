@@ -16,6 +16,7 @@ namespace pcgamg {
 constexpr int kSlice = 32;        // sliced-ELL slice height (one warp)
 constexpr int kBlock = 256;       // threads per block of the streaming kernels
 constexpr int kDenseMax = 4096;   // largest coarsest level solved densely
+constexpr int kCoarseBlock = 32;  // rows per block-Jacobi block of the iterative coarsest solve
 constexpr int kMaxPass = 8;
 
 // ------------------------------------------------------------------ errors
@@ -166,12 +167,41 @@ struct Ctl {
     int iter;            // V-cycles applied
     int maxit;
     int mode;
+    int flex;            // FCG(1) beta in either mode (iterative coarsest solve)
     int restart;         // next direction is p = z
     int check;           // recursive residual met rtol: form the true one
     int done;            // 1 converged, 2 error
     int status;          // AMG_* code once done
     int bodies;          // executions of the graph's loop body (2 iterations each)
     unsigned int counter[8];  // last-block-done counters of the reducing kernels
+};
+
+// Iterative coarsest solve (flexible CG + block-Jacobi with ILU(1) blocks of
+// kCoarseBlock rows): per-block dense data built by setup / refresh.
+struct CoarseIter {
+    int nb = 0;               // blocks (the last one may be ragged)
+    double *F = nullptr;      // ILU(1) factors, 32 x 32 per block, row-major: L strictly below the
+                              // diagonal (unit diagonal implied), U on and above; 0 outside the kept
+                              // pattern and on rows past n_L
+    double *Minv = nullptr;   // (L_b U_b)^{-1}, k-major: Minv[b*1024 + 32k + i] = (M_b^{-1})_{ik};
+                              // identity on rows past n_L
+    int *zero = nullptr;      // a device int holding 0 ("outer solve running") for amg_coarse_solve
+};
+
+// Device state of one iterative coarsest solve over K <= 32 columns.
+struct CCtl {
+    double bn[32], rho[32], pq[32], alpha[32], beta[32];
+    int active[32], its[32];
+    int any;                  // some column still iterating
+    unsigned counter[2];      // last-block tickets
+};
+
+// Work vectors of the iterative coarsest solve: (32 nb) x K row-major.
+struct CoarseWS {
+    int K = 0, grid = 0;
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+    double *partials = nullptr;
+    CCtl *ctl = nullptr;
 };
 
 // One level of the fused small-level tail of the V-cycle (device copy).
@@ -182,6 +212,7 @@ struct CtlM {
     int iter[32], active[32], restart[32], check[32], status[32];
     int pending[32];     // column awaits its first residual (new right-hand side)
     int k, K, maxit, mode, iter_all, any_check, done, bodies;
+    int flex;            // FCG(1) beta in either mode (iterative coarsest solve)
     unsigned int counter[8];
 };
 
@@ -197,6 +228,8 @@ struct MultiWS {
     float *r32 = nullptr;
     std::vector<MultiLevel> lev;
     double *bL = nullptr;
+    CoarseWS cws;                          // iterative coarsest solve (when the hierarchy uses it)
+    int flex = 0;                          // the hierarchy's V-cycle is flexible (iterative coarsest solve)
     double *partials = nullptr;
     CtlM *ctl = nullptr;
     CtlM *ctl_host = nullptr;
@@ -224,7 +257,13 @@ struct amg_hier {
     pcgamg::Mem mem;
     std::vector<pcgamg::Level> lev;
     int nL = 0;
-    double *Ainv = nullptr;   // inverse of the coarsest matrix, row-major
+    double *Ainv = nullptr;   // inverse of the coarsest matrix, row-major (dense coarsest solve)
+    // iterative coarsest solve (Sec. 3.1: FCG + block-Jacobi ILU(1)), used
+    // when coarse_iter = 1; the V-cycle is then not a fixed operator and
+    // both modes run the flexible FCG(1) recurrence
+    int coarse_iter = 0;
+    pcgamg::CoarseIter cit;
+    pcgamg::CoarseWS cws;
     double *bL = nullptr;     // coarsest right-hand side in float64
     // Krylov workspace (level-0 length)
     double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr, *p = nullptr;
@@ -321,4 +360,12 @@ int mws_iterate(amg_hier *h, MultiWS &W, int mode, int iterations, cudaStream_t 
 int capture_solve_prefix(amg_hier *h, int mode, cudaStream_t cs, PendingBody *pb, int *prefix_k);
 int capture_solve_body(const PendingBody &pb, cudaStream_t s, int *body_k);
 int ensure_hist(amg_hier *h, int maxit);
+// iterative coarsest solve (csrc/coarse.cu)
+int coarse_iter_build(amg_hier *h, cudaStream_t s);
+int cws_alloc(amg_hier *h, Mem &M, CoarseWS &W, int K);
+void cws_free(Mem &M, CoarseWS &W);
+int coarse_iter_launches(const amg_hier *h);
+template <typename TO>
+int launch_coarse_iter(amg_hier *h, CoarseWS &W, const double *bL, TO *xL, const int *outer_done,
+                       const int *outer_live, cudaStream_t s);
 }  // namespace pcgamg

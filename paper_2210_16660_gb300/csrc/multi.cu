@@ -383,7 +383,8 @@ __global__ void __launch_bounds__(kMB) k_post_m(int n, const int32_t *__restrict
                     ctl->rho[c] = rho;
                     double beta = 0.0;
                     if (!ctl->restart[c])
-                        beta = ctl->mode == AMG_MODE_FCG32 ? -zqc / ctl->pq_old[c] : rho / ctl->rho_old[c];
+                        beta = ctl->mode == AMG_MODE_FCG32 || ctl->flex ? -zqc / ctl->pq_old[c]
+                                                                        : rho / ctl->rho_old[c];
                     ctl->beta[c] = beta;
                 }
             }
@@ -729,8 +730,11 @@ int launch_vcycle_m(amg_hier *h, MultiWS &W, cudaStream_t s) {
                 lv.nc, lv.rptr, lv.ridx, P::t(mv), P::b(W.lev[l + 1]), P::dinv(lev[l + 1]), P::xpre(W.lev[l + 1]),
                 ctl);
     }
-    k_coarse_m<T, K><<<grid_of((int64_t)h->nL * (K / 2) * 32), kMB, 0, s>>>(h->nL, h->Ainv, W.bL, P::x(W.lev[L]),
-                                                                            ctl);
+    if (h->coarse_iter)
+        PCG_TRY(launch_coarse_iter<T>(h, W.cws, W.bL, P::x(W.lev[L]), &ctl->done, ctl->active, s));
+    else
+        k_coarse_m<T, K><<<grid_of((int64_t)h->nL * (K / 2) * 32), kMB, 0, s>>>(h->nL, h->Ainv, W.bL,
+                                                                                P::x(W.lev[L]), ctl);
     for (int l = L - 1; l >= 1; l--) {
         Level &lv = lev[l];
         MultiLevel &mv = W.lev[l];
@@ -756,6 +760,7 @@ int launch_iteration_m(amg_hier *h, MultiWS &W, int mode, cudaStream_t s) {
     MultiLevel &m0 = W.lev[0];
     int n = l0.A.n;
     if (mode == AMG_MODE_FCG32) PCG_TRY((launch_vcycle_m<float, true, K>(h, W, s)));
+    else if (h->coarse_iter) PCG_TRY((launch_vcycle_m<double, true, K>(h, W, s)));  // flexible: FCG(1) beta
     else PCG_TRY((launch_vcycle_m<double, false, K>(h, W, s)));
     k_axpy_m<K><<<W.grid, kMB, 0, s>>>(n, W.z, W.p, W.ctl);
     WITH_COLS_M(l0.S, (k_spmm_m<IDX, K><<<W.grid, kMB, 0, s>>>(n, l0.S.sptr, cols, l0.S.v64, W.p, W.q, W.partials,
@@ -917,6 +922,7 @@ int solve_multi_k(amg_hier *h, int k, const double *B, double *X, double rtol, i
     c0.rtol = rtol;
     c0.maxit = maxit;
     c0.mode = h->mode;
+    c0.flex = h->coarse_iter;
     c0.k = k;
     c0.K = K;
     for (int q = 0; q < K; q++) c0.pending[q] = 1;
@@ -1003,6 +1009,8 @@ int mws_alloc(amg_hier *h, Mem &M, MultiWS &W, int K, int hist_cap, int which) {
         }
     }
     PCG_TRY(alloc(M, &W.bL, (int64_t)h->nL * K));
+    W.flex = h->coarse_iter;
+    if (h->coarse_iter) PCG_TRY(cws_alloc(h, M, W.cws, K));
     int sms = 0;
     PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     int64_t want = (nk + kMB - 1) / kMB;
@@ -1052,6 +1060,7 @@ void mws_free(Mem &M, MultiWS &W) {
     }
     W.lev.clear();
     release(M, W.bL);
+    cws_free(M, W.cws);
     release(M, W.partials);
     release(M, W.ctl);
     release(M, W.hist);
@@ -1108,6 +1117,7 @@ int mws_reset(MultiWS &W, int mode, double rtol, int maxit, cudaStream_t s) {
     c0.rtol = rtol;
     c0.maxit = maxit;
     c0.mode = mode;
+    c0.flex = W.flex;
     c0.k = W.K;
     c0.K = W.K;
     c0.done = 1;

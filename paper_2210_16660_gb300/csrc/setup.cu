@@ -919,10 +919,15 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
         return AMG_ERR_ARG;
     }
     if (prm->n_pass < 1 || prm->n_pass > kMaxPass || prm->coarse_max < 1 || prm->max_levels < 1 ||
-        (prm->mode != AMG_MODE_PCG64 && prm->mode != AMG_MODE_FCG32)) {
+        (prm->mode != AMG_MODE_PCG64 && prm->mode != AMG_MODE_FCG32) || prm->coarse_solver < AMG_COARSE_AUTO ||
+        prm->coarse_solver > AMG_COARSE_ITER || prm->coarse_maxit < 0 || prm->coarse_maxit > 1000 ||
+        !(prm->coarse_tol >= 0.0 && prm->coarse_tol < 1.0)) {
         set_error("amg_setup: bad parameters");
         return AMG_ERR_ARG;
     }
+    // 0 selects the defaults of the iterative coarsest solve
+    if (h->prm.coarse_maxit == 0) h->prm.coarse_maxit = 30;
+    if (h->prm.coarse_tol == 0.0) h->prm.coarse_tol = 1e-3;
     int n = (int)A->n;
     int64_t nnz = A->nnz;
     h->lev.reserve((size_t)prm->max_levels + 1);
@@ -1015,18 +1020,39 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
     int L = (int)h->lev.size() - 1;
     for (int l = 0; l <= L; l++) PCG_TRY(finish_level(h, h->lev[l], l == L, s));
 
-    // dense inverse of the coarsest matrix
+    // coarsest solver: dense inverse up to kDenseMax rows (AUTO), else the
+    // iterative FCG + block-Jacobi ILU(1) solve of Sec. 3.1
     Level &lc = h->lev[L];
     int nL = lc.A.n;
-    if (nL > kDenseMax) {
+    int cs = prm->coarse_solver;
+    h->coarse_iter = cs == AMG_COARSE_ITER || (cs == AMG_COARSE_AUTO && nL > kDenseMax) ? 1 : 0;
+    if (h->coarse_iter && L == 0) {
+        if (cs == AMG_COARSE_ITER) {
+            set_error("amg_setup: the iterative coarsest solve needs at least two levels (lower coarse_max)");
+            return AMG_ERR_ARG;
+        }
+        set_error("amg_setup: single level of %d rows above the dense limit %d (lower coarse_max)", nL, kDenseMax);
+        return AMG_ERR_COARSE;
+    }
+    if (!h->coarse_iter && nL > kDenseMax) {
         set_error("amg_setup: coarsening stalled at %d rows (dense limit %d)", nL, kDenseMax);
         return AMG_ERR_COARSE;
     }
     h->nL = nL;
+    PCG_TRY(alloc(M, &h->bL, nL));
+    if (h->coarse_iter) {
+        PCG_TRY(coarse_iter_build(h, s));
+        PCG_TRY(alloc_solve_workspace(h));
+        PCG_CK(cudaStreamSynchronize(s));
+        h->setup_ms[0] = now_ms() - t_begin;
+        h->setup_ms[1] = t_match;
+        h->setup_ms[2] = t_rap;
+        h->setup_ms[3] = h->setup_ms[0] - t_match - t_rap;
+        return AMG_OK;
+    }
     double *ad = nullptr;
     PCG_TRY(alloc(M, &ad, (size_t)nL * nL));
     PCG_TRY(alloc(M, &h->Ainv, (size_t)nL * nL));
-    PCG_TRY(alloc(M, &h->bL, nL));
     PCG_TRY(alloc(M, &dflag, 1));
     PCG_CK(cudaMemsetAsync(ad, 0, sizeof(double) * (size_t)nL * nL, s));
     PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
@@ -1194,9 +1220,21 @@ int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s) {
         PCG_LAUNCH_CK();
         if (h->gs_nu) PCG_TRY(fill_gs_parts(lv, h->gs_blocks, s));
     }
-    // dense inverse of the coarsest matrix, in place
+    // coarsest solver's data, in place
     Level &lc = h->lev[L];
     int nL = lc.A.n;
+    if (h->coarse_iter) {
+        release(M, dflag);
+        int st = coarse_iter_build(h, s);
+        if (st) {
+            set_error("amg_refresh: an ILU(1) pivot of the coarsest level is not positive; the handle refuses "
+                      "solves until a refresh succeeds");
+            return st;
+        }
+        h->invalid = 0;
+        h->refresh_ms = now_ms() - t_begin;
+        return AMG_OK;
+    }
     double *ad = nullptr;
     PCG_TRY(alloc(M, &ad, (size_t)nL * nL));
     PCG_CK(cudaMemsetAsync(ad, 0, sizeof(double) * (size_t)nL * nL, s));

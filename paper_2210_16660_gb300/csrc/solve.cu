@@ -101,7 +101,9 @@ __device__ __forceinline__ void fail(Ctl *c, int status) {
 }
 
 // rho = r.z and beta of the next direction (last block of the kernel that
-// produced z): PCG beta = rho / rho_old, FCG(1) beta = -(z.q_old) / (p.q)_old.
+// produced z): PCG beta = rho / rho_old, FCG(1) beta = -(z.q_old) / (p.q)_old
+// (the float32 V-cycle, and either precision when the iterative coarsest
+// solve makes the V-cycle vary from one application to the next).
 __device__ __forceinline__ void finish_rho(Ctl *ctl, double rz, double zq) {
     ctl->counter[0] = 0;
     if (!isfinite(rz) || !isfinite(zq)) { fail(ctl, AMG_ERR_NAN); return; }
@@ -109,7 +111,7 @@ __device__ __forceinline__ void finish_rho(Ctl *ctl, double rz, double zq) {
     ctl->rho = rz;
     ctl->zq = zq;
     double beta = 0.0;
-    if (!ctl->restart) beta = ctl->mode == AMG_MODE_FCG32 ? -zq / ctl->pq_old : rz / ctl->rho_old;
+    if (!ctl->restart) beta = ctl->mode == AMG_MODE_FCG32 || ctl->flex ? -zq / ctl->pq_old : rz / ctl->rho_old;
     ctl->beta = beta;
 }
 
@@ -828,6 +830,24 @@ void launch_up_phase(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
                                   (const T *)P::b(lv), P::dinv(lv), P::x(lv), ctl)));
 }
 
+// Coarsest solve of the single-column V-cycle: x_L = A_L^{-1} b_L with the
+// dense inverse, or the iterative solve (FCG + block-Jacobi ILU(1)). Adds
+// the kernels launched to *kernels.
+template <typename T>
+int launch_coarsest(amg_hier *h, cudaStream_t s, int *kernels) {
+    using P = LP<T>;
+    Level &lc = h->lev.back();
+    if (h->coarse_iter) {
+        PCG_TRY(launch_coarse_iter<T>(h, h->cws, h->bL, P::x(lc), &h->ctl->done, nullptr, s));
+        *kernels += coarse_iter_launches(h);
+        return AMG_OK;
+    }
+    launch_k(h->pdl, k_coarse<T>, (h->nL * 32 + kBlock - 1) / kBlock, kBlock, s, h->nL, h->Ainv, h->bL, P::x(lc),
+             (const Ctl *)h->ctl);
+    *kernels += 1;
+    return AMG_OK;
+}
+
 // z = B r (one V-cycle in precision T), including rho / beta. Kernels are
 // launched with programmatic dependent launch when h->pdl (see pdl_enter).
 template <typename T, bool FCG>
@@ -867,9 +887,9 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     int spc = prof_begin(h, kLevelSpan + 3 * F + 2, s);
     if (F < L) {
         PCG_TRY(launch_smem_tail<T>(h, s));
+        kernels += 1;
     } else {
-        launch_k(pdl, k_coarse<T>, (h->nL * 32 + kBlock - 1) / kBlock, kBlock, s, h->nL, h->Ainv, h->bL,
-                 P::x(lev[L]), ctl);
+        PCG_TRY(launch_coarsest<T>(h, s, &kernels));
     }
     prof_end(h, spc, s);
     for (int l = F - 1; l >= 1; l--) {
@@ -880,7 +900,7 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
         kernels += (sh & 4) ? 1 : 2;
         prof_end(h, spl, s);
     }
-    kernels += 1 + 2;  // coarsest (or tail), prolongation and post sweep of level 0
+    kernels += 2;  // prolongation and post sweep of level 0
     prof_end(h, sp2, s);
     int sp3 = prof_begin(h, 1, s);
     launch_k(pdl, k_prolong<T>, h->gridv, kBlock, s, l0.A.n, P::xpre(l0), P::p(l0), l0.agg, P::x(lev[1]),
@@ -974,7 +994,7 @@ int launch_gs(amg_hier *h, int l, bool pre, const T *b, T *target, cudaStream_t 
 
 // z = B r with the hybrid Gauss-Seidel smoother (gs_nu sweeps each side):
 // the l1-Jacobi V-cycle with its smoothing steps replaced, the coarsest solve
-// by k_coarse (no cluster tail), rho and beta by k_gs_finish0.
+// by launch_coarsest (no cluster tail), rho and beta by k_gs_finish0.
 template <typename T, bool FCG>
 int launch_vcycle_gs(amg_hier *h, cudaStream_t s) {
     using P = LP<T>;
@@ -1007,9 +1027,7 @@ int launch_vcycle_gs(amg_hier *h, cudaStream_t s) {
         prof_end(h, spl, s);
     }
     int spc = prof_begin(h, kLevelSpan + 3 * L + 2, s);
-    launch_k(pdl, k_coarse<T>, (h->nL * 32 + kBlock - 1) / kBlock, kBlock, s, h->nL, h->Ainv, h->bL, P::x(lev[L]),
-             (const Ctl *)ctl);
-    kernels += 1;
+    PCG_TRY(launch_coarsest<T>(h, s, &kernels));
     prof_end(h, spc, s);
     for (int l = L - 1; l >= 1; l--) {
         Level &lv = lev[l];
@@ -1046,6 +1064,10 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
     } else if (MODE == AMG_MODE_FCG32) {
         if (h->gs_nu) PCG_TRY((launch_vcycle_gs<float, true>(h, s)));
         else PCG_TRY((launch_vcycle<float, true>(h, s)));
+    } else if (h->coarse_iter) {
+        // the float64 V-cycle is not a fixed operator either: FCG(1) beta
+        if (h->gs_nu) PCG_TRY((launch_vcycle_gs<double, true>(h, s)));
+        else PCG_TRY((launch_vcycle<double, true>(h, s)));
     } else {
         if (h->gs_nu) PCG_TRY((launch_vcycle_gs<double, false>(h, s)));
         else PCG_TRY((launch_vcycle<double, false>(h, s)));
@@ -1214,6 +1236,7 @@ bool is_device_ptr(const void *p) {
 // separately instead.
 int setup_tail(amg_hier *h) {
     h->tail_first[0] = h->tail_first[1] = 0;
+    if (h->coarse_iter) return AMG_OK;  // the tail holds a dense coarsest inverse
     const char *e = getenv("PCGAMG_TAIL");
     if (e && e[0] == '0') return AMG_OK;
     return setup_smem_tail(h);
@@ -1291,6 +1314,7 @@ int alloc_solve_workspace(amg_hier *h) {
     PCG_CK(cudaMallocHost(&h->ctl_host, sizeof(Ctl)));
     h->hist_cap = 1001;
     PCG_TRY(alloc(M, &h->hist, h->hist_cap));
+    if (h->coarse_iter) PCG_TRY(cws_alloc(h, M, h->cws, 1));
     PCG_TRY(setup_tail(h));
     return AMG_OK;
 }
@@ -1408,6 +1432,7 @@ int solve_launch(amg_hier *h, int mode, const double *b, const double *x0, doubl
     c0.rtol = rtol;
     c0.maxit = maxit;
     c0.mode = mode;
+    c0.flex = h->coarse_iter;
     c0.restart = 1;
     *h->ctl_host = c0;
     PCG_CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));
@@ -1458,6 +1483,7 @@ int solve_impl(amg_hier *h, const double *b, double *x, double rtol, int maxit, 
     c0.rtol = rtol;
     c0.maxit = maxit;
     c0.mode = h->mode;
+    c0.flex = h->coarse_iter;
     c0.restart = 1;
     *h->ctl_host = c0;
     PCG_CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s));

@@ -27,9 +27,7 @@ from . import workloads as W
 @dataclasses.dataclass
 class Mesh:
     """One resident mesh: its problem, hierarchy and a pool of time steps
-    ``(b_t, x0_t)`` on the device (requests cycle through the pool). Meshes
-    finer than 128^3 keep the z-spacing range of the 128^3 mesh
-    (``workloads.capped_grading``)."""
+    ``(b_t, x0_t)`` on the device (requests cycle through the pool)."""
     name: str
     problem: W.Problem
     amg: B.AMG
@@ -37,15 +35,18 @@ class Mesh:
 
 
 def prepare_meshes(sizes=(64, 128, 192), ratio: float = 1.04, seed: int = 5, pool: int = 4,
-                   device: str = "cuda") -> list[Mesh]:
+                   device: str = "cuda", lx: float = 1.0, coarse: str = "auto", coarse_max: int = 200) -> list[Mesh]:
+    """Meshes N^3 with z graded by ``ratio`` (x stretched to ``lx``), each
+    with its hierarchy (coarsest solver ``coarse``: a mesh whose coarsening
+    stalls above 4096 rows gets the iterative coarsest solve under "auto")
+    and a chain of ``pool`` time steps."""
     import torch
     meshes = []
     for idx, N in enumerate(sizes):
-        r = W.capped_grading(N, ratio)
-        prob = W.make_problem(N, r, seed=seed + idx, name=f"q1_{N}cube_r{r}")
+        prob = W.make_problem(N, ratio, seed=seed + idx, lx=lx, name=f"q1_{N}cube_r{ratio}")
         _, xs0 = W.make_rhs(prob, 1, seed + 100 + idx)
         chain = W.time_steps(prob, np.ascontiguousarray(xs0[:, 0]), pool, seed + 200 + idx)
-        amg = B.AMG.from_csr(prob.A, mode="fcg32")
+        amg = B.AMG.from_csr(prob.A, mode="fcg32", coarse=coarse, coarse_max=coarse_max)
         steps = [(torch.from_numpy(b).to(device), torch.from_numpy(np.ascontiguousarray(x0)).to(device))
                  for b, x0, _ in chain]
         meshes.append(Mesh(prob.name, prob, amg, steps))

@@ -266,17 +266,6 @@ def batch_sizes(count: int = 48, lo: int = 24, hi: int = 112, seed: int = 3) -> 
     return [int(lo + int(v % np.uint64(hi - lo + 1))) for v in w]
 
 
-def capped_grading(N: int, ratio: float, ref_N: int = 128) -> float:
-    """z-grading ratio for an N^3 mesh whose largest-to-smallest z spacing
-    does not exceed that of the ref_N^3 mesh at ``ratio`` (ratio^(ref_N-2)),
-    rounded to 4 decimals. Finer meshes than ref_N keep the range, so the
-    far-field cells are not stretched further (1.04 at 192^3 would span
-    1.04^190 ~ 1700)."""
-    if N <= ref_N:
-        return ratio
-    return round(ratio ** ((ref_N - 2) / (N - 2)), 4)
-
-
 def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
     """Arrival times (s) of a Poisson stream of ``count`` requests at ``rate``
     per second, starting at 0: exponential gaps ``-ln(u) / rate`` with ``u``

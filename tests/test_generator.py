@@ -173,15 +173,3 @@ def test_time_step_chain():
         rms = np.sqrt(np.mean(prev * prev))
         assert 0 < np.linalg.norm(xs - prev) / (rms * np.sqrt(prob.A.n)) < 0.02
         prev = xs
-
-
-def test_capped_grading_keeps_the_spacing_range():
-    """Meshes up to 128^3 keep the ratio; finer ones get the ratio whose
-    largest/smallest z spacing matches the 128^3 mesh's (to 4 decimals)."""
-    assert W.capped_grading(64, 1.04) == 1.04 and W.capped_grading(128, 1.04) == 1.04
-    for N in (160, 192, 320):
-        r = W.capped_grading(N, 1.04)
-        assert r < 1.04
-        assert abs(np.log(r ** (N - 2)) - np.log(1.04 ** 126)) < 0.01 * np.log(1.04 ** 126) * 5
-        h = W.graded_spacing(N, r)
-        assert abs(h.max() / h.min() - r ** (N - 2)) < 1e-9 * r ** (N - 2)

@@ -250,12 +250,15 @@ def test_bad_server_arguments(meshes):
 
 
 def test_full_size_serving_meshes():
-    """The benchmark's serving meshes (64^3, 128^3 and 192^3, resident) with
-    the default server: a burst of requests over all three, every one within
+    """The benchmark's serving meshes (64^3, 128^3 and 192^3 at z grading
+    1.04, resident; the 192^3 hierarchy stalls above the dense limit and uses
+    the iterative coarsest solve) with the default server: a burst of
+    requests over all three, every one within
     rtol by the host's own residual for one request per mesh, each equal to
     its result served alone in the same kind of place, and the 64^3 request
     against the oracle."""
     meshes = S.prepare_meshes((64, 128, 192), ratio=1.04, seed=5, pool=2)
+    assert [m.amg.coarse_info()["kind"] for m in meshes] == ["dense", "dense", "iter"]
     srv = S.make_server(meshes, "fcg32")
     reqs = [(i % 3, (i // 3) % 2) for i in range(12)]
     xs, tickets = [], []
