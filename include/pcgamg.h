@@ -395,10 +395,11 @@ int amg_profile(amg_handle h, int enable);
 
 /* Accumulated device time (ms) and launch count per kernel kind since the
  * last read, then reset. kinds: 0 level-0 pre-smooth/residual, 1 level-0
- * prolong/post-smooth (+ r.z), 2 q = A p (+ p.q), 3 x/r update, 4 true
- * residual, 5 levels >= 1 incl. restriction and coarsest solve (one span per
- * V-cycle), 6 p = z + beta p. ms and counts are host arrays of length
- * nkinds (<= 7). */
+ * post-smooth (+ r.z; with the Gauss-Seidel smoother the whole level-0 up
+ * phase), 2 q = A p (+ p.q), 3 x/r update, 4 true residual, 5 levels >= 1
+ * incl. restriction and coarsest solve (one span per V-cycle), 6 p = z +
+ * beta p, 7 level-0 prolongation. ms and counts are host arrays of length
+ * nkinds (<= 8). */
 int amg_profile_read(amg_handle h, double *ms, int64_t *counts, int nkinds);
 
 /* Per-level V-cycle time (ms) and span counts since the last read, then
@@ -420,15 +421,19 @@ int64_t amg_launch_count(amg_handle h);
  * cannot allocate device memory while they solve, such as an application
  * that gives the whole GPU to its own memory pool, or a time-step loop that
  * cannot take the device synchronisation an allocation may cause.
- * b, x, r: device pointers to n values (r is written); norms: 2 doubles,
- * host or device (a host pointer makes the call wait for the result).
+ * b, x, r: device pointers to n values on the handle's device, which must
+ * be the current one (r is written and must not overlap b or x); norms: 2
+ * doubles, host or device (a host pointer makes the call wait for the
+ * result, so a call on a stream being captured needs a device pointer).
  * Scratch: a fixed 512 KiB array inside the library (per GPU, kept until the
  * process exits) holds one partial sum pair per 256 rows, so at most
  * 8,388,608 rows are accepted; larger levels return AMG_ERR_ARG. The first
  * call on a device looks up that array's device address, so make it before
  * any stream capture. All calls share the array: calls that overlap on the
  * GPU (different streams, threads or handles) race and must be ordered by
- * the caller. Calls no cudaMalloc, cudaFree or allocating library routine. */
+ * the caller. Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: AMG_ERR_ARG (NULL or host b/x/r, r overlapping b or x, another
+ * current device, too many rows, host norms during a capture), AMG_ERR_CUDA. */
 int amg_residual_noalloc(amg_handle h, const double *b, const double *x, double *r, double *norms,
                          void *stream);
 

@@ -201,6 +201,16 @@ def use_torch_allocator(enable: bool = True) -> None:
     _torch_alloc_refs = refs
 
 
+def _current_device() -> int | None:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_device()
+    except Exception:
+        return None
+    return None
+
+
 def _stream_ptr(stream) -> int | None:
     if stream is None:
         try:
@@ -264,6 +274,7 @@ class AMG:
         self._h = h
         self.n = nrows
         self.mode = mode
+        self.device = _current_device()
 
     @classmethod
     def from_csr(cls, A, **kw):
@@ -359,7 +370,7 @@ class AMG:
             raise AmgError(st, last_error())
         return rp, ci, v
 
-    KINDS = ("down0", "up0", "spmv", "update", "residual", "coarse_levels", "axpy")
+    KINDS = ("down0", "post0", "spmv", "update", "residual", "coarse_levels", "axpy", "prolong0")
 
     def profile(self, enable: bool = True):
         st = load().amg_profile(self._h, int(enable))
@@ -367,9 +378,9 @@ class AMG:
             raise AmgError(st, last_error())
 
     def profile_read(self) -> dict:
-        ms = np.zeros(7)
-        cnt = np.zeros(7, np.int64)
-        load().amg_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, 7)
+        ms = np.zeros(8)
+        cnt = np.zeros(8, np.int64)
+        load().amg_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data, 8)
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KINDS)}
 
     def autotune(self, reps: int = 5, stream=None) -> int:
@@ -410,6 +421,12 @@ class AMG:
 
     def residual_noalloc(self, b, x, r, stream=None):
         """``amg_residual_noalloc``: r = b - A x (device tensors); returns (||r||, ||b||)."""
+        for name, t in (("b", b), ("x", x), ("r", r)):
+            n = t.size if isinstance(t, np.ndarray) else t.numel()
+            if n != self.n:
+                raise ValueError(f"{name} holds {n} values, the hierarchy has {self.n} rows")
+            if hasattr(t, "device") and getattr(t, "is_cuda", False) and t.device.index != self.device:
+                raise ValueError(f"{name} is on cuda:{t.device.index}, the hierarchy on cuda:{self.device}")
         norms = np.zeros(2)
         bp, _ = _ptr(b, np.float64)
         xp, _ = _ptr(x, np.float64)

@@ -15,9 +15,9 @@
 // SM, so the count of float64 warp instructions is what the apply costs).
 //
 // One inner iteration is two launches (no grid-wide waits):
-//   k_cq : p = z + beta p_old (into the other p buffer), q = A p with the
-//          gathered entries formed as z_j + beta p_old_j, p.q;
-//          the last block forms alpha = rho / p.q
+//   k_cq : p = z + beta p_old (into the other p buffer) and q = A p, formed
+//          as A z + beta q_old (A p_old = q_old: one gathered vector and one
+//          FMA per stored entry), p.q; the last block forms alpha = rho / p.q
 //   k_cx : x += alpha p, r -= alpha q, z = M^{-1} r (block-local), and the
 //          partial sums r.r, r.z, z.q; the last block applies the stop test
 //          and forms rho and beta = -(z.q) / (p.q)_old of the next iteration
@@ -39,6 +39,7 @@ constexpr int kB = kCoarseBlock;  // 32 rows per block
 constexpr int kCT = 256;          // threads per block of the solve kernels
 constexpr int kCW = kCT / 32;     // warps per block
 constexpr int kNoLev = 1 << 20;   // "no entry" level of fill
+constexpr int kQU = 4;            // matrix entries a lane loads ahead of their gathers
 
 // ------------------------------------------------------------------ setup
 // ILU(1) of block b, one thread per block. Row il of the block: the stored
@@ -135,16 +136,35 @@ __device__ __forceinline__ void st_cols(double *p, const double (&o)[KC]) {
 
 // z_b = M_b^{-1} r_b for this warp's block: lane i sums (M^{-1})_{ik} r_k over
 // k = 0..31 in order, r_k taken from lane k.
+// All 32 entries of the lane's row are loaded before the first FMA (one
+// round trip to L2 instead of a chain of them).
+__device__ __forceinline__ void block_row(const double *__restrict__ Mb, int lane, double (&m)[kB]) {
+#pragma unroll
+    for (int k = 0; k < kB; k++) m[k] = __ldg(Mb + k * kB + lane);
+}
+
+template <int KC>
+__device__ __forceinline__ void block_apply_m(const double (&m)[kB], const double (&r)[KC], double (&z)[KC]) {
+#pragma unroll
+    for (int v = 0; v < KC; v++) z[v] = 0.0;
+#pragma unroll
+    for (int k = 0; k < kB; k++) {
+#pragma unroll
+        for (int v = 0; v < KC; v++) z[v] = fma(m[k], __shfl_sync(0xffffffffu, r[v], k), z[v]);
+    }
+}
+
 template <int KC>
 __device__ __forceinline__ void block_apply(const double *__restrict__ Mb, const double (&r)[KC], double (&z)[KC],
                                             int lane) {
+    double m[kB];
+    block_row(Mb, lane, m);
 #pragma unroll
     for (int v = 0; v < KC; v++) z[v] = 0.0;
-#pragma unroll 8
-    for (int k = 0; k < kB; k++) {
-        double m = __ldg(Mb + k * kB + lane);
 #pragma unroll
-        for (int v = 0; v < KC; v++) z[v] = fma(m, __shfl_sync(0xffffffffu, r[v], k), z[v]);
+    for (int k = 0; k < kB; k++) {
+#pragma unroll
+        for (int v = 0; v < KC; v++) z[v] = fma(m[k], __shfl_sync(0xffffffffu, r[v], k), z[v]);
     }
 }
 
@@ -296,24 +316,57 @@ __global__ void __launch_bounds__(kCT) k_cinit(int n, int nb, int K, const doubl
     }
 }
 
-// p_new = z + beta p_old and q = A p_new over the block's sliced-ELL slice
-// (the gathered entries formed as z_j + beta p_old_j), p.q; the last block
-// forms alpha = rho / p.q (a p.q that is not a positive finite number stops
-// the column with its current x).
+// p_new = z + beta p_old and q = A p_new = A z + beta q_old over the
+// sliced-ELL slices (q_old = A p_old from the previous iteration), p.q; the
+// last block forms alpha = rho / p.q (a p.q that is not a positive finite
+// number stops the column with its current x). Four lanes share a row: lane
+// quarter s takes the row's entries s, s+4, s+8, ... in chunks whose columns
+// and values are all loaded before their gathers, and the four partial sums
+// meet in a shuffle tree ((s0 + s1) + (s2 + s3)), so a warp covers 8 rows of
+// a slice and the longest row's chain is a quarter of its length. The first
+// chunk's columns and values (written at setup only) are loaded before the
+// wait for the preceding kernel.
 template <int KC, typename IDX>
 __global__ void __launch_bounds__(kCT) k_cq(int n, int nb, int K, const int32_t *__restrict__ sptr,
                                             const IDX *__restrict__ col, const double *__restrict__ val,
                                             const double *__restrict__ z, const double *__restrict__ pold,
                                             double *__restrict__ pnew, double *__restrict__ q, double *partials,
                                             CCtl *ctl) {
-    pdl_enter();
-    if (!ctl->any) return;
     int G = K / KC;
     Items it = items(G);
-    int lane = threadIdx.x & 31;
+    int lane = threadIdx.x & 31, s = lane & 3;
+    // the warp's first item: its matrix chunk does not depend on earlier kernels
+    int j0[kQU];
+    double a0[kQU];
+    int wdt0 = 0;
+    int32_t base0 = 0;
+    {
+        int wi = it.wg;
+        int b = wi / (4 * G), quarter = (wi / G) & 3;
+        int rl = 8 * quarter + (lane >> 2), i = b * kB + rl;
+#pragma unroll
+        for (int u = 0; u < kQU; u++) { j0[u] = 0; a0[u] = 0.0; }
+        if (wi < nb * 4 * G && i < n) {
+            base0 = __ldg(sptr + b);
+            wdt0 = (__ldg(sptr + b + 1) - base0) >> 5;
+            if (s < wdt0) {
+#pragma unroll
+                for (int u = 0; u < kQU; u++) {
+                    int k = s + 4 * u;
+                    int kk = k < wdt0 ? k : s;
+                    if constexpr (sizeof(IDX) == 2) j0[u] = i + (int)__ldg(col + base0 + rl + kk * kB);
+                    else j0[u] = __ldg(col + base0 + rl + kk * kB);
+                    double av = __ldg(val + base0 + rl + kk * kB);
+                    a0[u] = k < wdt0 ? av : 0.0;
+                }
+            }
+        }
+    }
+    pdl_enter();
+    if (!ctl->any) return;
     int c0 = it.g * KC;
     double beta[KC];
-    bool live = false;
+    bool live = false, first = true;
 #pragma unroll
     for (int v = 0; v < KC; v++) {
         beta[v] = ctl->beta[c0 + v];
@@ -321,44 +374,72 @@ __global__ void __launch_bounds__(kCT) k_cq(int n, int nb, int K, const int32_t 
     }
     double acc[1][KC] = {};
     if (live) {
-        for (int wi = it.wg; wi < nb * G; wi += it.nw) {
-            int b = wi / G, i = b * kB + lane;
-            int64_t o = (int64_t)i * K + c0;
-            double zi[KC], pi[KC], qi[KC];
-            ld_cols<KC>(z + o, zi);
-            ld_cols<KC>(pold + o, pi);
+        for (int wi = it.wg; wi < nb * 4 * G; wi += it.nw, first = false) {
+            int b = wi / (4 * G), quarter = (wi / G) & 3;
+            int rl = 8 * quarter + (lane >> 2);  // row within the slice
+            int i = b * kB + rl;
+            double qi[KC];
 #pragma unroll
-            for (int v = 0; v < KC; v++) {
-                pi[v] = beta[v] == 0.0 ? zi[v] : zi[v] + beta[v] * pi[v];
-                qi[v] = 0.0;
-            }
+            for (int v = 0; v < KC; v++) qi[v] = 0.0;
             if (i < n) {
-                int32_t base = __ldg(sptr + b);
-                int wdt = (__ldg(sptr + b + 1) - base) >> 5;
-                const IDX *cp = col + base + lane;
-                const double *ap = val + base + lane;
-                for (int k = 0; k < wdt; k++) {
-                    int j;
-                    if constexpr (sizeof(IDX) == 2) j = i + (int)__ldg(cp + k * kB);
-                    else j = __ldg(cp + k * kB);
-                    double a = __ldg(ap + k * kB);
-                    double zj[KC], pj[KC];
-                    ld_cols<KC>(z + (int64_t)j * K + c0, zj);
-                    ld_cols<KC>(pold + (int64_t)j * K + c0, pj);
+                int32_t base = first ? base0 : __ldg(sptr + b);
+                int wdt = first ? wdt0 : (__ldg(sptr + b + 1) - base) >> 5;
+                const IDX *cp = col + base + rl;
+                const double *ap = val + base + rl;
+                for (int k0 = s; k0 < wdt; k0 += 4 * kQU) {
+                    int j[kQU];
+                    double a[kQU];
+                    if (first && k0 == s) {
 #pragma unroll
-                    for (int v = 0; v < KC; v++) {
-                        double e = beta[v] == 0.0 ? zj[v] : zj[v] + beta[v] * pj[v];
-                        qi[v] = fma(a, e, qi[v]);
+                        for (int u = 0; u < kQU; u++) { j[u] = j0[u]; a[u] = a0[u]; }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < kQU; u++) {
+                            int k = k0 + 4 * u;
+                            int kk = k < wdt ? k : k0;  // a valid entry of the row
+                            if constexpr (sizeof(IDX) == 2) j[u] = i + (int)__ldg(cp + kk * kB);
+                            else j[u] = __ldg(cp + kk * kB);
+                            double av = __ldg(ap + kk * kB);
+                            a[u] = k < wdt ? av : 0.0;
+                        }
                     }
+                    double zj[kQU][KC];
+#pragma unroll
+                    for (int u = 0; u < kQU; u++) ld_cols<KC>(z + (int64_t)j[u] * K + c0, zj[u]);
+#pragma unroll
+                    for (int u = 0; u < kQU; u++)
+#pragma unroll
+                        for (int v = 0; v < KC; v++) qi[v] = fma(a[u], zj[u][v], qi[v]);
                 }
             }
-            st_cols<KC>(pnew + o, pi);
-            st_cols<KC>(q + o, qi);
 #pragma unroll
-            for (int v = 0; v < KC; v++) acc[0][v] += pi[v] * qi[v];
+            for (int v = 0; v < KC; v++) {
+                qi[v] += __shfl_xor_sync(0xffffffffu, qi[v], 1);
+                qi[v] += __shfl_xor_sync(0xffffffffu, qi[v], 2);
+            }
+            if (s == 0) {
+                int64_t o = (int64_t)i * K + c0;
+                double zi[KC], pi[KC], qo[KC];
+                ld_cols<KC>(z + o, zi);
+                ld_cols<KC>(pold + o, pi);
+                ld_cols<KC>(q + o, qo);
+#pragma unroll
+                for (int v = 0; v < KC; v++) {
+                    if (beta[v] != 0.0) {
+                        pi[v] = zi[v] + beta[v] * pi[v];
+                        qi[v] = qi[v] + beta[v] * qo[v];
+                    } else {
+                        pi[v] = zi[v];
+                    }
+                }
+                st_cols<KC>(pnew + o, pi);
+                st_cols<KC>(q + o, qi);
+#pragma unroll
+                for (int v = 0; v < KC; v++) acc[0][v] += pi[v] * qi[v];
+            }
         }
     }
-    if (publish<KC, 1>(acc, it.g, it.wg < nb * G, K, partials, &ctl->counter[1])) {
+    if (publish<KC, 1>(acc, it.g, it.wg < nb * 4 * G, K, partials, &ctl->counter[1])) {
         __shared__ double res[32];
         final_sums<1>(partials, K, res);
         if (threadIdx.x == 0) {
@@ -391,11 +472,14 @@ __global__ void __launch_bounds__(kCT) k_cx(int n, int nb, int K, const double *
                                             double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
                                             TO *__restrict__ xo, double *partials, CCtl *ctl, int iter, int maxit,
                                             double tol) {
-    pdl_enter();
-    if (!ctl->any) return;
     int G = K / KC;
     Items it = items(G);
     int lane = threadIdx.x & 31;
+    // the first block's inverse row (written at setup only) before the wait
+    double m0[kB];
+    if (it.wg < nb * G) block_row(Minv + (int64_t)(it.wg / G) * kB * kB, lane, m0);
+    pdl_enter();
+    if (!ctl->any) return;
     int c0 = it.g * KC;
     double alpha[KC];
     bool act[KC];
@@ -423,7 +507,8 @@ __global__ void __launch_bounds__(kCT) k_cx(int n, int nb, int K, const double *
                     ri[v] = fma(-alpha[v], qi[v], ri[v]);
                 }
             }
-            block_apply<KC>(Minv + (int64_t)b * kB * kB, ri, zi, lane);
+            if (wi == it.wg) block_apply_m<KC>(m0, ri, zi);
+            else block_apply<KC>(Minv + (int64_t)b * kB * kB, ri, zi, lane);
             st_cols<KC>(x + o, xi);
             st_cols<KC>(r + o, ri);
             st_cols<KC>(z + o, zi);
@@ -467,7 +552,7 @@ int grid_for_items(amg_hier *h, int items, int G) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms < 1) sms = 152;
     int want = (items + kCW - 1) / kCW;
-    int cap = sms * 2;
+    int cap = sms * 4;
     int g = want < cap ? want : cap;
     if (g < 1) g = 1;
     // the warp count must be a multiple of G (a warp's column group is fixed)
@@ -503,7 +588,7 @@ int launch_ci(amg_hier *h, CoarseWS &W, const double *bL, TO *xL, const int *out
         double *pold = (it & 1) ? W.p1 : W.p0;
         double *pnew = (it & 1) ? W.p0 : W.p1;
         cudaError_t e = cudaSuccess;
-        WITH_COARSE_COLS(lc.S, (e = launch_k(pdl, k_cq<KC, IDX>, g, kCT, s, n, nb, K, (const int32_t *)lc.S.sptr,
+        WITH_COARSE_COLS(lc.S, (e = launch_k(pdl, k_cq<KC, IDX>, W.grid_q, kCT, s, n, nb, K, (const int32_t *)lc.S.sptr,
                                              cols, (const double *)lc.S.v64, (const double *)W.z,
                                              (const double *)pold, pnew, W.q, W.partials, W.ctl)));
         PCG_CK(e);
@@ -554,13 +639,14 @@ int cws_alloc(amg_hier *h, Mem &M, CoarseWS &W, int K) {
     W.K = K;
     int KC = K == 1 ? 1 : 2;
     W.grid = grid_for_items(h, nb * (K / KC), K / KC);
+    W.grid_q = grid_for_items(h, nb * 4 * (K / KC), K / KC);
     PCG_TRY(alloc(M, &W.x, m));
     PCG_TRY(alloc(M, &W.r, m));
     PCG_TRY(alloc(M, &W.z, m));
     PCG_TRY(alloc(M, &W.p0, m));
     PCG_TRY(alloc(M, &W.p1, m));
     PCG_TRY(alloc(M, &W.q, m));
-    PCG_TRY(alloc(M, &W.partials, (size_t)3 * K * W.grid));
+    PCG_TRY(alloc(M, &W.partials, (size_t)3 * K * (W.grid > W.grid_q ? W.grid : W.grid_q)));
     PCG_TRY(alloc(M, &W.ctl, 1));
     if (M.dry) return AMG_OK;
     PCG_CK(cudaMemsetAsync(W.ctl, 0, sizeof(CCtl), M.stream));
@@ -582,6 +668,7 @@ void cws_free(Mem &M, CoarseWS &W) {
     release(M, W.ctl);
     W.K = 0;
     W.grid = 0;
+    W.grid_q = 0;
 }
 
 // Kernels launched by one iterative coarsest solve.

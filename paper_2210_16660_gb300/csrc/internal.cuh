@@ -198,9 +198,9 @@ struct CCtl {
 
 // Work vectors of the iterative coarsest solve: (32 nb) x K row-major.
 struct CoarseWS {
-    int K = 0, grid = 0;
+    int K = 0, grid = 0, grid_q = 0;   // blocks of the block-local kernels and of the SpMV
     double *x = nullptr, *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
-    double *partials = nullptr;
+    double *partials = nullptr;        // 3 K max(grid, grid_q) doubles
     CCtl *ctl = nullptr;
 };
 
@@ -279,7 +279,7 @@ struct amg_hier {
     double last_true_rel = 0.0;
     double setup_ms[4] = {0, 0, 0, 0};
     // kernel timing (amg_profile)
-    static constexpr int kKinds = 7;
+    static constexpr int kKinds = 8;
     int profile = 0;
     std::vector<cudaEvent_t> ev;      // pool: pairs per kind per iteration of a chunk
     int ev_used = 0;

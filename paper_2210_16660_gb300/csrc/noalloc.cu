@@ -131,6 +131,12 @@ __global__ void __launch_bounds__(kNaBlock) k_residual_na(int n, const int32_t *
     }
 }
 
+// [a, a + n) and [b, b + n) share an address
+bool na_overlap(const double *a, const double *b, int64_t n) {
+    uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b, len = (uintptr_t)n * sizeof(double);
+    return a0 < b0 + len && b0 < a0 + len;
+}
+
 bool na_is_device(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -164,12 +170,34 @@ extern "C" int amg_residual_noalloc(amg_handle h, const double *b, const double 
                   "memory)");
         return AMG_ERR_ARG;
     }
+    // r is written while other threads still read x and b as gathered
+    // columns: it must not share memory with either
+    if (na_overlap(r, b, n) || na_overlap(r, x, n)) {
+        set_error("amg_residual_noalloc: r overlaps b or x");
+        return AMG_ERR_ARG;
+    }
+    int dev = 0;
+    PCG_CK(cudaGetDevice(&dev));
+    if (dev != h->device) {
+        set_error("amg_residual_noalloc: the current device %d is not the handle's device %d", dev, h->device);
+        return AMG_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool host_norms = !na_is_device(norms);
+    if (host_norms) {
+        // a host norms pointer makes the call wait, which a stream capture forbids
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        PCG_CK(cudaStreamIsCapturing(s, &cap));
+        if (cap != cudaStreamCaptureStatusNone) {
+            set_error("amg_residual_noalloc: norms must be a device pointer while the stream is captured");
+            return AMG_ERR_ARG;
+        }
+    }
     void *base = nullptr;
     PCG_TRY(na_scratch(&base));
     double *partials = static_cast<double *>(base);
     double *dnorms = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + kNaPartialBytes);
     unsigned *counter = reinterpret_cast<unsigned *>(static_cast<unsigned char *>(base) + kNaPartialBytes + 64);
-    cudaStream_t s = (cudaStream_t)stream;
     PCG_CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
     int blocks = (n + kNaBlock - 1) / kNaBlock;
     if (blocks < 1) blocks = 1;
@@ -181,6 +209,6 @@ extern "C" int amg_residual_noalloc(amg_handle h, const double *b, const double 
                                                            dnorms, counter);
     PCG_LAUNCH_CK();
     PCG_CK(cudaMemcpyAsync(norms, dnorms, 2 * sizeof(double), cudaMemcpyDefault, s));
-    if (!na_is_device(norms)) PCG_CK(cudaStreamSynchronize(s));
+    if (host_norms) PCG_CK(cudaStreamSynchronize(s));
     return AMG_OK;
 }

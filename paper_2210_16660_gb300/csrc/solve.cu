@@ -620,8 +620,9 @@ inline int grid_rows(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
 // ------------------------------------------------------------ profiling
 // CUDA-event spans around kernel launches (only when profiling is on).
-// kinds: 0 down0, 1 up0 (prolong0 + post0), 2 q = A p, 3 update,
-// 4 true residual, 5 levels >= 1 and the coarsest solve, 6 p = z + beta p.
+// kinds: 0 down0, 1 post0 (the whole up phase of level 0 with the
+// Gauss-Seidel smoother), 2 q = A p, 3 update, 4 true residual, 5 levels >= 1
+// and the coarsest solve, 6 p = z + beta p, 7 prolong0.
 constexpr int kEvPairs = 256;
 
 // Opens a span of `kind` (kinds < kKinds: the kernel kinds above; kinds
@@ -902,9 +903,11 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     }
     kernels += 2;  // prolongation and post sweep of level 0
     prof_end(h, sp2, s);
-    int sp3 = prof_begin(h, 1, s);
+    int sp7 = prof_begin(h, 7, s);
     launch_k(pdl, k_prolong<T>, h->gridv, kBlock, s, l0.A.n, P::xpre(l0), P::p(l0), l0.agg, P::x(lev[1]),
              P::xp(l0), ctl);
+    prof_end(h, sp7, s);
+    int sp3 = prof_begin(h, 1, s);
     WITH_COLS(l0.S, (launch_k(pdl, k_post<T, double, true, FCG, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n,
                               l0.S.sptr, cols, P::val(l0), P::xp(l0), b0, P::dinv(l0), h->z, h->r, h->q, h->partials,
                               ctl)));
