@@ -56,6 +56,7 @@ extern "C" {
 #define AMG_ERR_COARSE 8    /* the dense coarsest solve was asked for (or a single level
                                was left) with more than 4096 rows */
 #define AMG_ERR_BUSY 9      /* serving: the request queue is full */
+#define AMG_ERR_MATCH 10    /* setup: a matching pass did not finish within 20000 rounds */
 
 /* Coarsest solver (Sec. 3.1). AUTO: the dense direct solve when the coarsest
  * level has at most 4096 rows, else the iterative one. DENSE: the dense
@@ -127,7 +128,8 @@ int amg_set_allocator(amg_alloc_fn alloc, amg_free_fn dealloc, void *ctx);
  * A is copied; the caller may free it after the call returns.
  * Errors: AMG_ERR_ARG (bad CSR or parameters; ITER with a single level),
  * AMG_ERR_OOM, AMG_ERR_BREAKDOWN (coarsest not SPD, or an ILU(1) pivot that
- * is not positive), AMG_ERR_COARSE, AMG_ERR_CUDA. *out is NULL on error. */
+ * is not positive), AMG_ERR_COARSE, AMG_ERR_MATCH, AMG_ERR_CUDA. *out is
+ * NULL on error. */
 int amg_setup(const amg_csr *A, const amg_params *p, void *stream, amg_handle *out);
 
 /* Partial reuse of the hierarchy (Sec. 4: when the mesh topology stays and

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_NAN, ERR_CUDA, ERR_TIMEOUT, ERR_COARSE, ERR_BUSY = range(10)
+OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_NAN, ERR_CUDA, ERR_TIMEOUT, ERR_COARSE, ERR_BUSY, ERR_MATCH = range(11)
 MODE_PCG64, MODE_FCG32 = 0, 1
 _MODES = {"pcg64": MODE_PCG64, "fcg32": MODE_FCG32}
 COARSE_AUTO, COARSE_DENSE, COARSE_ITER = 0, 1, 2

@@ -203,27 +203,61 @@ __device__ __forceinline__ bool edge_before(double c1, int a1, int b1, double c2
     return b1 < b2;
 }
 
-// One round of the locally-dominant matching, part 1: every free vertex
-// points at its first candidate edge (c > 1) to another free vertex.
-__global__ void k_match_cand(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+// Candidate list of each row for one matching pass: the neighbours j with
+// c_ij > 1, in the strict total order of edge_before (largest weight first,
+// ties by the smaller (min, max) pair). Weights do not change while the pass
+// runs, so they are formed once here (same rounding as the oracle's) and
+// sorted in the row's own slots [rp[i], rp[i] + len[i]) by insertion.
+__global__ void k_match_prep(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                              const double *__restrict__ v, const double *__restrict__ dg,
-                             const double *__restrict__ w, const int32_t *__restrict__ mate,
-                             int32_t *__restrict__ cand, int *any) {
+                             const double *__restrict__ w, int32_t *__restrict__ lst, double *__restrict__ lc,
+                             int32_t *__restrict__ len, int32_t *__restrict__ ptr) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (mate[i] >= 0) { cand[i] = -1; return; }
-    double bc = 0.0;
-    int bj = -1, ba = 0, bb = 0;
-    for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+    int32_t r0 = rp[i];
+    int m = 0;
+    for (int32_t k = r0; k < rp[i + 1]; k++) {
         int j = ci[k];
-        if (j == i || mate[j] >= 0) continue;
+        if (j == i) continue;
         int a = min(i, j), b = max(i, j);
         double c = edge_weight(v[k], dg[a], dg[b], w[a], w[b]);
         if (!(c > 1.0)) continue;
-        if (bj < 0 || edge_before(c, a, b, bc, ba, bb)) { bc = c; bj = j; ba = a; bb = b; }
+        // insert (c, j) into the sorted prefix
+        int t = m;
+        while (t > 0) {
+            int jp = lst[r0 + t - 1];
+            double cp = lc[r0 + t - 1];
+            if (!edge_before(c, a, b, cp, min(i, jp), max(i, jp))) break;
+            lst[r0 + t] = jp;
+            lc[r0 + t] = cp;
+            t--;
+        }
+        lst[r0 + t] = j;
+        lc[r0 + t] = c;
+        m++;
     }
-    cand[i] = bj;
-    if (bj >= 0) *any = 1;
+    len[i] = m;
+    ptr[i] = 0;
+}
+
+// One round of the locally-dominant matching, part 1: every free vertex
+// points at its best candidate that is still free (its list pointer moves
+// past matched neighbours: vertices only ever become matched, so the first
+// free entry of the sorted list is the best free candidate). any is set when
+// some vertex points somewhere.
+__global__ void k_match_round(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ lst,
+                              const int32_t *__restrict__ len, int32_t *__restrict__ ptr,
+                              const int32_t *__restrict__ mate, int32_t *__restrict__ cand, int *any) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (mate[i] >= 0) { cand[i] = -1; return; }
+    int32_t r0 = rp[i];
+    int p = ptr[i], e = len[i];
+    while (p < e && mate[lst[r0 + p]] >= 0) p++;
+    ptr[i] = p;
+    int j = p < e ? lst[r0 + p] : -1;
+    cand[i] = j;
+    if (j >= 0) *any = 1;
 }
 
 // Part 2: mutual pointers are locally dominant edges; take them.
@@ -683,6 +717,9 @@ double now_ms() {
                std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+constexpr int kMatchBatch = 8;      // matching rounds launched per host check
+constexpr int kMatchRounds = 20000; // rounds allowed per pass
+
 int read_flag(int *dflag, cudaStream_t s, int *out) {
     PCG_CK(cudaMemcpyAsync(out, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     PCG_CK(cudaStreamSynchronize(s));
@@ -747,27 +784,45 @@ int pairwise_pass(amg_hier *h, const DevCSR &cur, const double *w, int32_t **agg
     int32_t *mate = nullptr, *cand = nullptr, *lead = nullptr, *idx = nullptr, *agg = nullptr;
     int32_t *mem0 = nullptr, *mem1 = nullptr;
     int *dflag = nullptr;
+    int32_t *lst = nullptr, *len = nullptr, *ptr = nullptr;
+    double *lc = nullptr;
     PCG_TRY(alloc(M, &dg, m));
     PCG_TRY(alloc(M, &mate, m));
     PCG_TRY(alloc(M, &cand, m));
-    PCG_TRY(alloc(M, &dflag, 1));
+    PCG_TRY(alloc(M, &lst, cur.nnz));
+    PCG_TRY(alloc(M, &lc, cur.nnz));
+    PCG_TRY(alloc(M, &len, m));
+    PCG_TRY(alloc(M, &ptr, m));
+    PCG_TRY(alloc(M, &dflag, kMatchBatch));
     double t0 = now_ms();
     k_diag<<<grid_for(m), kBlock, 0, s>>>(m, cur.rp, cur.ci, cur.v, dg);
     k_fill<int32_t><<<grid_for(m), kBlock, 0, s>>>(mate, m, -1);
+    k_match_prep<<<grid_for(m, 128), 128, 0, s>>>(m, cur.rp, cur.ci, cur.v, dg, w, lst, lc, len, ptr);
     PCG_LAUNCH_CK();
-    for (int round = 0;; round++) {
-        PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s));
-        k_match_cand<<<grid_for(m), kBlock, 0, s>>>(m, cur.rp, cur.ci, cur.v, dg, w, mate, cand, dflag);
-        k_match_commit<<<grid_for(m), kBlock, 0, s>>>(m, cand, mate);
+    release(M, lc);
+    // rounds in batches of kMatchBatch, one host check per batch: a round
+    // after the last productive one finds no candidate and changes nothing
+    int rounds = 0;
+    for (;;) {
+        PCG_CK(cudaMemsetAsync(dflag, 0, sizeof(int) * kMatchBatch, s));
+        for (int r = 0; r < kMatchBatch; r++) {
+            k_match_round<<<grid_for(m), kBlock, 0, s>>>(m, cur.rp, lst, len, ptr, mate, cand, dflag + r);
+            k_match_commit<<<grid_for(m), kBlock, 0, s>>>(m, cand, mate);
+        }
         PCG_LAUNCH_CK();
-        int any = 0;
-        PCG_TRY(read_flag(dflag, s, &any));
-        if (!any) break;
-        if (round >= 20000) {
-            set_error("matching did not finish in 20000 rounds");
-            return AMG_ERR_CUDA;
+        int any[kMatchBatch];
+        PCG_CK(cudaMemcpyAsync(any, dflag, sizeof(int) * kMatchBatch, cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaStreamSynchronize(s));
+        rounds += kMatchBatch;
+        if (!any[kMatchBatch - 1]) break;
+        if (rounds >= kMatchRounds) {
+            set_error("amg_setup: the matching did not finish in %d rounds", kMatchRounds);
+            return AMG_ERR_MATCH;
         }
     }
+    release(M, lst);
+    release(M, len);
+    release(M, ptr);
     release(M, cand);
     release(M, dg);
     *t_match += now_ms() - t0;
