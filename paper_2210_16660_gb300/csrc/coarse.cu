@@ -363,6 +363,10 @@ __global__ void __launch_bounds__(kCT) k_cq(int n, int nb, int K, const int32_t 
         }
     }
     pdl_enter();
+    z = after_wait(z);
+    pold = after_wait(pold);
+    pnew = after_wait(pnew);
+    q = after_wait(q);
     if (!ctl->any) return;
     int c0 = it.g * KC;
     double beta[KC];
@@ -479,6 +483,12 @@ __global__ void __launch_bounds__(kCT) k_cx(int n, int nb, int K, const double *
     double m0[kB];
     if (it.wg < nb * G) block_row(Minv + (int64_t)(it.wg / G) * kB * kB, lane, m0);
     pdl_enter();
+    pnew = after_wait(pnew);
+    q = after_wait(q);
+    x = after_wait(x);
+    r = after_wait(r);
+    z = after_wait(z);
+    xo = after_wait(xo);
     if (!ctl->any) return;
     int c0 = it.g * KC;
     double alpha[KC];

@@ -49,6 +49,17 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// A kernel that reads static data before pdl_enter() passes every pointer to
+// data the preceding kernel wrote through after_wait() once pdl_enter() has
+// returned: the empty volatile asm stays after the wait (volatile asms keep
+// their order) and the pointer it yields is unknown to the compiler before
+// it, so no read-only-path load through it can be hoisted above the wait.
+template <typename T>
+__device__ __forceinline__ T *after_wait(T *p) {
+    asm volatile("" : "+l"(p));
+    return p;
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s,
                             Args... args) {

@@ -75,6 +75,9 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tail_smem(SmemTailPlan plan, c
         for (int k = tid; k < plan.static_bytes / 16; k += nth) dst[k] = __ldg(src + k);
     }
     pdl_enter();
+    bF = after_wait(bF);
+    xpreF = after_wait(xpreF);
+    xF = after_wait(xF);
     if (ctl->done) return;
     // ... and the entry level's b and xpre rows (written by the previous kernel)
     {
