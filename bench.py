@@ -50,6 +50,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--multi-k", type=int, default=32, help="right-hand sides of the multi-column form (0: skip)")
     ap.add_argument("--multi-N", type=int, default=160, help="mesh of the multi-column form (N^3 nodes)")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="instead of the default run: arrival-rate sweep of the mixed and plain float64 servers "
+                         "(--sweep-count requests per rate) and an 8 GB admission run")
+    ap.add_argument("--sweep-count", type=int, default=2000)
     ap.add_argument("--large", action="store_true",
                     help="instead of the default run: one 320^3 mesh, 8 right-hand sides, per-level rates")
     ap.add_argument("--multi-reps", type=int, default=3)
@@ -66,6 +70,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-refresh", action="store_true", help="skip the partial-reuse (amg_refresh) measurement")
     ap.add_argument("--gs-nu", type=int, default=4, help="sweeps of the hybrid Gauss-Seidel comparison (0: skip)")
     ap.add_argument("--gs-blocks", type=int, default=65536, help="row blocks per level of the Gauss-Seidel smoother")
+    ap.add_argument("--no-smoothed", action="store_true", help="skip the smoothed-aggregation comparison")
     return ap.parse_args(argv)
 
 
@@ -657,6 +662,49 @@ def run_ours(args):
             smoother[sm] = row
         ga.close()
 
+    # smoothed aggregation (Sec. 3.1): P = (I - omega D^-1 A) P_hat on every
+    # level against the tentative P_hat, same system and right-hand sides
+    smoothed = {}
+    if not args.no_smoothed:
+        smoothed = {"workload": prob.name,
+                    "note": "tentative n_pass = 2 (the default) against smoothed aggregation with the paper's "
+                            "aggregate sizes |G| <= 8 (n_pass = 3, MLVSMATCH3) and |G| <= 16 (n_pass = 4, "
+                            "MLVSMATCH4); l1-Jacobi smoothing in all three"}
+        cands = [("tentative_npass2", amg, False)]
+        for npass in (3, 4):
+            t0 = time.perf_counter()
+            sa = B.AMG.from_csr(prob.A, mode="fcg32", stream=stream, smoothed=True, n_pass=npass)
+            torch.cuda.synchronize()
+            cands.append((f"smoothed_npass{npass}", sa, True))
+        for name, h, is_sa in cands:
+            info = h.info()
+            vb = {"fcg32": 4, "pcg64": 8}
+            row = {"levels": len(info), "rows_nnz": info,
+                   "operator_complexity": sum(z for _, z in info) / info[0][1]}
+            for mode in ("fcg32", "pcg64"):
+                h.set_mode(mode)
+                m = timed_solves(h, bs, x, 3, 1, args.rtol, args.maxit, torch, stream, None, device)
+                # V-cycle bytes: two sweeps of every level's matrix as stored
+                # (values + columns) plus the transfers (aggregate maps, or P
+                # and P^T as CSR: value + column per entry, twice)
+                byt = 0
+                for l in range(len(info) - 1):
+                    lay = h.level_layout(l)
+                    byt += 2 * lay["stored"] * (vb[mode] + lay["index_bytes"])
+                    if is_sa:
+                        byt += 2 * len(h.prolongator(l)[1]) * (vb[mode] + 4)
+                    else:
+                        byt += 2 * info[l][0] * (vb[mode] + 4)
+                its = statistics.median(m["iters"])
+                row[mode] = {"iters": its, "ms_per_solve": m["total_ms"] / 3, "solves_per_s": 3e3 / m["total_ms"],
+                             "vcycle_bytes": byt, "vcycle_bytes_x_iters": byt * its}
+            h.set_mode("fcg32")
+            row["setup_ms"] = h.setup_times()["total_ms"]
+            smoothed[name] = row
+        for name, h, is_sa in cands:
+            if is_sa:
+                h.close()
+
     # end to end through the C ABI with host buffers (pinned), copies inside the call
     pin_b = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
     pin_x = torch.zeros(prob.A.n, dtype=torch.float64).pin_memory().numpy()
@@ -775,6 +823,7 @@ def run_ours(args):
             "serving": serving,
             "refresh": refresh,
             "smoother": smoother,
+            "smoothed": smoothed,
             "fp64": {"value": solves / (f64_ms / 1e3), "unit": UNIT, "ms_per_step": f64_ms / args.steps,
                      "latency_ms": {"p50": pct(f64["lat_ms"], 50), "p99": pct(f64["lat_ms"], 99)},
                      "iters": statistics.median(f64["iters"]), "gpu_launches": f64["launches"]},
@@ -863,8 +912,41 @@ def run_large(args):
     return 0
 
 
+def run_serve_sweep(args):
+    """Serving over the resident 64^3 / 128^3 / 192^3 meshes (r = 1.04, warm
+    starts): saturated rates, an arrival-rate sweep with p50/p99 latency per
+    rate for the mixed batching server and the plain float64 server, and an
+    admission run under an 8 GB device budget."""
+    import torch
+    from paper_2210_16660_gb300 import serving as SV
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    meshes = SV.prepare_meshes(tuple(args.serve_sizes), ratio=args.ratio, seed=5, pool=4, device=device)
+    if not args.no_autotune:
+        for mm in meshes:
+            mm.amg.autotune(reps=10)
+    kw = dict(slots=args.serve_slots, max_engines=args.serve_engines, chunk=args.serve_chunk, rtol=args.rtol,
+              maxit=args.maxit, solo=not args.serve_no_solo, batch_min=args.serve_batch_min)
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = SV.serve_sweep(meshes, count=args.sweep_count, **kw)
+    clocks = sampler.stop()
+    line = {"metric": "serving: solves/s and p50/p99 latency (ms) per arrival rate, mixed batching server vs "
+                      "plain FP64 pcg_solve, rel.res 1e-8",
+            "config": {"meshes": [{"name": mm.name, "n": mm.problem.A.n, "coarse": mm.amg.coarse_info()["kind"]}
+                                  for mm in meshes],
+                       "arrivals": "Poisson, mesh uniform", "server": kw},
+            "clocks": clocks, **res}
+    print(json.dumps(line), flush=True)
+    for mm in meshes:
+        mm.amg.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.serve_sweep:
+        return run_serve_sweep(args)
     if args.large:
         return run_large(args)
     if args.impl == "reference":

@@ -105,6 +105,10 @@ typedef struct {
                          (30; 0 = 30) */
     double coarse_tol;/* iterative coarsest solve: stop at ||r|| <= coarse_tol ||b||, in
                          [0, 1) (1e-3; 0 = 1e-3) */
+    int smoothed;     /* 0: tentative prolongator P_hat (restriction and prolongation
+                         through the aggregate map); 1: smoothed aggregation,
+                         P = (I - omega D^-1 A) P_hat with omega = 1 / ||D^-1 A||_inf and
+                         D = diag(A), coarse matrices P^T A P (Sec. 3.1) (0) */
 } amg_params;
 
 /* Fill p with the defaults listed above. */
@@ -162,9 +166,12 @@ int amg_refresh(amg_handle h, const amg_csr *A, void *stream);
  * sweep give the values of the default. Re-forms every level's smoother
  * diagonal (and a float32 CSR copy of the level matrices for the sweeps);
  * the next solve recaptures its graph; the shared-memory cluster tail is not
- * used while nu > 0. Multi-column, batched and served solves run the l1-Jacobi
- * kernels only and return AMG_ERR_ARG for a handle with nu > 0; amg_autotune
- * returns AMG_OK without changes for it. Synchronises stream.
+ * used while nu > 0. In the float32 V-cycle, where a level's blocks divide
+ * its 32-row slices (and no row has more than 8 already-updated in-block
+ * entries), a sweep is one launch, one warp per slice; otherwise two. Single and batched solves take nu > 0;
+ * multi-column and served solves run the l1-Jacobi kernels only and return
+ * AMG_ERR_ARG for such a handle; amg_autotune returns AMG_OK without changes
+ * for it. Synchronises stream.
  * Errors: AMG_ERR_ARG (NULL, nu or nblocks out of range), AMG_ERR_OOM,
  * AMG_ERR_CUDA. */
 int amg_set_smoother(amg_handle h, int nu, int nblocks, void *stream);
@@ -385,6 +392,12 @@ int amg_level_layout(amg_handle h, int level, int *slice, int64_t *stored, int *
 
 /* Copy level l's matrix in CSR form to host buffers (row_ptr n+1, col/val nnz). */
 int amg_level_csr(amg_handle h, int level, int32_t *row_ptr, int32_t *col, double *val);
+
+/* Smoothed prolongator of level l (amg_params.smoothed = 1; AMG_ERR_ARG
+ * otherwise, and for the coarsest level) in CSR form, columns sorted: *nnz
+ * stored entries; row_ptr (n_l + 1), col and val (nnz) host buffers, each may
+ * be NULL (call with NULL arrays to size them). */
+int amg_level_prolongator(amg_handle h, int level, int64_t *nnz, int32_t *row_ptr, int32_t *col, double *val);
 
 /* Setup time split, milliseconds (host buffer of 4): total, matching,
  * Galerkin products, everything else. */

@@ -31,7 +31,7 @@ EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode
            "amg_serve_plan", "amg_server_create", "amg_server_mesh_info", "amg_server_info", "amg_server_submit",
            "amg_server_progress", "amg_server_result", "amg_server_destroy", "amg_autotune", "amg_level_shape",
            "amg_set_level_shape", "amg_profile_levels", "amg_refresh", "amg_refresh_time", "amg_set_smoother",
-           "amg_coarse_info", "amg_coarse_factors", "amg_coarse_solve")
+           "amg_coarse_info", "amg_coarse_factors", "amg_coarse_solve", "amg_level_prolongator")
 
 
 class AmgCsr(C.Structure):
@@ -42,7 +42,7 @@ class AmgCsr(C.Structure):
 class AmgParams(C.Structure):
     _fields_ = [("coarse_max", C.c_int), ("n_pass", C.c_int), ("max_levels", C.c_int), ("mode", C.c_int),
                 ("hbm_budget", C.c_size_t), ("coarse_solver", C.c_int), ("coarse_maxit", C.c_int),
-                ("coarse_tol", C.c_double)]
+                ("coarse_tol", C.c_double), ("smoothed", C.c_int)]
 
 
 class ServerParams(C.Structure):
@@ -97,6 +97,8 @@ def load(build_if_missing: bool = True):
     lib.amg_refresh_time.restype = I
     lib.amg_set_smoother.argtypes = [P, I, I, P]
     lib.amg_set_smoother.restype = I
+    lib.amg_level_prolongator.argtypes = [P, I, C.POINTER(C.c_int64), P, P, P]
+    lib.amg_level_prolongator.restype = I
     lib.amg_coarse_info.argtypes = [P, C.POINTER(I), C.POINTER(I), C.POINTER(I)]
     lib.amg_coarse_info.restype = I
     lib.amg_coarse_factors.argtypes = [P, P]
@@ -252,7 +254,7 @@ class AMG:
 
     def __init__(self, row_ptr, col, val, n: int | None = None, coarse_max: int = 200, n_pass: int = 2,
                  max_levels: int = 30, mode: str = "pcg64", hbm_budget: int = 0, stream=None,
-                 coarse: str = "auto", coarse_maxit: int = 30, coarse_tol: float = 1e-3):
+                 coarse: str = "auto", coarse_maxit: int = 30, coarse_tol: float = 1e-3, smoothed: bool = False):
         lib = load()
         rp, rp_dev = _ptr(row_ptr, np.int32)
         ci, ci_dev = _ptr(col, np.int32)
@@ -267,6 +269,7 @@ class AMG:
         prm.coarse_max, prm.n_pass, prm.max_levels = coarse_max, n_pass, max_levels
         prm.mode, prm.hbm_budget = _MODES[mode], hbm_budget
         prm.coarse_solver, prm.coarse_maxit, prm.coarse_tol = _COARSE[coarse], coarse_maxit, coarse_tol
+        prm.smoothed = int(bool(smoothed))
         h = C.c_void_p()
         st = lib.amg_setup(C.byref(csr), C.byref(prm), _stream_ptr(stream), C.byref(h))
         if st:
@@ -435,6 +438,22 @@ class AMG:
         if st:
             raise AmgError(st, last_error())
         return float(norms[0]), float(norms[1])
+
+    def prolongator(self, level: int):
+        """``amg_level_prolongator``: the smoothed P of a level as CSR parts."""
+        lib = load()
+        nz = C.c_int64()
+        st = lib.amg_level_prolongator(self._h, level, C.byref(nz), None, None, None)
+        if st:
+            raise AmgError(st, last_error())
+        n = self.info()[level][0]
+        rp = np.empty(n + 1, np.int32)
+        ci = np.empty(max(nz.value, 1), np.int32)
+        v = np.empty(max(nz.value, 1))
+        st = lib.amg_level_prolongator(self._h, level, C.byref(nz), rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+        if st:
+            raise AmgError(st, last_error())
+        return rp, ci[: nz.value], v[: nz.value]
 
     def coarse_info(self) -> dict:
         """``amg_coarse_info``: the coarsest solver in use ("dense"/"iter"),

@@ -105,10 +105,6 @@ int amg_batch_create(int m, const amg_handle *hs, amg_batch *out) {
             set_error("amg_batch_create: handle %d is NULL", i);
             return AMG_ERR_ARG;
         }
-        if (hs[i]->gs_nu) {
-            set_error("amg_batch_create: handle %d smooths by Gauss-Seidel (batches run the l1-Jacobi sweeps)", i);
-            return AMG_ERR_ARG;
-        }
         for (int j = 0; j < i; j++)
             if (hs[j] == hs[i]) {
                 set_error("amg_batch_create: handle %d appears twice (each system needs its own handle)", i);
@@ -152,8 +148,8 @@ int pcg_solve_batch(amg_batch b, const double *const *B, double *const *X, doubl
             set_error("pcg_solve_batch: NULL vector for system %d", i);
             return AMG_ERR_ARG;
         }
-        if (h->invalid || h->gs_nu) {
-            set_error("pcg_solve_batch: system %d: its last amg_refresh failed, or it smooths by Gauss-Seidel", i);
+        if (h->invalid) {
+            set_error("pcg_solve_batch: system %d: its last amg_refresh failed", i);
             return AMG_ERR_ARG;
         }
         h->mem.stream = s;

@@ -217,8 +217,9 @@ int amg_set_level_shape(amg_handle h, int level, const int *shape) {
         return AMG_ERR_ARG;
     }
     for (int i = 0; i < 4; i++)
-        if (shape[i] < 0 || shape[i] > 7) {
-            set_error("amg_set_level_shape: shape values are 0..7");
+        if (shape[i] < 0 || shape[i] > 7 || (h->smoothed && (shape[i] & 4))) {
+            set_error("amg_set_level_shape: shape values are 0..7 (0..3 with smoothed aggregation: the fused "
+                      "shapes transfer through the aggregate map)");
             return AMG_ERR_ARG;
         }
     for (int p = 0; p < 2; p++)
@@ -241,9 +242,10 @@ int amg_level_shape(amg_handle h, int level, int *shape) {
 int pcg_solve_multi(amg_handle h, int k, const double *B, double *X, double rtol, int maxit, int *iters,
                     double *res_hist, void *stream) {
     set_error("");
-    if (!h || h->invalid || h->gs_nu) {
-        set_error("pcg_solve_multi: NULL handle, its last amg_refresh failed, or it smooths by Gauss-Seidel "
-                  "(the multi-column kernels implement the l1-Jacobi sweeps only)");
+    if (!h || h->invalid || !gs_multi_ok(h) || h->smoothed) {
+        set_error("pcg_solve_multi: NULL handle, its last amg_refresh failed, it smooths by Gauss-Seidel with "
+                  "blocks the one-warp sweeps cannot take (block sizes must divide 32), or it uses smoothed "
+                  "aggregation (the multi-column kernels implement the tentative transfers only)");
         return AMG_ERR_ARG;
     }
     return solve_multi_impl(h, k, B, X, rtol, maxit, iters, res_hist, (cudaStream_t)stream);
@@ -326,6 +328,20 @@ int amg_level_csr(amg_handle h, int level, int32_t *row_ptr, int32_t *col, doubl
     if (row_ptr) PCG_CK(cudaMemcpy(row_ptr, a.rp, sizeof(int32_t) * ((size_t)a.n + 1), cudaMemcpyDeviceToHost));
     if (col) PCG_CK(cudaMemcpy(col, a.ci, sizeof(int32_t) * a.nnz, cudaMemcpyDeviceToHost));
     if (val) PCG_CK(cudaMemcpy(val, a.v, sizeof(double) * a.nnz, cudaMemcpyDeviceToHost));
+    return AMG_OK;
+}
+
+int amg_level_prolongator(amg_handle h, int level, int64_t *nnz, int32_t *row_ptr, int32_t *col, double *val) {
+    set_error("");
+    if (!h || !h->smoothed || level < 0 || level + 1 >= (int)h->lev.size()) {
+        set_error("amg_level_prolongator: bad handle or level, or the handle uses the tentative prolongator");
+        return AMG_ERR_ARG;
+    }
+    const DevCSR &P = h->lev[level].P;
+    if (nnz) *nnz = P.nnz;
+    if (row_ptr) PCG_CK(cudaMemcpy(row_ptr, P.rp, sizeof(int32_t) * ((size_t)P.n + 1), cudaMemcpyDeviceToHost));
+    if (col) PCG_CK(cudaMemcpy(col, P.ci, sizeof(int32_t) * P.nnz, cudaMemcpyDeviceToHost));
+    if (val) PCG_CK(cudaMemcpy(val, P.v, sizeof(double) * P.nnz, cudaMemcpyDeviceToHost));
     return AMG_OK;
 }
 

@@ -134,6 +134,15 @@ struct Level {
     int32_t *rptr = nullptr;  // members of each coarse row: rptr[nc+1], ridx[...]
     int32_t *ridx = nullptr;
     float *v32csr = nullptr;  // float32 copy of A.v (CSR order), for the Gauss-Seidel sweeps
+    // smoothed aggregation (amg_params.smoothed): the explicit prolongator P
+    // (n_l x n_{l+1}, columns sorted) and its transpose Pt (rows of each
+    // column in increasing order), float64 and float32 values; ones64/ones32
+    // stand in for the tentative weight in the down sweep, which then leaves
+    // the plain residual b - A xpre for the restriction by P^T
+    DevCSR P, Pt;
+    float *P32 = nullptr, *Pt32 = nullptr;
+    double *ones64 = nullptr;
+    float *ones32 = nullptr;
     // two-phase Gauss-Seidel sweeps (blocks of at most 32 rows): for the
     // forward [0] and backward [1] pass, each row's in-block entries that the
     // pass has already updated (j < r in the block, resp. j > r), width
@@ -273,6 +282,7 @@ struct amg_hier {
     // when coarse_iter = 1; the V-cycle is then not a fixed operator and
     // both modes run the flexible FCG(1) recurrence
     int coarse_iter = 0;
+    int smoothed = 0;         // smoothed-aggregation prolongators (amg_params.smoothed)
     pcgamg::CoarseIter cit;
     pcgamg::CoarseWS cws;
     double *bL = nullptr;     // coarsest right-hand side in float64
@@ -318,6 +328,7 @@ struct amg_hier {
     // gs_nu sweeps of l1 hybrid Gauss-Seidel over gs_blocks row blocks per
     // level (amg_set_smoother)
     int gs_nu = 0, gs_blocks = 0;
+    int gs_fused = 1;  // one-launch warp sweeps where the blocks fit the slices (PCGAMG_GS_FUSED=0: off)
     double refresh_ms = 0;  // host time of the last amg_refresh
     int use_graph = 1;
     int no_col16 = 0;
@@ -362,6 +373,7 @@ int solve_launch(amg_hier *h, int mode, const double *b, const double *x0, doubl
 int solve_collect(amg_hier *h, int mode, double *x, cudaStream_t s, int *status, int *iters, double *true_rel,
                   int64_t *kernels);
 int mws_alloc(amg_hier *h, Mem &M, MultiWS &W, int K, int hist_cap, int which);
+bool gs_multi_ok(const amg_hier *h);
 void mws_free(Mem &M, MultiWS &W);
 size_t mws_bytes(amg_hier *h, int K, int hist_cap, int which);
 int mws_reset(MultiWS &W, int mode, double rtol, int maxit, cudaStream_t s);
@@ -371,6 +383,9 @@ int mws_iterate(amg_hier *h, MultiWS &W, int mode, int iterations, cudaStream_t 
 int capture_solve_prefix(amg_hier *h, int mode, cudaStream_t cs, PendingBody *pb, int *prefix_k);
 int capture_solve_body(const PendingBody &pb, cudaStream_t s, int *body_k);
 int ensure_hist(amg_hier *h, int maxit);
+int scan_counts(Mem &M, const int32_t *in, int32_t *out, int64_t n, int32_t *total_host, cudaStream_t s);
+// smoothed aggregation (csrc/smoothed.cu)
+int build_smoothed(amg_hier *h, Level &lv, int nc, DevCSR *out, cudaStream_t s);
 // iterative coarsest solve (csrc/coarse.cu)
 int coarse_iter_build(amg_hier *h, cudaStream_t s);
 int cws_alloc(amg_hier *h, Mem &M, CoarseWS &W, int K);

@@ -392,6 +392,161 @@ __global__ void __launch_bounds__(kMB) k_post_m(int n, const int32_t *__restrict
     }
 }
 
+// ------------------------------------------------------------ hybrid Gauss-Seidel
+// One sweep of the l1 hybrid Gauss-Seidel smoother for K columns (the
+// single-column k_gs_warp per column group): one warp per (32-row slice,
+// group of V columns), a lane per row. Phase one sums each row's entries with
+// x_old except the in-block ones this pass has already updated; phase two
+// runs the slice's rows in pass order in 32 steps, each finished value
+// broadcast by a shuffle and added by the rows whose next in-block entry (in
+// pass order) is that row. Needs blocks whose size divides 32 and rows with
+// at most kGsPartM in-block entries of the pass.
+constexpr int kGsPartM = 8;
+
+template <typename T, typename IDX, int U, bool FWD, bool ZERO, bool STREAM, int K>
+__global__ void __launch_bounds__(kMB) k_gs_warp_m(int n, int nb, int w, const int32_t *__restrict__ sptr,
+                                                  const IDX *__restrict__ col, const T *__restrict__ val,
+                                                  const int32_t *__restrict__ pci, const T *__restrict__ pv,
+                                                  const T *__restrict__ dinv, const T *__restrict__ b,
+                                                  const T *__restrict__ xo, T *__restrict__ xn,
+                                                  const CtlM *__restrict__ ctl) {
+    constexpr int V = VW<T>::V;
+    constexpr int G = K / V;
+    if (ctl->done) return;
+    const int lane = threadIdx.x & 31;
+    const int nsl = (n + 31) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < (int64_t)nsl * G; wi += nw) {
+        const int sl = (int)(wi / G), c0 = (int)(wi % G) * V;
+        if (!group_live<V>(ctl, c0)) continue;  // uniform over the warp
+        const int i = (sl << 5) + lane;
+        const bool valid = i < n;
+        const int64_t e0 = (int64_t)i * K + c0;
+        T acc[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = 0;
+        if (!ZERO && valid) {
+            const int lo = (i / nb) * nb, hi = min(n, lo + nb);
+            int32_t base = ldg(sptr + sl);
+            int wd = (ldg(sptr + sl + 1) - base) >> 5;
+            sell_row_vec<U, STREAM, V>(col + base + lane, val + base + lane, wd, i,
+                                       [&](int j, T (&x)[V]) {
+                                           bool done = FWD ? (j >= lo && j < i) : (j > i && j < hi);
+                                           if (done) {
+#pragma unroll
+                                               for (int v = 0; v < V; v++) x[v] = 0;
+                                           } else {
+                                               ld_vec<T, V>(xo + (int64_t)j * K + c0, x);
+                                           }
+                                       },
+                                       acc);
+        }
+        int rj[kGsPartM];
+        T ra[kGsPartM];
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kGsPartM; k++) {
+            bool ok = valid && k < w;
+            rj[k] = ok ? ldg(pci + (int64_t)i * w + k) : -1;
+            ra[k] = ok ? ldg(pv + (int64_t)i * w + k) : T(0);
+            cnt += rj[k] >= 0 ? 1 : 0;
+        }
+        int pj[kGsPartM];
+        T pa[kGsPartM];
+#pragma unroll
+        for (int k = 0; k < kGsPartM; k++) {
+            if (FWD) {
+                pj[k] = rj[k];
+                pa[k] = ra[k];
+            } else {
+                pj[k] = -1;
+                pa[k] = T(0);
+#pragma unroll
+                for (int m = 0; m < kGsPartM; m++)
+                    if (m == cnt - 1 - k) {
+                        pj[k] = rj[m];
+                        pa[k] = ra[m];
+                    }
+            }
+        }
+        T bv[V], xold[V], x[V];
+        const T di = valid ? ldg(dinv + i) : T(0);
+#pragma unroll
+        for (int v = 0; v < V; v++) bv[v] = xold[v] = x[v] = 0;
+        if (valid) {
+            ld_vec<T, V>(b + e0, bv);
+            if (!ZERO) ld_vec<T, V>(xo + e0, xold);
+        }
+#pragma unroll 2
+        for (int step = 0; step < 32; step++) {
+            const int t = FWD ? step : 31 - step;
+            if (lane == t)
+#pragma unroll
+                for (int v = 0; v < V; v++) x[v] = ZERO ? di * (bv[v] - acc[v]) : xold[v] + di * (bv[v] - acc[v]);
+            T xt[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) xt[v] = __shfl_sync(0xffffffffu, x[v], t);
+            if (pj[0] == (sl << 5) + t) {
+#pragma unroll
+                for (int v = 0; v < V; v++) acc[v] += pa[0] * xt[v];
+#pragma unroll
+                for (int k = 0; k + 1 < kGsPartM; k++) {
+                    pj[k] = pj[k + 1];
+                    pa[k] = pa[k + 1];
+                }
+                pj[kGsPartM - 1] = -1;
+            }
+        }
+        if (valid) st_vec<T, V>(xn + e0, x);
+    }
+}
+
+// Level 0 after the Gauss-Seidel post-smoothing: z = x (widened), r.z and
+// (FCG) z.q_old per column; the last block forms rho and beta per column.
+template <typename T, bool FCG, int K>
+__global__ void __launch_bounds__(kMB) k_gs_finish0_m(int n, const T *__restrict__ x, const double *__restrict__ r64,
+                                                     const double *__restrict__ qold, double *__restrict__ z,
+                                                     double *partials, CtlM *ctl) {
+    constexpr int V = VW<T>::V;
+    if (ctl->done) return;
+    double rz[V], zq[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) rz[v] = zq[v] = 0.0;
+    MK_LIVE(V)
+    MK_FOR(live_ ? n : 0, V) {
+        MK_IDX(V)
+        T xv[V];
+        ld_vec<T, V>(x + e0, xv);
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            double zo = (double)xv[v];
+            z[e0 + v] = zo;
+            rz[v] += ldg(r64 + e0 + v) * zo;
+            if (FCG) zq[v] += zo * ldg(qold + e0 + v);
+        }
+    }
+    __shared__ double res[2 * kMaxK];
+    if (publish_cols<K, V>(rz, zq, partials, &ctl->counter[0])) {
+        final_cols<K>(partials, res);
+        if (threadIdx.x == 0) ctl->counter[0] = 0;
+        int c = threadIdx.x;
+        if (c < K && ctl->active[c]) {
+            double rho = res[c], zqc = res[K + c];
+            if (!isfinite(rho) || !isfinite(zqc)) {
+                col_fail(ctl, c, AMG_ERR_NAN);
+            } else if (!(rho > 0.0)) {
+                col_fail(ctl, c, AMG_ERR_BREAKDOWN);
+            } else {
+                ctl->rho[c] = rho;
+                double beta = 0.0;
+                if (!ctl->restart[c])
+                    beta = ctl->mode == AMG_MODE_FCG32 || ctl->flex ? -zqc / ctl->pq_old[c] : rho / ctl->rho_old[c];
+                ctl->beta[c] = beta;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ Krylov
 template <int K>
 __global__ void __launch_bounds__(kMB) k_axpy_m(int n, const double *__restrict__ z, double *__restrict__ p,
@@ -668,6 +823,7 @@ struct MP<float> {
     static float *t(MultiLevel &m) { return m.t32; }
     static float *xpre(MultiLevel &m) { return m.xpre32; }
     static float *xp(MultiLevel &m) { return m.xp32; }
+    static const float *part(const Level &l, int d) { return l.gs_v32[d]; }
 };
 template <>
 struct MP<double> {
@@ -679,6 +835,7 @@ struct MP<double> {
     static double *t(MultiLevel &m) { return m.t64; }
     static double *xpre(MultiLevel &m) { return m.xpre64; }
     static double *xp(MultiLevel &m) { return m.xp64; }
+    static const double *part(const Level &l, int d) { return l.gs_v64[d]; }
 };
 
 #define WITH_COLS_M(S, BODY)              \
@@ -693,6 +850,47 @@ struct MP<double> {
             BODY;                         \
         }                                 \
     } while (0)
+
+// gs_nu Gauss-Seidel sweeps of level l for K columns: pre-smoothing
+// (forward, from zero, into the level's xpre) or post-smoothing (backward,
+// from xp, into x); sweeps alternate between the target and t so the last
+// writes the target.
+template <typename T, int K>
+void launch_gs_m(amg_hier *h, MultiWS &W, int l, bool pre, const T *b, T *target, cudaStream_t s) {
+    using P = MP<T>;
+    constexpr int V = VW<T>::V;
+    Level &lv = h->lev[l];
+    MultiLevel &mv = W.lev[l];
+    const int n = lv.A.n, nu = h->gs_nu, nb = gs_rows(n, h->gs_blocks), d = pre ? 0 : 1;
+    const int w = lv.gs_w[d];
+    const int grid = grid_of((((int64_t)n + 31) / 32) * (K / V) * 32);
+    const T *src = pre ? nullptr : (const T *)P::xp(mv);
+    const bool big = n > kSmallRows;
+    for (int sw = 1; sw <= nu; sw++) {
+        T *dst = (nu - sw) % 2 == 0 ? target : P::t(mv);
+        const bool zero = pre && sw == 1;
+#define PCG_GSM(UU, ST)                                                                                          \
+    do {                                                                                                         \
+        if (zero)                                                                                                \
+            WITH_COLS_M(lv.S, (k_gs_warp_m<T, IDX, UU, true, true, ST, K><<<grid, kMB, 0, s>>>(                  \
+                                  n, nb, w, lv.S.sptr, cols, P::val(lv), lv.gs_ci[d], P::part(lv, d), P::dinv(lv), \
+                                  b, src, dst, W.ctl)));                                                         \
+        else if (pre)                                                                                            \
+            WITH_COLS_M(lv.S, (k_gs_warp_m<T, IDX, UU, true, false, ST, K><<<grid, kMB, 0, s>>>(                 \
+                                  n, nb, w, lv.S.sptr, cols, P::val(lv), lv.gs_ci[d], P::part(lv, d), P::dinv(lv), \
+                                  b, src, dst, W.ctl)));                                                         \
+        else                                                                                                     \
+            WITH_COLS_M(lv.S, (k_gs_warp_m<T, IDX, UU, false, false, ST, K><<<grid, kMB, 0, s>>>(                \
+                                  n, nb, w, lv.S.sptr, cols, P::val(lv), lv.gs_ci[d], P::part(lv, d), P::dinv(lv), \
+                                  b, src, dst, W.ctl)));                                                         \
+    } while (0)
+        if (l == 0) PCG_GSM(kUnroll, true);
+        else if (big) PCG_GSM(kUnroll, false);
+        else PCG_GSM(kUnrollSmall, false);
+#undef PCG_GSM
+        src = dst;
+    }
+}
 
 template <typename T, bool FCG, int K>
 int launch_vcycle_m(amg_hier *h, MultiWS &W, cudaStream_t s) {
@@ -713,12 +911,15 @@ int launch_vcycle_m(amg_hier *h, MultiWS &W, cudaStream_t s) {
         set_error("pcg_solve_multi: single-level hierarchy not supported by the multi-column path");
         return AMG_ERR_ARG;
     }
+    const bool gs = h->gs_nu > 0;
+    if (gs) launch_gs_m<T, K>(h, W, 0, true, b0, P::xpre(m0), s);
     WITH_COLS_M(l0.S, (k_down_m<T, IDX, K, kUnroll, true><<<g0, kMB, 0, s>>>(
                           l0.A.n, l0.S.sptr, cols, P::val(l0), P::xpre(m0), b0, P::p(l0), P::t(m0), ctl)));
     for (int l = 0; l < L; l++) {
         Level &lv = lev[l];
         MultiLevel &mv = W.lev[l];
         int n = lv.A.n;
+        if (l > 0 && gs) launch_gs_m<T, K>(h, W, l, true, P::b(mv), P::xpre(mv), s);
         if (l > 0)
             WITH_COLS_M(lv.S, (k_down_m<T, IDX, K, kUnroll, false><<<gv(n), kMB, 0, s>>>(
                                   n, lv.S.sptr, cols, P::val(lv), P::xpre(mv), P::b(mv), P::p(lv), P::t(mv), ctl)));
@@ -741,12 +942,22 @@ int launch_vcycle_m(amg_hier *h, MultiWS &W, cudaStream_t s) {
         int n = lv.A.n;
         k_prolong_m<T, K><<<gv(n), kMB, 0, s>>>(n, P::xpre(mv), P::p(lv), lv.agg,
                                                                   P::x(W.lev[l + 1]), P::xp(mv), ctl);
+        if (gs) {
+            launch_gs_m<T, K>(h, W, l, false, P::b(mv), P::x(mv), s);
+            continue;
+        }
         WITH_COLS_M(lv.S, (k_post_m<T, T, false, false, IDX, K, kUnroll, false>
                            <<<gv(n), kMB, 0, s>>>(n, lv.S.sptr, cols, P::val(lv), P::xp(mv),
                                                                     P::b(mv), P::dinv(lv), P::x(mv), nullptr,
                                                                     nullptr, nullptr, ctl)));
     }
     k_prolong_m<T, K><<<g0, kMB, 0, s>>>(l0.A.n, P::xpre(m0), P::p(l0), l0.agg, P::x(W.lev[1]), P::xp(m0), ctl);
+    if (gs) {
+        launch_gs_m<T, K>(h, W, 0, false, b0, P::x(m0), s);
+        k_gs_finish0_m<T, FCG, K><<<g0, kMB, 0, s>>>(l0.A.n, (const T *)P::x(m0), W.r, W.q, W.z, W.partials, ctl);
+        PCG_LAUNCH_CK();
+        return AMG_OK;
+    }
     WITH_COLS_M(l0.S, (k_post_m<T, double, true, FCG, IDX, K, kUnroll, true><<<g0, kMB, 0, s>>>(
                           l0.A.n, l0.S.sptr, cols, P::val(l0), P::xp(m0), b0, P::dinv(l0), W.z, W.r, W.q,
                           W.partials, ctl)));
@@ -973,6 +1184,21 @@ int solve_multi_k(amg_hier *h, int k, const double *B, double *X, double rtol, i
 }
 
 }  // namespace
+
+// Whether the multi-column kernels can smooth h by Gauss-Seidel: every level
+// with sweeps has blocks whose size divides 32 and at most kGsPartM
+// already-updated in-block entries per row in each pass (one-warp sweeps).
+bool gs_multi_ok(const amg_hier *h) {
+    if (h->gs_nu <= 0) return true;
+    for (size_t l = 0; l + 1 < h->lev.size(); l++) {
+        const Level &lv = h->lev[l];
+        int nb = gs_rows(lv.A.n, h->gs_blocks);
+        if (nb > 32 || 32 % nb) return false;
+        for (int d = 0; d < 2; d++)
+            if (lv.gs_w[d] < 0 || lv.gs_w[d] > kGsPartM) return false;
+    }
+    return true;
+}
 
 // Allocates a K-column workspace; which: 1 float32 V-cycle vectors,
 // 2 float64 V-cycle vectors, 3 both.

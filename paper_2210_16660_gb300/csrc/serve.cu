@@ -386,8 +386,10 @@ int amg_server_create(const amg_server_params *p, int m, const amg_handle *meshe
             set_error("amg_server_create: mesh %d is NULL", i);
             return AMG_ERR_ARG;
         }
-        if (meshes[i]->gs_nu) {
-            set_error("amg_server_create: mesh %d smooths by Gauss-Seidel (engines run the l1-Jacobi sweeps)", i);
+        if (!gs_multi_ok(meshes[i]) || meshes[i]->smoothed) {
+            set_error("amg_server_create: mesh %d smooths by Gauss-Seidel with blocks the engines cannot take "
+                      "(block sizes must divide 32), or uses smoothed aggregation (engines run the tentative "
+                      "transfers)", i);
             return AMG_ERR_ARG;
         }
         if (meshes[i]->lev.size() < 2) {
@@ -493,8 +495,9 @@ int amg_server_submit(amg_server sv, int mesh, const double *b, const double *x0
                   mesh);
         return AMG_ERR_OOM;
     }
-    if (sv->meshes[mesh]->invalid || sv->meshes[mesh]->gs_nu) {
-        set_error("amg_server_submit: mesh %d: its last amg_refresh failed, or it smooths by Gauss-Seidel", mesh);
+    if (sv->meshes[mesh]->invalid || !gs_multi_ok(sv->meshes[mesh]) || sv->meshes[mesh]->smoothed) {
+        set_error("amg_server_submit: mesh %d: its last amg_refresh failed, or its smoother or prolongator "
+                  "changed to one the engines cannot take", mesh);
         return AMG_ERR_ARG;
     }
     if (sv->queued >= sv->prm.queue_cap) {

@@ -928,6 +928,12 @@ int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
     if (!coarsest) {
         PCG_TRY(alloc(M, &lv.p32, n));
         k_to_f32<<<grid_for(n), kBlock, 0, s>>>(lv.p, lv.p32, n);
+        if (h->smoothed) {
+            PCG_TRY(alloc(M, &lv.ones64, n));
+            PCG_TRY(alloc(M, &lv.ones32, n));
+            k_fill<double><<<grid_for(n), kBlock, 0, s>>>(lv.ones64, n, 1.0);
+            k_fill<float><<<grid_for(n), kBlock, 0, s>>>(lv.ones32, n, 1.0f);
+        }
         // members of each coarse row, increasing fine index
         int32_t *cnt = nullptr, *cur = nullptr;
         PCG_TRY(alloc(M, &cnt, lv.nc));
@@ -952,6 +958,11 @@ int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
 
 }  // namespace
 
+// Exclusive prefix sum of n int32 counts into out[0..n], total to the host.
+int scan_counts(Mem &M, const int32_t *in, int32_t *out, int64_t n, int32_t *total_host, cudaStream_t s) {
+    return scan_exclusive(M, in, out, n, total_host, s);
+}
+
 int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_t s) {
     double t_begin = now_ms(), t_match = 0, t_rap = 0;
     Mem &M = h->mem;
@@ -959,6 +970,7 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
     M.budget = prm->hbm_budget;
     h->prm = *prm;
     h->mode = prm->mode;
+    h->smoothed = prm->smoothed ? 1 : 0;
     // PCGAMG_GRAPH=0 launches each solve kernel on the stream instead of
     // replaying the whole-solve graph (same kernels; for profilers).
     const char *g = getenv("PCGAMG_GRAPH");
@@ -968,6 +980,9 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
     if (c16 && c16[0] == '0') h->no_col16 = 1;
     const char *pd = getenv("PCGAMG_PDL");
     if (pd && pd[0] == '0') h->pdl = 0;
+    // PCGAMG_GS_FUSED=0 keeps the two-launch Gauss-Seidel sweeps everywhere.
+    const char *gf = getenv("PCGAMG_GS_FUSED");
+    if (gf && gf[0] == '0') h->gs_fused = 0;
     if (!A || A->n <= 0 || A->n >= (int64_t)1 << 31 || A->nnz < A->n || A->nnz >= (int64_t)1 << 31 ||
         !A->row_ptr || !A->col || !A->val) {
         set_error("amg_setup: bad CSR sizes or NULL arrays");
@@ -976,6 +991,7 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
     if (prm->n_pass < 1 || prm->n_pass > kMaxPass || prm->coarse_max < 1 || prm->max_levels < 1 ||
         (prm->mode != AMG_MODE_PCG64 && prm->mode != AMG_MODE_FCG32) || prm->coarse_solver < AMG_COARSE_AUTO ||
         prm->coarse_solver > AMG_COARSE_ITER || prm->coarse_maxit < 0 || prm->coarse_maxit > 1000 ||
+        prm->smoothed < 0 || prm->smoothed > 1 ||
         !(prm->coarse_tol >= 0.0 && prm->coarse_tol < 1.0)) {
         set_error("amg_setup: bad parameters");
         return AMG_ERR_ARG;
@@ -1067,6 +1083,16 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
         lv.agg = cagg;
         lv.p = cp;
         lv.nc = nc;
+        if (h->smoothed) {
+            // P = (I - omega D^-1 A) P_hat and A_{l+1} = P^T A P replace the
+            // passes' tentative product (which only fed their matchings)
+            double t0 = now_ms();
+            DevCSR ac;
+            PCG_TRY(build_smoothed(h, lv, nc, &ac, s));
+            free_csr(M, cur);
+            cur = ac;
+            t_rap += now_ms() - t0;
+        }
         h->lev.emplace_back();
         Level &nx = h->lev[l + 1];
         nx.A = cur;
@@ -1195,6 +1221,16 @@ int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s) {
     int L = (int)h->lev.size() - 1;
     for (int l = 0; l < L; l++) {
         Level &lv = h->lev[l];
+        if (h->smoothed) {
+            // P and A_{l+1} = P^T A P formed again on their kept patterns
+            // from the kept map and weight (which do not depend on values)
+            int st = build_smoothed(h, lv, h->lev[l + 1].A.n, &h->lev[l + 1].A, s);
+            if (st) {
+                release(M, dflag);
+                return st;
+            }
+            continue;
+        }
         DevCSR cur = lv.A;
         double *curw = lv.w;
         bool own = false;

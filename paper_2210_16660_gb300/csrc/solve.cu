@@ -205,6 +205,40 @@ __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t *__re
     if (PRE) xprec[I] = ldg(dinvc + I) * s;
 }
 
+// Smoothed aggregation: b_c[I] = sum over the rows i of P's column I
+// (increasing i) of P_iI res_i, res = b - A xpre left by the down sweep
+// (launched with unit weights); PRE also forms xpre_c = dinv_c b_c.
+template <typename T, typename TO, bool PRE>
+__global__ void __launch_bounds__(kBlock) k_restrict_sa(int nc, const int32_t *__restrict__ trp,
+                                                        const int32_t *__restrict__ tri, const T *__restrict__ tv,
+                                                        const T *__restrict__ res, TO *__restrict__ bc,
+                                                        const T *__restrict__ dinvc, T *__restrict__ xprec,
+                                                        const Ctl *__restrict__ ctl) {
+    pdl_enter();
+    if (ctl->done) return;
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    T s = 0;
+    for (int32_t q = ldg(trp + I); q < ldg(trp + I + 1); q++) s += ldg(tv + q) * ldg(res + ldg(tri + q));
+    bc[I] = (TO)s;
+    if (PRE) xprec[I] = ldg(dinvc + I) * s;
+}
+
+// Smoothed aggregation: xp_i = xpre_i + sum over row i of P of P_iJ xc_J.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_prolong_sa(int n, const int32_t *__restrict__ prp,
+                                                       const int32_t *__restrict__ pci, const T *__restrict__ pv,
+                                                       const T *__restrict__ xpre, const T *__restrict__ xc,
+                                                       T *__restrict__ xp, const Ctl *__restrict__ ctl) {
+    pdl_enter();
+    if (ctl->done) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T s = 0;
+        for (int32_t q = ldg(prp + i); q < ldg(prp + i + 1); q++) s += ldg(pv + q) * ldg(xc + ldg(pci + q));
+        xp[i] = ldg(xpre + i) + s;
+    }
+}
+
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
@@ -362,6 +396,90 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_block(int n, int nb, int w, c
             x = ldg(xo + r) + ldg(dinv + r) * (ldg(b + r) - sum);
         wv[r - lo] = x;
         xn[r] = x;
+    }
+}
+
+// Both phases of a sweep in one warp per 32-row slice, for blocks whose size
+// divides 32 (so no block crosses a slice) and rows with at most kGsPart
+// already-updated in-block entries. Phase one as in k_gs_offsum, one lane per
+// row; phase two over the slice in 32 steps in pass order (FWD: rows
+// increasing, else decreasing): at step t lane t finishes its row,
+// x_t = x_old_t + d_t (b_t - acc_t), the value is broadcast by a shuffle, and
+// every lane whose next in-block entry (in pass order) is column t adds
+// a_rt x_t to its acc. Blocks of fewer rows run side by side in the same
+// steps. Same values as k_gs_block up to the order of the sums.
+constexpr int kGsPartMax = 8;
+
+template <typename T, typename IDX, int U, bool FWD, bool ZERO, bool STREAM>
+__global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_gs_warp(
+    int n, int nb, int w, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
+    const int32_t *__restrict__ pci, const T *__restrict__ pv, const T *__restrict__ dinv, const T *__restrict__ b,
+    const T *__restrict__ xo, T *__restrict__ xn, const Ctl *__restrict__ ctl) {
+    pdl_enter();
+    if (ctl->done) return;
+    const int lane = threadIdx.x & 31;
+    const int nsl = (n + 31) >> 5;
+    const int wstride = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    for (int sl = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); sl < nsl; sl += wstride) {
+        const int i = (sl << 5) + lane;
+        const bool valid = i < n;
+        T acc = 0;
+        if (!ZERO && valid) {
+            const int lo = (i / nb) * nb, hi = min(n, lo + nb);
+            SELL_ROW_BEGIN
+            acc = sell_row<U, STREAM>(c_, a_, w_, i, [&](int j) {
+                bool done = FWD ? (j >= lo && j < i) : (j > i && j < hi);
+                return done ? T(0) : ldg(xo + j);
+            });
+        }
+        // the row's in-block entries in pass order (padding -1 never matches)
+        int rj[kGsPartMax];
+        T ra[kGsPartMax];
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kGsPartMax; k++) {
+            bool ok = valid && k < w;
+            rj[k] = ok ? ldg(pci + (int64_t)i * w + k) : -1;
+            ra[k] = ok ? ldg(pv + (int64_t)i * w + k) : T(0);
+            cnt += rj[k] >= 0 ? 1 : 0;
+        }
+        int pj[kGsPartMax];
+        T pa[kGsPartMax];
+#pragma unroll
+        for (int k = 0; k < kGsPartMax; k++) {
+            if (FWD) {
+                pj[k] = rj[k];
+                pa[k] = ra[k];
+            } else {
+                pj[k] = -1;
+                pa[k] = T(0);
+#pragma unroll
+                for (int m = 0; m < kGsPartMax; m++)
+                    if (m == cnt - 1 - k) {
+                        pj[k] = rj[m];
+                        pa[k] = ra[m];
+                    }
+            }
+        }
+        const T bi = valid ? ldg(b + i) : T(0), di = valid ? ldg(dinv + i) : T(0);
+        const T xold = (!ZERO && valid) ? ldg(xo + i) : T(0);
+        T x = 0;
+#pragma unroll 4
+        for (int step = 0; step < 32; step++) {
+            const int t = FWD ? step : 31 - step;
+            if (lane == t) x = ZERO ? di * (bi - acc) : xold + di * (bi - acc);
+            const T xt = __shfl_sync(0xffffffffu, x, t);
+            if (pj[0] == (sl << 5) + t) {
+                acc += pa[0] * xt;
+#pragma unroll
+                for (int k = 0; k + 1 < kGsPartMax; k++) {
+                    pj[k] = pj[k + 1];
+                    pa[k] = pa[k + 1];
+                }
+                pj[kGsPartMax - 1] = -1;
+            }
+        }
+        if (valid) xn[i] = x;
     }
 }
 
@@ -678,6 +796,9 @@ struct LP<float> {
     static float *xpre(Level &l) { return l.xpre32; }
     static float *xp(Level &l) { return l.xp32; }
     static const float *r0(const amg_hier *h) { return h->r32; }
+    static const float *Pv(const Level &l) { return l.P32; }
+    static const float *Ptv(const Level &l) { return l.Pt32; }
+    static const float *ones(const Level &l) { return l.ones32; }
     static const float *csr(const Level &l) { return l.v32csr; }
     static const float *part(const Level &l, int d) { return l.gs_v32[d]; }
     static float *acc(const Level &l) { return reinterpret_cast<float *>(l.gs_acc); }
@@ -693,6 +814,9 @@ struct LP<double> {
     static double *xpre(Level &l) { return l.xpre64; }
     static double *xp(Level &l) { return l.xp64; }
     static const double *r0(const amg_hier *h) { return h->r; }
+    static const double *Pv(const Level &l) { return l.P.v; }
+    static const double *Ptv(const Level &l) { return l.Pt.v; }
+    static const double *ones(const Level &l) { return l.ones64; }
     static const double *csr(const Level &l) { return l.A.v; }
     static const double *part(const Level &l, int d) { return l.gs_v64[d]; }
     static double *acc(const Level &l) { return l.gs_acc; }
@@ -727,6 +851,30 @@ int shape_grid(const amg_hier *h, int n, int pi, int sweep, unsigned char shape)
     return w > 0 && w < g ? w : g;
 }
 
+// Weight of the down sweep's output t = w (b - A xpre): the tentative
+// prolongator's p (restriction by the aggregate map), or ones with
+// smoothed aggregation (the restriction then applies P^T).
+template <typename T>
+const T *pdown(const amg_hier *h, const Level &lv) {
+    return h->smoothed ? LP<T>::ones(lv) : LP<T>::p(lv);
+}
+
+// Prolongation to level l: xp = xpre + P x_{l+1} (through the aggregate map,
+// or the explicit smoothed P).
+template <typename T>
+void launch_prolong(amg_hier *h, int l, int grid, cudaStream_t s) {
+    using P = LP<T>;
+    auto &lev = h->lev;
+    Level &lv = lev[l];
+    int n = lv.A.n;
+    if (h->smoothed)
+        launch_k(h->pdl, k_prolong_sa<T>, grid, kBlock, s, n, (const int32_t *)lv.P.rp, (const int32_t *)lv.P.ci,
+                 P::Pv(lv), (const T *)P::xpre(lv), (const T *)P::x(lev[l + 1]), P::xp(lv), (const Ctl *)h->ctl);
+    else
+        launch_k(h->pdl, k_prolong<T>, grid, kBlock, s, n, (const T *)P::xpre(lv), P::p(lv), lv.agg,
+                 (const T *)P::x(lev[l + 1]), P::xp(lv), (const Ctl *)h->ctl);
+}
+
 // Down sweep of level l >= 1 with the given launch shape (bits 0 and 1).
 template <typename T>
 void launch_down(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
@@ -736,10 +884,10 @@ void launch_down(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
     int g = shape_grid(h, n, prec_index<T>(), 0, shape);
     if (shape & 1)
         WITH_COLS(lv.S, (launch_k(h->pdl, k_down<T, IDX, kUnrollSmall, false>, g, kBlock, s, n, lv.S.sptr, cols,
-                                  P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), (const Ctl *)h->ctl)));
+                                  P::val(lv), P::xpre(lv), P::b(lv), pdown<T>(h, lv), P::t(lv), (const Ctl *)h->ctl)));
     else
         WITH_COLS(lv.S, (launch_k(h->pdl, k_down<T, IDX, kUnroll, false>, g, kBlock, s, n, lv.S.sptr, cols,
-                                  P::val(lv), P::xpre(lv), P::b(lv), P::p(lv), P::t(lv), (const Ctl *)h->ctl)));
+                                  P::val(lv), P::xpre(lv), P::b(lv), pdown<T>(h, lv), P::t(lv), (const Ctl *)h->ctl)));
 }
 
 // Restriction from level l to l+1 (the coarsest gets float64 b_L).
@@ -749,6 +897,17 @@ void launch_restrict(amg_hier *h, int l, cudaStream_t s) {
     auto &lev = h->lev;
     Level &lv = lev[l];
     const Ctl *ctl = h->ctl;
+    if (h->smoothed) {
+        if (l + 2 == (int)lev.size())
+            launch_k(h->pdl, k_restrict_sa<T, double, false>, grid_rows(lv.nc), kBlock, s, lv.nc,
+                     (const int32_t *)lv.Pt.rp, (const int32_t *)lv.Pt.ci, P::Ptv(lv), (const T *)P::t(lv), h->bL,
+                     (const T *)nullptr, (T *)nullptr, ctl);
+        else
+            launch_k(h->pdl, k_restrict_sa<T, T, true>, grid_rows(lv.nc), kBlock, s, lv.nc,
+                     (const int32_t *)lv.Pt.rp, (const int32_t *)lv.Pt.ci, P::Ptv(lv), (const T *)P::t(lv),
+                     P::b(lev[l + 1]), P::dinv(lev[l + 1]), P::xpre(lev[l + 1]), ctl);
+        return;
+    }
     if (l + 2 == (int)lev.size())
         launch_k(h->pdl, k_restrict<T, double, false>, grid_rows(lv.nc), kBlock, s, lv.nc, lv.rptr, lv.ridx,
                  (const T *)P::t(lv), h->bL, (const T *)nullptr, (T *)nullptr, ctl);
@@ -762,7 +921,7 @@ void launch_restrict(amg_hier *h, int l, cudaStream_t s) {
 template <typename T>
 void launch_down_phase(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
     using P = LP<T>;
-    if (!(shape & 4)) {
+    if (!(shape & 4) || h->smoothed) {
         launch_down<T>(h, l, shape, s);
         launch_restrict<T>(h, l, s);
         return;
@@ -814,9 +973,8 @@ void launch_up_phase(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
     Level &lv = lev[l];
     int n = lv.A.n;
     const Ctl *ctl = h->ctl;
-    if (!(shape & 4)) {
-        launch_k(h->pdl, k_prolong<T>, grid_rows(n), kBlock, s, n, (const T *)P::xpre(lv), P::p(lv), lv.agg,
-                 (const T *)P::x(lev[l + 1]), P::xp(lv), ctl);
+    if (!(shape & 4) || h->smoothed) {
+        launch_prolong<T>(h, l, grid_rows(n), s);
         launch_post<T>(h, l, shape, s);
         return;
     }
@@ -863,7 +1021,7 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     int g0 = sizeof(T) == 4 ? h->grid32 : h->grid64;
     int sp1 = prof_begin(h, 0, s);
     WITH_COLS(l0.S, (launch_k(pdl, k_down<T, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n, l0.S.sptr, cols,
-                              P::val(l0), P::xpre(l0), b0, P::p(l0), P::t(l0), ctl)));
+                              P::val(l0), P::xpre(l0), b0, pdown<T>(h, l0), P::t(l0), ctl)));
     prof_end(h, sp1, s);
     int sp2 = prof_begin(h, 5, s);
     // levels handled by separate launches: 0..F-1; the tail runs F..L
@@ -904,8 +1062,7 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     kernels += 2;  // prolongation and post sweep of level 0
     prof_end(h, sp2, s);
     int sp7 = prof_begin(h, 7, s);
-    launch_k(pdl, k_prolong<T>, h->gridv, kBlock, s, l0.A.n, P::xpre(l0), P::p(l0), l0.agg, P::x(lev[1]),
-             P::xp(l0), ctl);
+    launch_prolong<T>(h, 0, h->gridv, s);
     prof_end(h, sp7, s);
     int sp3 = prof_begin(h, 1, s);
     WITH_COLS(l0.S, (launch_k(pdl, k_post<T, double, true, FCG, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n,
@@ -933,6 +1090,40 @@ int launch_gs(amg_hier *h, int l, bool pre, const T *b, T *target, cudaStream_t 
     const Ctl *ctl = h->ctl;
     const T *src = pre ? nullptr : (const T *)P::xp(lv);
     const int d = pre ? 0 : 1;  // the forward (pre) or backward (post) pass
+    // float32 only: a float64 warp instruction occupies the float64 pipe for
+    // all 32 lanes, and the one-warp recurrence issues two per step with one
+    // lane active; k_gs_block keeps a block per lane instead
+    if (sizeof(T) == 4 && lv.gs_w[d] >= 0 && lv.gs_w[d] <= kGsPartMax && nb <= 32 && 32 % nb == 0 &&
+        h->gs_fused) {
+        // both phases in one launch (one warp per slice)
+        const int w = lv.gs_w[d];
+        const int gr = grid_rows(n);
+        const bool big = n > kSmallRows;
+        const int32_t *pci = lv.gs_ci[d];
+        const T *pv = P::part(lv, d);
+        for (int sw = 1; sw <= nu; sw++) {
+            T *dst = (nu - sw) % 2 == 0 ? target : P::t(lv);
+            const bool zero = pre && sw == 1;
+#define PCG_GSW(UU, ST)                                                                                            \
+    do {                                                                                                            \
+        if (zero)                                                                                                   \
+            WITH_COLS(lv.S, (launch_k(h->pdl, k_gs_warp<T, IDX, UU, true, true, ST>, gr, kBlock, s, n, nb, w,       \
+                                      lv.S.sptr, cols, P::val(lv), pci, pv, P::dinv(lv), b, src, dst, ctl)));       \
+        else if (pre)                                                                                               \
+            WITH_COLS(lv.S, (launch_k(h->pdl, k_gs_warp<T, IDX, UU, true, false, ST>, gr, kBlock, s, n, nb, w,      \
+                                      lv.S.sptr, cols, P::val(lv), pci, pv, P::dinv(lv), b, src, dst, ctl)));       \
+        else                                                                                                        \
+            WITH_COLS(lv.S, (launch_k(h->pdl, k_gs_warp<T, IDX, UU, false, false, ST>, gr, kBlock, s, n, nb, w,     \
+                                      lv.S.sptr, cols, P::val(lv), pci, pv, P::dinv(lv), b, src, dst, ctl)));       \
+    } while (0)
+            if (l == 0) PCG_GSW(kUnroll, true);
+            else if (big) PCG_GSW(kUnroll, false);
+            else PCG_GSW(kUnrollSmall, false);
+#undef PCG_GSW
+            src = dst;
+        }
+        return nu;
+    }
     if (lv.gs_w[d] >= 0) {
         // two-phase sweeps
         const int w = lv.gs_w[d];
@@ -1012,7 +1203,7 @@ int launch_vcycle_gs(amg_hier *h, cudaStream_t s) {
     int sp1 = prof_begin(h, 0, s);
     kernels += launch_gs<T>(h, 0, true, b0, P::xpre(l0), s);
     WITH_COLS(l0.S, (launch_k(pdl, k_down<T, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n, l0.S.sptr, cols,
-                              P::val(l0), (const T *)P::xpre(l0), b0, P::p(l0), P::t(l0), (const Ctl *)ctl)));
+                              P::val(l0), (const T *)P::xpre(l0), b0, pdown<T>(h, l0), P::t(l0), (const Ctl *)ctl)));
     kernels += 1;
     prof_end(h, sp1, s);
     int sp2 = prof_begin(h, 5, s);
@@ -1035,15 +1226,13 @@ int launch_vcycle_gs(amg_hier *h, cudaStream_t s) {
     for (int l = L - 1; l >= 1; l--) {
         Level &lv = lev[l];
         int spl = prof_begin(h, kLevelSpan + 3 * l + 1, s);
-        launch_k(pdl, k_prolong<T>, grid_rows(lv.A.n), kBlock, s, lv.A.n, (const T *)P::xpre(lv), P::p(lv), lv.agg,
-                 (const T *)P::x(lev[l + 1]), P::xp(lv), (const Ctl *)ctl);
+        launch_prolong<T>(h, l, grid_rows(lv.A.n), s);
         kernels += 1 + launch_gs<T>(h, l, false, P::b(lv), P::x(lv), s);
         prof_end(h, spl, s);
     }
     prof_end(h, sp2, s);
     int sp3 = prof_begin(h, 1, s);
-    launch_k(pdl, k_prolong<T>, h->gridv, kBlock, s, l0.A.n, (const T *)P::xpre(l0), P::p(l0), l0.agg,
-             (const T *)P::x(lev[1]), P::xp(l0), (const Ctl *)ctl);
+    launch_prolong<T>(h, 0, h->gridv, s);
     kernels += 1 + launch_gs<T>(h, 0, false, b0, P::x(l0), s);
     launch_k(pdl, k_gs_finish0<T, FCG>, g0, kBlock, s, l0.A.n, (const T *)P::x(l0), (const double *)h->r,
              (const double *)h->q, h->z, h->partials, ctl);
@@ -1239,7 +1428,8 @@ bool is_device_ptr(const void *p) {
 // separately instead.
 int setup_tail(amg_hier *h) {
     h->tail_first[0] = h->tail_first[1] = 0;
-    if (h->coarse_iter) return AMG_OK;  // the tail holds a dense coarsest inverse
+    // the tail holds a dense coarsest inverse and aggregate-map transfers
+    if (h->coarse_iter || h->smoothed) return AMG_OK;
     const char *e = getenv("PCGAMG_TAIL");
     if (e && e[0] == '0') return AMG_OK;
     return setup_smem_tail(h);
@@ -1365,7 +1555,8 @@ int tune_level(amg_hier *h, int l, cudaStream_t s, int reps, cudaEvent_t e0, cud
 int autotune_impl(amg_hier *h, cudaStream_t s, int reps, int *changed) {
     int L = (int)h->lev.size() - 1;
     *changed = 0;
-    if (h->gs_nu) return AMG_OK;  // the shapes tune the l1-Jacobi sweeps only
+    // the shapes tune the l1-Jacobi sweeps and the tentative transfers only
+    if (h->gs_nu || h->smoothed) return AMG_OK;
     if (reps < 1) reps = 1;
     PCG_CK(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
     for (int l = 1; l <= L; l++) {
@@ -1395,7 +1586,7 @@ int autotune_impl(amg_hier *h, cudaStream_t s, int reps, int *changed) {
 // Drops every captured whole-solve graph of h (they are rebuilt on the next
 // solve) and marks batch graphs holding h as stale.
 void drop_graphs(amg_hier *h) {
-    for (auto *set : {h->gexec, h->gexec_nt})
+    for (auto *set : {h->gexec, h->gexec_nt, h->multi.gexec})
         for (int m = 0; m < 2; m++) {
             if (set[m]) cudaGraphExecDestroy(set[m]);
             set[m] = nullptr;

@@ -197,6 +197,51 @@ def serve_modes(meshes: list[Mesh], count: int, load_fraction: float = 0.7, seed
     return out
 
 
+def serve_sweep(meshes: list[Mesh], count: int = 2000, start_fraction: float = 0.35, factor: float = 1.5,
+                seed: int = 7, budget_bytes: int = 8 << 30, **server_kw) -> dict:
+    """Arrival-rate sweep of the mixed batching server and the plain float64
+    server (pcg_solve, one request at a time) on the same streams.
+
+    Each server's saturated rate is measured first (``count // 4`` requests
+    queued at once). Rates then grow geometrically by ``factor`` from
+    ``start_fraction`` times the plain server's saturated rate; a server is
+    run at every rate below its own saturated rate (above it its queue only
+    grows), ``count`` requests per rate. Then one run of the mixed server with
+    an ``budget_bytes`` device budget for hierarchies and engines: meshes that
+    do not fit are not admitted and their requests are refused."""
+    rtol = server_kw.get("rtol", 1e-8)
+    maxit = server_kw.get("maxit", 1000)
+    run_sequential(meshes, "pcg64", float("inf"), 16, seed + 1, rtol, maxit)    # warm-up
+    plain_sat = run_sequential(meshes, "pcg64", float("inf"), max(64, count // 4), seed, rtol, maxit)
+    srv = make_server(meshes, "fcg32", **server_kw)
+    try:
+        run_stream(srv, meshes, float("inf"), 16, seed + 1)                       # warm-up
+        mixed_sat = run_stream(srv, meshes, float("inf"), max(64, count // 4), seed)
+        rates = []
+        r = start_fraction * plain_sat["solves_per_s"]
+        while r < mixed_sat["solves_per_s"]:
+            rates.append(r)
+            r *= factor
+        mixed_rows = [run_stream(srv, meshes, rate, count, seed + 10 + k) for k, rate in enumerate(rates)]
+    finally:
+        srv.close()
+    plain_rows = [run_sequential(meshes, "pcg64", rate, count, seed + 10 + k, rtol, maxit)
+                  for k, rate in enumerate(rates) if rate < plain_sat["solves_per_s"]]
+    kw = dict(server_kw)
+    kw["hbm_budget"] = budget_bytes
+    small = make_server(meshes, "fcg32", **kw)
+    try:
+        admitted = [small.mesh_info(i)[0] > 0 for i in range(len(meshes))]
+        budget_run = run_stream(small, meshes, 0.7 * mixed_sat["solves_per_s"], max(64, count // 4), seed + 99)
+        used = small.info()
+    finally:
+        small.close()
+    return {"requests_per_rate": count, "rates": rates,
+            "mixed": {"saturated": mixed_sat, "sweep": mixed_rows},
+            "fp64_plain": {"saturated": plain_sat, "sweep": plain_rows},
+            "budget": {"bytes": budget_bytes, "admitted": admitted, "run": budget_run, "info": used}}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--sizes", type=int, nargs="+", default=[64, 128, 192])
