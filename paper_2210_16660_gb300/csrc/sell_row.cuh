@@ -95,4 +95,53 @@ __device__ __forceinline__ T sell_row(const IDX *__restrict__ c, const T *__rest
     return acc;
 }
 
+// One sliced-ELL row split into its static part, loaded by load() (slice
+// base and width, the first chunk's columns and values: matrix data, written
+// only by setup and refresh, so a kernel may load it before it waits for the
+// preceding kernel), and the product, dot(), which gathers x. Every chunk of
+// U entries is loaded masked, the next chunk's loads issued before the
+// current chunk's gathers, so a row of w entries costs about ceil(w / U)
+// dependent gather round trips whatever U is. Entries are summed one by one
+// in storage order (acc += a_k x(j_k)), as in sell_row.
+template <int U, bool STREAM, typename IDX, typename T>
+struct SellRow {
+    const IDX *c;
+    const T *a;
+    int w;
+    int j[U];
+    T v[U];
+
+    __device__ __forceinline__ void load(const int32_t *__restrict__ sptr, const IDX *__restrict__ col,
+                                         const T *__restrict__ val, int row) {
+        const int s = row >> 5, lane = row & 31;
+        const int32_t base = __ldg(sptr + s);
+        w = (__ldg(sptr + s + 1) - base) >> 5;
+        c = col + base + lane;
+        a = val + base + lane;
+        sell_chunk<U, STREAM>(c, a, 0, w, row, j, v);
+    }
+
+    template <typename F>
+    __device__ __forceinline__ T dot(int row, F xval) {
+        T acc = 0;
+        for (int k = 0; k < w; k += U) {
+            T x[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) x[u] = (k + u < w) ? xval(j[u]) : T(0);
+            int jn[U];
+            T vn[U];
+            sell_chunk<U, STREAM>(c, a, k + U, w, row, jn, vn);
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (k + u < w) acc += v[u] * x[u];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                j[u] = jn[u];
+                v[u] = vn[u];
+            }
+        }
+        return acc;
+    }
+};
+
 }  // namespace pcgamg

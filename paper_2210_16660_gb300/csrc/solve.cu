@@ -125,20 +125,44 @@ __device__ __forceinline__ void finish_rho(Ctl *ctl, double rz, double zq) {
 // ------------------------------------------------------------ V-cycle sweeps
 template <typename T>
 struct Occ { static constexpr int kMinBlocks = sizeof(T) == 4 ? 6 : 4; };
+// Sweeps with 16-entry chunks hold two chunks (the current one and the one
+// in flight) in registers: two float32 blocks per SM, one float64.
+template <typename T, int U>
+struct SweepOcc { static constexpr int kMinBlocks = U <= 4 ? Occ<T>::kMinBlocks : (sizeof(T) == 4 ? 2 : 1); };
+
+// The V-cycle sweeps, restriction and prolongation read their first row's
+// static data (matrix entries, weights, aggregate maps: written only by
+// setup and refresh) before pdl_enter(), so it arrives while the preceding
+// kernel drains; what a preceding kernel wrote is read through after_wait()
+// pointers once the wait has returned.
 
 // Pre-smooth from zero, residual, weighted restriction input:
 // t_i = p_i (b_i - sum_j a_ij xpre_j), xpre = D^-1 b.
 template <typename T, typename IDX, int U, bool STREAM>
-__global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_down(
+__global__ void __launch_bounds__(kBlock, SweepOcc<T, U>::kMinBlocks) k_down(
     int n, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
     const T *__restrict__ xpre, const T *__restrict__ b, const T *__restrict__ p, T *__restrict__ t,
     const Ctl *__restrict__ ctl) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    SellRow<U, STREAM, IDX, T> R;
+    T pi = 0;
+    if (i < n) {
+        R.load(sptr, col, val, i);
+        pi = ldg(p + i);
+    }
     pdl_enter();
+    xpre = after_wait(xpre);
+    b = after_wait(b);
+    ctl = after_wait(ctl);
     if (ctl->done) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        SELL_ROW_BEGIN
-        T acc = sell_row<U, STREAM>(c_, a_, w_, i, [&](int j) { return ldg(xpre + j); });
-        t[i] = ldg(p + i) * (ldg(b + i) - acc);
+    for (; i < n; i += stride) {
+        T acc = R.dot(i, [&](int j) { return ldg(xpre + j); });
+        t[i] = pi * (ldg(b + i) - acc);
+        if (i + stride < n) {
+            R.load(sptr, col, val, i + stride);
+            pi = ldg(p + i + stride);
+        }
     }
 }
 
@@ -147,13 +171,27 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong(int n, const T *__restrict__ xpre, const T *__restrict__ p,
                                                     const int32_t *__restrict__ agg, const T *__restrict__ xc,
                                                     T *__restrict__ xp, const Ctl *__restrict__ ctl) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    int a = -1;
+    T pw = 0;
+    if (i < n) {
+        a = ldg(agg + i);
+        pw = ldg(p + i);
+    }
     pdl_enter();
+    xpre = after_wait(xpre);
+    xc = after_wait(xc);
+    ctl = after_wait(ctl);
     if (ctl->done) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (; i < n; i += stride) {
         T x = ldg(xpre + i);
-        int a = ldg(agg + i);
-        if (a >= 0) x += ldg(p + i) * ldg(xc + a);
+        if (a >= 0) x += pw * ldg(xc + a);
         xp[i] = x;
+        if (i + stride < n) {
+            a = ldg(agg + i + stride);
+            pw = ldg(p + i + stride);
+        }
     }
 }
 
@@ -161,21 +199,37 @@ __global__ void __launch_bounds__(kBlock) k_prolong(int n, const T *__restrict__
 // z is written in float64 and the kernel also forms r.z (float64 r) and, for
 // FCG(1), z.q_old; its last block turns them into rho and beta.
 template <typename T, typename TZ, bool DOT, bool FCG, typename IDX, int U, bool STREAM>
-__global__ void __launch_bounds__(kBlock, Occ<T>::kMinBlocks) k_post(
+__global__ void __launch_bounds__(kBlock, SweepOcc<T, U>::kMinBlocks) k_post(
     int n, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
     const T *__restrict__ xp, const T *__restrict__ b, const T *__restrict__ dinv, TZ *__restrict__ z,
     const double *__restrict__ r64, const double *__restrict__ qold, double *partials, Ctl *ctl) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    SellRow<U, STREAM, IDX, T> R;
+    T di = 0;
+    if (i < n) {
+        R.load(sptr, col, val, i);
+        di = ldg(dinv + i);
+    }
     pdl_enter();
+    xp = after_wait(xp);
+    b = after_wait(b);
+    r64 = after_wait(r64);
+    qold = after_wait(qold);
+    ctl = after_wait(ctl);
     if (ctl->done) return;
     double rz = 0.0, zq = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        SELL_ROW_BEGIN
-        T acc = sell_row<U, STREAM>(c_, a_, w_, i, [&](int j) { return ldg(xp + j); });
-        TZ zo = (TZ)(ldg(xp + i) + ldg(dinv + i) * (ldg(b + i) - acc));
+    for (; i < n; i += stride) {
+        T acc = R.dot(i, [&](int j) { return ldg(xp + j); });
+        TZ zo = (TZ)(ldg(xp + i) + di * (ldg(b + i) - acc));
         z[i] = zo;
         if (DOT) {
             rz += ldg(r64 + i) * (double)zo;
             if (FCG) zq += (double)zo * ldg(qold + i);
+        }
+        if (i + stride < n) {
+            R.load(sptr, col, val, i + stride);
+            di = ldg(dinv + i + stride);
         }
     }
     if (DOT) {
@@ -195,14 +249,32 @@ __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t *__re
                                                      const int32_t *__restrict__ ridx, const T *__restrict__ t,
                                                      TO *__restrict__ bc, const T *__restrict__ dinvc,
                                                      T *__restrict__ xprec, const Ctl *__restrict__ ctl) {
-    pdl_enter();
-    if (ctl->done) return;
+    constexpr int M = 4;  // members read before the wait
     int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
+    int32_t k0 = 0, k1 = 0;
+    int m[M];
+    T dc = 0;
+    if (I < nc) {
+        k0 = ldg(rptr + I);
+        k1 = ldg(rptr + I + 1);
+#pragma unroll
+        for (int u = 0; u < M; u++) m[u] = k0 + u < k1 ? ldg(ridx + k0 + u) : 0;
+        if (PRE) dc = ldg(dinvc + I);
+    }
+    pdl_enter();
+    t = after_wait(t);
+    ctl = after_wait(ctl);
+    if (ctl->done || I >= nc) return;
+    T tv[M];
+#pragma unroll
+    for (int u = 0; u < M; u++) tv[u] = k0 + u < k1 ? ldg(t + m[u]) : T(0);
     T s = 0;
-    for (int32_t k = ldg(rptr + I); k < ldg(rptr + I + 1); k++) s += ldg(t + ldg(ridx + k));
+#pragma unroll
+    for (int u = 0; u < M; u++)
+        if (k0 + u < k1) s += tv[u];
+    for (int32_t k = k0 + M; k < k1; k++) s += ldg(t + ldg(ridx + k));
     bc[I] = (TO)s;
-    if (PRE) xprec[I] = ldg(dinvc + I) * s;
+    if (PRE) xprec[I] = dc * s;
 }
 
 // Smoothed aggregation: b_c[I] = sum over the rows i of P's column I
@@ -256,18 +328,36 @@ __global__ void __launch_bounds__(kBlock) k_down_restrict(int nc, const int32_t 
                                                           const T *__restrict__ p, TO *__restrict__ bc,
                                                           const T *__restrict__ dinvc, T *__restrict__ xprec,
                                                           const Ctl *__restrict__ ctl) {
-    pdl_enter();
-    if (ctl->done) return;
     int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
+    int32_t q0 = 0, q1 = 0;
+    int i = 0;
+    SellRow<U, false, IDX, T> R;
+    T pi = 0;
+    if (I < nc) {
+        q0 = ldg(rptr + I);
+        q1 = ldg(rptr + I + 1);
+        if (q0 < q1) {
+            i = ldg(ridx + q0);
+            R.load(sptr, col, val, i);
+            pi = ldg(p + i);
+        }
+    }
+    pdl_enter();
+    xpre = after_wait(xpre);
+    b = after_wait(b);
+    ctl = after_wait(ctl);
+    if (ctl->done || I >= nc) return;
     T sum = 0;
-    for (int32_t q = ldg(rptr + I); q < ldg(rptr + I + 1); q++) {
-        int i = ldg(ridx + q);
-        SELL_ROW_BEGIN
-        T acc = sell_row<U, false>(c_, a_, w_, i, [&](int j) { return ldg(xpre + j); });
+    for (int32_t q = q0; q < q1; q++) {
+        T acc = R.dot(i, [&](int j) { return ldg(xpre + j); });
         // rounded product (never contracted into the sum), as k_down stores t
-        T t = mul_rn(ldg(p + i), ldg(b + i) - acc);
+        T t = mul_rn(pi, ldg(b + i) - acc);
         sum += t;
+        if (q + 1 < q1) {
+            i = ldg(ridx + q + 1);
+            R.load(sptr, col, val, i);
+            pi = ldg(p + i);
+        }
     }
     bc[I] = (TO)sum;
     if (PRE) xprec[I] = ldg(dinvc + I) * sum;
@@ -284,7 +374,19 @@ __global__ void __launch_bounds__(kBlock) k_prolong_post(int n, const int32_t *_
                                                          const int32_t *__restrict__ agg, const T *__restrict__ xc,
                                                          const T *__restrict__ b, const T *__restrict__ dinv,
                                                          T *__restrict__ z, const Ctl *__restrict__ ctl) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    SellRow<U, false, IDX, T> R;
+    T di = 0;
+    if (i < n) {
+        R.load(sptr, col, val, i);
+        di = ldg(dinv + i);
+    }
     pdl_enter();
+    xpre = after_wait(xpre);
+    xc = after_wait(xc);
+    b = after_wait(b);
+    ctl = after_wait(ctl);
     if (ctl->done) return;
     auto xp = [&](int j) {
         T x = ldg(xpre + j);
@@ -292,10 +394,13 @@ __global__ void __launch_bounds__(kBlock) k_prolong_post(int n, const int32_t *_
         if (a >= 0) x += ldg(p + j) * ldg(xc + a);
         return x;
     };
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        SELL_ROW_BEGIN
-        T acc = sell_row<U, false>(c_, a_, w_, i, xp);
-        z[i] = xp(i) + ldg(dinv + i) * (ldg(b + i) - acc);
+    for (; i < n; i += stride) {
+        T acc = R.dot(i, xp);
+        z[i] = xp(i) + di * (ldg(b + i) - acc);
+        if (i + stride < n) {
+            R.load(sptr, col, val, i + stride);
+            di = ldg(dinv + i + stride);
+        }
     }
 }
 
