@@ -168,34 +168,42 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- roofline
 def algorithmic_bytes(kind: str, mode: str, n0: int, nnz0: int, n1: int, ib: int = 4,
-                      flexible: bool = False) -> float:
+                      flexible: bool = False, stored: int = 0, pat_entries: int = 0) -> float:
     """Compulsory DRAM bytes of one launch of a level-0 kernel (each array once).
 
-    Matrix: value + column (ib = 2 bytes for int16 offsets, else 4) per
-    stored entry, one int32 slice pointer per 32 rows. Vectors as the kernels
-    read/write them (gathered vectors counted once). A vector the kernel
-    launched just before wrote and this one reads (xp between the
+    Matrix: a value per nonzero; a column (ib = 2 bytes for int16 offsets,
+    else 4) per nonzero of the slices stored without a shared offset
+    pattern, and for the slices with one (``pat_entries`` of the ``stored``
+    entries) the pattern itself, ib per entry column, plus one pattern flag
+    (ib) per slice; one int32 slice pointer per 32 rows. Vectors as the
+    kernels read/write them (gathered vectors counted once). A vector the
+    kernel launched just before wrote and this one reads (xp between the
     prolongation and the post sweep, 8-17 MB at 128^3) is served by the L2
     and not counted. ``flexible``: the FCG(1) beta in float64 too (the
     iterative coarsest solve), so the post sweep also reads q_old.
     """
     sptr = 4 * (n0 // 32 + 1)
+    if pat_entries and stored:
+        uf = pat_entries / stored
+        idx = nnz0 * (1 - uf) * ib + ib * (pat_entries / 32 + (n0 + 31) // 32)
+    else:
+        idx = nnz0 * ib
     vb = 4 if mode == "fcg32" else 8          # V-cycle value / vector bytes
     remit = 12 if mode == "fcg32" else 16     # r32 + xpre32 written, dinv32 read | xpre64 written, dinv read
     if kind == "spmv":      # p read, q written; float64 A
-        return nnz0 * (8 + ib) + n0 * 16 + sptr
+        return nnz0 * 8 + idx + n0 * 16 + sptr
     if kind == "axpy":      # z, p read; p written
         return n0 * 24
     if kind == "update":    # x, p, r, q read; x, r written; + the V-cycle's copy of r
         return n0 * (48 + remit)
-    if kind == "residual":  # b, x read; r written; + the V-cycle's copy of r
+    if kind == "residual":  # b, x read; r written; + the V-cycle's copy of r (columns entry by entry)
         return nnz0 * (8 + ib) + n0 * (24 + remit) + sptr
     if kind == "down0":     # xpre, b (r32 / r), p read; t written
-        return nnz0 * (vb + ib) + n0 * 4 * vb + sptr
+        return nnz0 * vb + idx + n0 * 4 * vb + sptr
     if kind == "prolong0":  # xpre, p, agg read, x_1 gathered, xp written
         return n0 * (3 * vb + 4) + n1 * vb
     if kind == "post0":     # b (r32 | r), dinv read, z (float64) written; xp from L2
-        post = nnz0 * (vb + ib) + n0 * (2 * vb + 8) + sptr
+        post = nnz0 * vb + idx + n0 * (2 * vb + 8) + sptr
         if mode == "fcg32":
             post += n0 * 8                   # float64 r for r.z
         if mode == "fcg32" or flexible:
@@ -755,6 +763,8 @@ def run_ours(args):
     n0, nnz0 = levels[0]
     n1 = levels[1][0] if len(levels) > 1 else 0
     ib0 = amg.level_layout(0)["index_bytes"]
+    stored0 = amg.level_layout(0)["stored"]
+    pat0 = amg.level_pattern(0)
     peak = peaks.get("hbm_gbs")
     peak_src = "measured"
     if not peak:
@@ -772,7 +782,7 @@ def run_ours(args):
             if k == "residual":
                 entry["note"] = "runs a full sweep only when the recursive residual met rtol; other launches exit"
             elif k != "coarse_levels":
-                bl = algorithmic_bytes(k, mode, n0, nnz0, n1, ib0)
+                bl = algorithmic_bytes(k, mode, n0, nnz0, n1, ib0, stored=stored0, pat_entries=pat0["entries"])
                 entry["algorithmic_bytes"] = bl
                 entry["gbs"] = bl / (ms / cnt * 1e-3) / 1e9
                 entry["frac_of_hbm"] = entry["gbs"] / peak
@@ -814,7 +824,8 @@ def run_ours(args):
             "config": headline_config(args, n0, nnz0),
             "serving_summary": serving_summary(serving),
             "hierarchy": {"levels": len(levels), "rows_nnz": levels, "coarse": amg.coarse_info(),
-                          "layout": [amg.level_layout(l) for l in range(len(levels))]},
+                          "layout": [amg.level_layout(l) for l in range(len(levels))],
+                          "level0_patterns": pat0},
             "iters": {"median": statistics.median(m["iters"]), "min": min(m["iters"]), "max": max(m["iters"])},
             "latency_ms": {"p50": pct(m["lat_ms"], 50), "p99": pct(m["lat_ms"], 99)},
             "true_rel": m["true_rel"],

@@ -26,7 +26,7 @@ _COARSE = {"auto": COARSE_AUTO, "dense": COARSE_DENSE, "iter": COARSE_ITER}
 EXPORTS = ("amg_default_params", "amg_set_allocator", "amg_setup", "amg_set_mode", "pcg_solve",
            "amg_last_true_residual", "amg_info", "amg_level_agg", "amg_level_csr", "amg_setup_times",
            "amg_destroy", "amg_last_error", "amg_profile", "amg_profile_read", "amg_launch_count",
-           "amg_level_layout", "amg_residual_noalloc", "pcg_solve_multi", "amg_multi_info",
+           "amg_level_layout", "amg_level_pattern", "amg_residual_noalloc", "pcg_solve_multi", "amg_multi_info",
            "amg_batch_create", "pcg_solve_batch", "amg_batch_destroy", "amg_server_default_params",
            "amg_serve_plan", "amg_server_create", "amg_server_mesh_info", "amg_server_info", "amg_server_submit",
            "amg_server_progress", "amg_server_result", "amg_server_destroy", "amg_autotune", "amg_level_shape",
@@ -87,6 +87,8 @@ def load(build_if_missing: bool = True):
     lib.amg_level_agg.restype = I
     lib.amg_level_layout.argtypes = [P, I, C.POINTER(I), C.POINTER(C.c_int64), C.POINTER(I)]
     lib.amg_level_layout.restype = I
+    lib.amg_level_pattern.argtypes = [P, I, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.amg_level_pattern.restype = I
     lib.amg_level_csr.argtypes = [P, I, P, P, P]
     lib.amg_level_csr.restype = I
     lib.amg_setup_times.argtypes = [P, P]
@@ -362,6 +364,15 @@ class AMG:
         if r:
             raise AmgError(r, last_error())
         return {"slice": sl.value, "stored": st.value, "index_bytes": ib.value}
+
+    def level_pattern(self, level: int) -> dict:
+        """Slices (and their stored entries) of a level kept with a shared
+        offset pattern (level 0 of a structured mesh: nearly all)."""
+        sl, en = C.c_int64(), C.c_int64()
+        r = load().amg_level_pattern(self._h, level, C.byref(sl), C.byref(en))
+        if r:
+            raise AmgError(r, last_error())
+        return {"slices": sl.value, "entries": en.value}
 
     def level_csr(self, level: int):
         n, z = self.info()[level]

@@ -319,6 +319,17 @@ int amg_level_layout(amg_handle h, int level, int *slice, int64_t *stored, int *
     return AMG_OK;
 }
 
+int amg_level_pattern(amg_handle h, int level, int64_t *slices, int64_t *entries) {
+    if (!h || level < 0 || level >= (int)h->lev.size()) {
+        set_error("amg_level_pattern: bad handle or level");
+        return AMG_ERR_ARG;
+    }
+    const Sell &S = h->lev[level].S;
+    if (slices) *slices = S.upat ? S.uniform_slices : 0;
+    if (entries) *entries = S.upat ? S.uniform_entries : 0;
+    return AMG_OK;
+}
+
 int amg_level_csr(amg_handle h, int level, int32_t *row_ptr, int32_t *col, double *val) {
     if (!h || level < 0 || level >= (int)h->lev.size()) {
         set_error("amg_level_csr: bad handle or level");

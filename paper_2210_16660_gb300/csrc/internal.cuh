@@ -110,6 +110,13 @@ struct DevCSR {
 // Sliced ELL with slice height 32: entry k of row 32*s + lane lives at
 // sptr[s] + 32*k + lane; rows shorter than the slice width are padded with
 // their own index and a zero value. One warp streams one slice.
+// First pattern entry of a slice whose rows do not share one offset
+// pattern (no stored offset takes this value: 16-bit offsets satisfy
+// |col - row| < 2^15, and 32-bit ones are row differences of int32 indices
+// inside [0, n)).
+template <typename IDX>
+constexpr IDX kNoPattern = sizeof(IDX) == 2 ? (IDX)INT16_MIN : (IDX)INT32_MIN;
+
 struct Sell {
     int n = 0, nslices = 0;
     int64_t nnz_pad = 0;
@@ -118,6 +125,16 @@ struct Sell {
     int16_t *col16 = nullptr;  // col - row when every |col - row| < 2^15, else null
     double *v64 = nullptr;
     float *v32 = nullptr;
+    // Shared offset patterns (level 0; null elsewhere). A slice whose rows
+    // all take their columns from one offset pattern (i + o_0 < i + o_1 <
+    // ...) is stored in pattern order, each row's absent offsets as explicit
+    // zeros, and upat[sptr[s] / 32 + k] = o_k holds the pattern once for the
+    // slice; any other slice has upat[sptr[s] / 32] = kNoPattern. The
+    // pattern has the column type: upat16 beside col16, else upat. col and
+    // col16 stay complete, so a kernel may read either form.
+    int32_t *upat = nullptr;
+    int16_t *upat16 = nullptr;
+    int64_t uniform_slices = 0, uniform_entries = 0;
 };
 
 struct Level {
@@ -332,6 +349,7 @@ struct amg_hier {
     double refresh_ms = 0;  // host time of the last amg_refresh
     int use_graph = 1;
     int no_col16 = 0;
+    int no_uniform = 0;  // PCGAMG_UNIFORM=0: no shared offset patterns on level 0
     int pdl = 1;  // programmatic dependent launch between solve kernels
     int graph_gen = 0;       // bumped whenever captured graphs go stale
     // shared-memory cluster tail: levels tail_first..L in one cluster launch,

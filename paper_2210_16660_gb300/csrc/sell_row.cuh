@@ -3,6 +3,8 @@
 
 #include <cstdint>
 
+#include "internal.cuh"
+
 namespace pcgamg {
 
 // Sum over the stored entries of one sliced-ELL row: acc = sum_k a_k x(j_k),
@@ -103,22 +105,56 @@ __device__ __forceinline__ T sell_row(const IDX *__restrict__ c, const T *__rest
 // current chunk's gathers, so a row of w entries costs about ceil(w / U)
 // dependent gather round trips whatever U is. Entries are summed one by one
 // in storage order (acc += a_k x(j_k)), as in sell_row.
+//
+// With upat (level 0), a slice stored with a shared offset pattern takes
+// column i + o_k from the pattern, one offset per entry column of the slice
+// read by every lane of the warp, instead of one column index per entry: the
+// column of entry k is rb + c[cs k], with (c, cs, rb) = (the row's column
+// indices, 32, row or 0) or (the slice's pattern, 1, row).
+template <typename IDX>
+__device__ __forceinline__ int col_base(int row);
+template <>
+__device__ __forceinline__ int col_base<int32_t>(int) { return 0; }
+template <>
+__device__ __forceinline__ int col_base<int16_t>(int row) { return row; }
+
 template <int U, bool STREAM, typename IDX, typename T>
 struct SellRow {
     const IDX *c;
     const T *a;
-    int w;
+    int w, cs, rb;
     int j[U];
     T v[U];
 
+    __device__ __forceinline__ void chunk(int k, int row, int (&jj)[U], T (&vv)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (k + u < w) {
+                jj[u] = rb + (int)ld_mat<STREAM>(c + cs * (k + u));
+                vv[u] = ld_mat<STREAM>(a + 32 * (k + u));
+            } else {
+                jj[u] = row;
+                vv[u] = T(0);
+            }
+        }
+    }
+
     __device__ __forceinline__ void load(const int32_t *__restrict__ sptr, const IDX *__restrict__ col,
-                                         const T *__restrict__ val, int row) {
+                                         const T *__restrict__ val, int row,
+                                         const IDX *__restrict__ upat = nullptr) {
         const int s = row >> 5, lane = row & 31;
         const int32_t base = __ldg(sptr + s);
         w = (__ldg(sptr + s + 1) - base) >> 5;
-        c = col + base + lane;
         a = val + base + lane;
-        sell_chunk<U, STREAM>(c, a, 0, w, row, j, v);
+        c = col + base + lane;
+        cs = 32;
+        rb = col_base<IDX>(row);
+        if (upat && __ldg(upat + (base >> 5)) != kNoPattern<IDX>) {
+            c = upat + (base >> 5);
+            cs = 1;
+            rb = row;
+        }
+        chunk(0, row, j, v);
     }
 
     template <typename F>
@@ -130,7 +166,7 @@ struct SellRow {
             for (int u = 0; u < U; u++) x[u] = (k + u < w) ? xval(j[u]) : T(0);
             int jn[U];
             T vn[U];
-            sell_chunk<U, STREAM>(c, a, k + U, w, row, jn, vn);
+            chunk(k + U, row, jn, vn);
 #pragma unroll
             for (int u = 0; u < U; u++)
                 if (k + u < w) acc += v[u] * x[u];

@@ -694,9 +694,12 @@ __global__ void k_pass_weights(int m, int nc, const int32_t *__restrict__ first,
 }
 
 // Values only of the sliced-ELL copies (the layout and columns are those of
-// the same pattern, already in place).
-__global__ void k_sell_vals(int n, int nsl, const int32_t *__restrict__ rp, const double *__restrict__ v,
-                            const int32_t *__restrict__ sptr, double *__restrict__ v64, float *__restrict__ v32) {
+// the same pattern, already in place). A slice with a shared offset pattern
+// (upat) takes row i's value for offset o_k from its CSR entry of column
+// i + o_k, or 0 where the row has none.
+__global__ void k_sell_vals(int n, int nsl, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ v, const int32_t *__restrict__ sptr,
+                            const int32_t *__restrict__ upat, double *__restrict__ v64, float *__restrict__ v32) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nsl * kSlice) return;
     int s = i / kSlice, lane = i % kSlice;
@@ -704,12 +707,80 @@ __global__ void k_sell_vals(int n, int nsl, const int32_t *__restrict__ rp, cons
     int w = (sptr[s + 1] - base) / kSlice;
     int len = i < n ? rp[i + 1] - rp[i] : 0;
     int32_t r0 = i < n ? rp[i] : 0;
+    const bool uni = upat && upat[base / kSlice] != kNoPattern<int32_t>;
+    int q = 0;
     for (int k = 0; k < w; k++) {
         int32_t e = base + k * kSlice + lane;
-        double a = k < len ? v[r0 + k] : 0.0;
+        double a = 0.0;
+        if (uni) {
+            if (q < len && ci[r0 + q] - i == upat[base / kSlice + k]) a = v[r0 + q++];
+        } else if (k < len) {
+            a = v[r0 + k];
+        }
         v64[e] = a;
         v32[e] = __double2float_rn(a);
     }
+}
+
+// 16-bit copy of the offset patterns (beside 16-bit column offsets).
+__global__ void k_pattern16(const int32_t *__restrict__ up, int16_t *__restrict__ up16, int64_t m) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < m) up16[q] = up[q] == kNoPattern<int32_t> ? kNoPattern<int16_t> : (int16_t)up[q];
+}
+
+// Shared offset patterns of level 0, one warp per slice. The candidate is
+// the offsets j - i of the slice's longest row (the lowest lane among those
+// of the slice's width); the slice takes it when every row's offsets are a
+// subset of it and every i + o_k is a row index. It is then rewritten in
+// pattern order: entry k of row i gets column i + o_k and the row's value
+// there, or 0 where the row has no entry of that offset (a row's entries
+// keep their increasing column order, the zeros fall between them), and
+// upat receives the pattern; otherwise upat marks the slice kNoPattern.
+__global__ void k_sell_uniform(int n, int nsl, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               const double *__restrict__ v, const int32_t *__restrict__ sptr,
+                               int32_t *__restrict__ col, int16_t *__restrict__ col16, double *__restrict__ v64,
+                               float *__restrict__ v32, int32_t *__restrict__ upat, unsigned long long *count) {
+    const int lane = threadIdx.x & 31;
+    const int s = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (s >= nsl) return;  // the whole warp leaves together
+    const int32_t base = sptr[s];
+    const int w = (sptr[s + 1] - base) / kSlice;
+    const int i = s * kSlice + lane;
+    const bool real = i < n;
+    const int32_t r0 = real ? rp[i] : 0;
+    const int len = real ? rp[i + 1] - r0 : 0;
+    const unsigned longest = __ballot_sync(0xffffffffu, real && len == w);
+    const int isrc = s * kSlice + __ffs(longest) - 1;
+    const int32_t rs = rp[isrc];
+    bool ok = true;
+    if (real) {
+        int q = 0;
+        for (int k = 0; k < w; k++) {
+            const int o = ci[rs + k] - isrc;
+            const int64_t j = (int64_t)i + o;
+            if (j < 0 || j >= n) ok = false;
+            if (q < len && ci[r0 + q] - i == o) q++;
+        }
+        if (q != len) ok = false;
+    }
+    if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) upat[base / kSlice] = kNoPattern<int32_t>;
+        return;
+    }
+    int q = 0;
+    for (int k = 0; k < w; k++) {
+        const int o = ci[rs + k] - isrc;
+        if (lane == 0) upat[base / kSlice + k] = o;
+        if (!real) continue;  // lanes past the last row are never swept
+        const int32_t e = base + k * kSlice + lane;
+        double a = 0.0;
+        if (q < len && ci[r0 + q] - i == o) a = v[r0 + q++];
+        col[e] = i + o;
+        if (col16) col16[e] = (int16_t)o;
+        v64[e] = a;
+        v32[e] = __double2float_rn(a);
+    }
+    if (lane == 0) atomicAdd(count, 1ull);
 }
 
 double now_ms() {
@@ -857,7 +928,7 @@ int pairwise_pass(amg_hier *h, const DevCSR &cur, const double *w, int32_t **agg
     return AMG_OK;
 }
 
-int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
+int finish_level(amg_hier *h, Level &lv, bool first, bool coarsest, cudaStream_t s) {
     Mem &M = h->mem;
     int n = lv.A.n;
     PCG_TRY(alloc(M, &lv.dinv, n));
@@ -912,6 +983,41 @@ int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
             k_col16_fill<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(n, S.nslices, S.sptr, S.col,
                                                                                   S.col16);
             PCG_LAUNCH_CK();
+        }
+    }
+    // shared offset patterns (level 0: the level the Krylov and level-0
+    // sweeps stream every iteration)
+    if (first && !h->no_uniform) {
+        PCG_TRY(alloc(M, &S.upat, (size_t)tot / kSlice));
+        unsigned long long *dcount = nullptr;
+        PCG_TRY(alloc(M, &dcount, 1));
+        PCG_CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
+        k_sell_uniform<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(
+            n, S.nslices, lv.A.rp, lv.A.ci, lv.A.v, S.sptr, S.col, S.col16, S.v64, S.v32, S.upat, dcount);
+        PCG_LAUNCH_CK();
+        unsigned long long cnt = 0;
+        PCG_CK(cudaMemcpyAsync(&cnt, dcount, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaStreamSynchronize(s));
+        release(M, dcount);
+        S.uniform_slices = (int64_t)cnt;
+        if (cnt == 0) {
+            release(M, S.upat);
+            S.upat = nullptr;
+        } else {
+            // entries of the uniform slices: sum of their widths x 32
+            std::vector<int32_t> sp((size_t)S.nslices + 1), up((size_t)tot / kSlice);
+            PCG_CK(cudaMemcpy(sp.data(), S.sptr, sizeof(int32_t) * sp.size(), cudaMemcpyDeviceToHost));
+            PCG_CK(cudaMemcpy(up.data(), S.upat, sizeof(int32_t) * up.size(), cudaMemcpyDeviceToHost));
+            int64_t e = 0;
+            for (int q = 0; q < S.nslices; q++)
+                if (up[sp[q] / kSlice] != kNoPattern<int32_t>) e += sp[q + 1] - sp[q];
+            S.uniform_entries = e;
+            if (S.col16) {
+                PCG_TRY(alloc(M, &S.upat16, (size_t)tot / kSlice));
+                k_pattern16<<<grid_for((int64_t)tot / kSlice), kBlock, 0, s>>>(S.upat, S.upat16,
+                                                                               (int64_t)tot / kSlice);
+                PCG_LAUNCH_CK();
+            }
         }
     }
     // work vectors
@@ -978,6 +1084,9 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
     // PCGAMG_COL16=0 keeps int32 columns on every level.
     const char *c16 = getenv("PCGAMG_COL16");
     if (c16 && c16[0] == '0') h->no_col16 = 1;
+    // PCGAMG_UNIFORM=0 stores level 0 without shared offset patterns.
+    const char *un = getenv("PCGAMG_UNIFORM");
+    if (un && un[0] == '0') h->no_uniform = 1;
     const char *pd = getenv("PCGAMG_PDL");
     if (pd && pd[0] == '0') h->pdl = 0;
     // PCGAMG_GS_FUSED=0 keeps the two-launch Gauss-Seidel sweeps everywhere.
@@ -1099,7 +1208,7 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
         nx.w = curw;
     }
     int L = (int)h->lev.size() - 1;
-    for (int l = 0; l <= L; l++) PCG_TRY(finish_level(h, h->lev[l], l == L, s));
+    for (int l = 0; l <= L; l++) PCG_TRY(finish_level(h, h->lev[l], l == 0, l == L, s));
 
     // coarsest solver: dense inverse up to kDenseMax rows (AUTO), else the
     // iterative FCG + block-Jacobi ILU(1) solve of Sec. 3.1
@@ -1305,8 +1414,8 @@ int refresh_impl(amg_hier *h, const amg_csr *A, cudaStream_t s) {
                                                         lv.dinv, lv.dinv32);
         else
             k_l1diag<<<grid_for(nl), kBlock, 0, s>>>(nl, lv.A.rp, lv.A.v, lv.dinv, lv.dinv32);
-        k_sell_vals<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(nl, S.nslices, lv.A.rp, lv.A.v,
-                                                                             S.sptr, S.v64, S.v32);
+        k_sell_vals<<<grid_for((int64_t)S.nslices * kSlice), kBlock, 0, s>>>(nl, S.nslices, lv.A.rp, lv.A.ci,
+                                                                             lv.A.v, S.sptr, S.upat, S.v64, S.v32);
         if (lv.v32csr) k_to_f32<<<grid_for(lv.A.nnz), kBlock, 0, s>>>(lv.A.v, lv.v32csr, lv.A.nnz);
         PCG_LAUNCH_CK();
         if (h->gs_nu) PCG_TRY(fill_gs_parts(lv, h->gs_blocks, s));

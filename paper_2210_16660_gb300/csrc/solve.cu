@@ -141,14 +141,14 @@ struct SweepOcc { static constexpr int kMinBlocks = U <= 4 ? Occ<T>::kMinBlocks 
 template <typename T, typename IDX, int U, bool STREAM>
 __global__ void __launch_bounds__(kBlock, SweepOcc<T, U>::kMinBlocks) k_down(
     int n, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
-    const T *__restrict__ xpre, const T *__restrict__ b, const T *__restrict__ p, T *__restrict__ t,
-    const Ctl *__restrict__ ctl) {
+    const IDX *__restrict__ upat, const T *__restrict__ xpre, const T *__restrict__ b,
+    const T *__restrict__ p, T *__restrict__ t, const Ctl *__restrict__ ctl) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     SellRow<U, STREAM, IDX, T> R;
     T pi = 0;
     if (i < n) {
-        R.load(sptr, col, val, i);
+        R.load(sptr, col, val, i, upat);
         pi = ldg(p + i);
     }
     pdl_enter();
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kBlock, SweepOcc<T, U>::kMinBlocks) k_down(
         T acc = R.dot(i, [&](int j) { return ldg(xpre + j); });
         t[i] = pi * (ldg(b + i) - acc);
         if (i + stride < n) {
-            R.load(sptr, col, val, i + stride);
+            R.load(sptr, col, val, i + stride, upat);
             pi = ldg(p + i + stride);
         }
     }
@@ -201,14 +201,15 @@ __global__ void __launch_bounds__(kBlock) k_prolong(int n, const T *__restrict__
 template <typename T, typename TZ, bool DOT, bool FCG, typename IDX, int U, bool STREAM>
 __global__ void __launch_bounds__(kBlock, SweepOcc<T, U>::kMinBlocks) k_post(
     int n, const int32_t *__restrict__ sptr, const IDX *__restrict__ col, const T *__restrict__ val,
-    const T *__restrict__ xp, const T *__restrict__ b, const T *__restrict__ dinv, TZ *__restrict__ z,
-    const double *__restrict__ r64, const double *__restrict__ qold, double *partials, Ctl *ctl) {
+    const IDX *__restrict__ upat, const T *__restrict__ xp, const T *__restrict__ b,
+    const T *__restrict__ dinv, TZ *__restrict__ z, const double *__restrict__ r64,
+    const double *__restrict__ qold, double *partials, Ctl *ctl) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     SellRow<U, STREAM, IDX, T> R;
     T di = 0;
     if (i < n) {
-        R.load(sptr, col, val, i);
+        R.load(sptr, col, val, i, upat);
         di = ldg(dinv + i);
     }
     pdl_enter();
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kBlock, SweepOcc<T, U>::kMinBlocks) k_post(
             if (FCG) zq += (double)zo * ldg(qold + i);
         }
         if (i + stride < n) {
-            R.load(sptr, col, val, i + stride);
+            R.load(sptr, col, val, i + stride, upat);
             di = ldg(dinv + i + stride);
         }
     }
@@ -681,16 +682,22 @@ __global__ void __launch_bounds__(kBlock) k_axpy_p(int n, const double *__restri
 template <typename IDX>
 __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int32_t *__restrict__ sptr,
                                                     const IDX *__restrict__ col, const double *__restrict__ val,
-                                                    const double *__restrict__ p, double *__restrict__ q,
-                                                    double *partials, Ctl *ctl) {
+                                                    const IDX *__restrict__ upat, const double *__restrict__ p,
+                                                    double *__restrict__ q, double *partials, Ctl *ctl) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    SellRow<kUnroll, true, IDX, double> R;
+    if (i < n) R.load(sptr, col, val, i, upat);
     pdl_enter();
+    p = after_wait(p);
+    ctl = after_wait(ctl);
     if (ctl->done) return;
     double pq = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        SELL_ROW_BEGIN
-        double acc = sell_row<kUnroll, true>(c_, a_, w_, i, [&](int j) { return ldg(p + j); });
+    for (; i < n; i += stride) {
+        double acc = R.dot(i, [&](int j) { return ldg(p + j); });
         q[i] = acc;
         pq += ldg(p + i) * acc;
+        if (i + stride < n) R.load(sptr, col, val, i + stride, upat);
     }
     if (publish_partials(pq, 0.0, partials, &ctl->counter[1])) {
         double a, unused;
@@ -933,15 +940,19 @@ REmit remit(amg_hier *h) {
 }
 
 // Launch with the level's column array: int16 offsets when present.
+// BODY sees IDX (the column type), cols (the columns) and pats (the shared
+// offset patterns in the column type, or null).
 #define WITH_COLS(S, BODY)                          \
     do {                                            \
         if ((S).col16) {                            \
             using IDX = int16_t;                    \
             const IDX *cols = (S).col16;            \
+            [[maybe_unused]] const IDX *pats = (S).upat16; \
             BODY;                                   \
         } else {                                    \
             using IDX = int32_t;                    \
             const IDX *cols = (S).col;              \
+            [[maybe_unused]] const IDX *pats = (S).upat; \
             BODY;                                   \
         }                                           \
     } while (0)
@@ -989,10 +1000,10 @@ void launch_down(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
     int g = shape_grid(h, n, prec_index<T>(), 0, shape);
     if (shape & 1)
         WITH_COLS(lv.S, (launch_k(h->pdl, k_down<T, IDX, kUnrollSmall, false>, g, kBlock, s, n, lv.S.sptr, cols,
-                                  P::val(lv), P::xpre(lv), P::b(lv), pdown<T>(h, lv), P::t(lv), (const Ctl *)h->ctl)));
+                                  P::val(lv), pats, P::xpre(lv), P::b(lv), pdown<T>(h, lv), P::t(lv), (const Ctl *)h->ctl)));
     else
         WITH_COLS(lv.S, (launch_k(h->pdl, k_down<T, IDX, kUnroll, false>, g, kBlock, s, n, lv.S.sptr, cols,
-                                  P::val(lv), P::xpre(lv), P::b(lv), pdown<T>(h, lv), P::t(lv), (const Ctl *)h->ctl)));
+                                  P::val(lv), pats, P::xpre(lv), P::b(lv), pdown<T>(h, lv), P::t(lv), (const Ctl *)h->ctl)));
 }
 
 // Restriction from level l to l+1 (the coarsest gets float64 b_L).
@@ -1061,11 +1072,11 @@ void launch_post(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
     int g = shape_grid(h, n, prec_index<T>(), 1, shape);
     if (shape & 1)
         WITH_COLS(lv.S, (launch_k(h->pdl, k_post<T, T, false, false, IDX, kUnrollSmall, false>, g, kBlock, s, n,
-                                  lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv),
+                                  lv.S.sptr, cols, P::val(lv), pats, P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv),
                                   (const double *)nullptr, (const double *)nullptr, (double *)nullptr, h->ctl)));
     else
         WITH_COLS(lv.S, (launch_k(h->pdl, k_post<T, T, false, false, IDX, kUnroll, false>, g, kBlock, s, n,
-                                  lv.S.sptr, cols, P::val(lv), P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv),
+                                  lv.S.sptr, cols, P::val(lv), pats, P::xp(lv), P::b(lv), P::dinv(lv), P::x(lv),
                                   (const double *)nullptr, (const double *)nullptr, (double *)nullptr, h->ctl)));
 }
 
@@ -1112,6 +1123,31 @@ int launch_coarsest(amg_hier *h, cudaStream_t s, int *kernels) {
     return AMG_OK;
 }
 
+// One wave of the level-0 sweeps of precision T.
+template <typename T>
+int grid0(const amg_hier *h) { return sizeof(T) == 4 ? h->grid32 : h->grid64; }
+
+// Level-0 down sweep t = p (b - A xpre) (evict-first matrix stream, shared
+// offset patterns where level 0 has them).
+template <typename T>
+void launch_down0(amg_hier *h, const T *b0, cudaStream_t s) {
+    using P = LP<T>;
+    Level &l0 = h->lev[0];
+    WITH_COLS(l0.S, (launch_k(h->pdl, k_down<T, IDX, kUnroll, true>, grid0<T>(h), kBlock, s, l0.A.n, l0.S.sptr,
+                              cols, P::val(l0), pats, (const T *)P::xpre(l0), b0,
+                              pdown<T>(h, l0), P::t(l0), (const Ctl *)h->ctl)));
+}
+
+// Level-0 post sweep z = xp + dinv (b - A xp) with r.z (and z.q_old).
+template <typename T, bool FCG>
+void launch_post0(amg_hier *h, const T *b0, cudaStream_t s) {
+    using P = LP<T>;
+    Level &l0 = h->lev[0];
+    WITH_COLS(l0.S, (launch_k(h->pdl, k_post<T, double, true, FCG, IDX, kUnroll, true>, grid0<T>(h), kBlock, s,
+                              l0.A.n, l0.S.sptr, cols, P::val(l0), pats, P::xp(l0), b0,
+                              P::dinv(l0), h->z, h->r, h->q, h->partials, h->ctl)));
+}
+
 // z = B r (one V-cycle in precision T), including rho / beta. Kernels are
 // launched with programmatic dependent launch when h->pdl (see pdl_enter).
 template <typename T, bool FCG>
@@ -1119,14 +1155,9 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     using P = LP<T>;
     auto &lev = h->lev;
     int L = (int)lev.size() - 1;
-    Ctl *ctl = h->ctl;
-    Level &l0 = lev[0];
     const T *b0 = P::r0(h);
-    const bool pdl = h->pdl;
-    int g0 = sizeof(T) == 4 ? h->grid32 : h->grid64;
     int sp1 = prof_begin(h, 0, s);
-    WITH_COLS(l0.S, (launch_k(pdl, k_down<T, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n, l0.S.sptr, cols,
-                              P::val(l0), P::xpre(l0), b0, pdown<T>(h, l0), P::t(l0), ctl)));
+    launch_down0<T>(h, b0, s);
     prof_end(h, sp1, s);
     int sp2 = prof_begin(h, 5, s);
     // levels handled by separate launches: 0..F-1; the tail runs F..L
@@ -1170,9 +1201,7 @@ int launch_vcycle(amg_hier *h, cudaStream_t s) {
     launch_prolong<T>(h, 0, h->gridv, s);
     prof_end(h, sp7, s);
     int sp3 = prof_begin(h, 1, s);
-    WITH_COLS(l0.S, (launch_k(pdl, k_post<T, double, true, FCG, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n,
-                              l0.S.sptr, cols, P::val(l0), P::xp(l0), b0, P::dinv(l0), h->z, h->r, h->q, h->partials,
-                              ctl)));
+    launch_post0<T, FCG>(h, b0, s);
     prof_end(h, sp3, s);
     h->launches += kernels;
     PCG_LAUNCH_CK();
@@ -1303,12 +1332,10 @@ int launch_vcycle_gs(amg_hier *h, cudaStream_t s) {
     Level &l0 = lev[0];
     const T *b0 = P::r0(h);
     const bool pdl = h->pdl;
-    int g0 = sizeof(T) == 4 ? h->grid32 : h->grid64;
     int kernels = 0;
     int sp1 = prof_begin(h, 0, s);
     kernels += launch_gs<T>(h, 0, true, b0, P::xpre(l0), s);
-    WITH_COLS(l0.S, (launch_k(pdl, k_down<T, IDX, kUnroll, true>, g0, kBlock, s, l0.A.n, l0.S.sptr, cols,
-                              P::val(l0), (const T *)P::xpre(l0), b0, pdown<T>(h, l0), P::t(l0), (const Ctl *)ctl)));
+    launch_down0<T>(h, b0, s);
     kernels += 1;
     prof_end(h, sp1, s);
     int sp2 = prof_begin(h, 5, s);
@@ -1339,7 +1366,8 @@ int launch_vcycle_gs(amg_hier *h, cudaStream_t s) {
     int sp3 = prof_begin(h, 1, s);
     launch_prolong<T>(h, 0, h->gridv, s);
     kernels += 1 + launch_gs<T>(h, 0, false, b0, P::x(l0), s);
-    launch_k(pdl, k_gs_finish0<T, FCG>, g0, kBlock, s, l0.A.n, (const T *)P::x(l0), (const double *)h->r,
+    // the post sweep's grid, so rho is summed in the same order as there
+    launch_k(pdl, k_gs_finish0<T, FCG>, grid0<T>(h), kBlock, s, l0.A.n, (const T *)P::x(l0), (const double *)h->r,
              (const double *)h->q, h->z, h->partials, ctl);
     kernels += 1;
     prof_end(h, sp3, s);
@@ -1373,7 +1401,8 @@ int launch_iteration_t(amg_hier *h, cudaStream_t s) {
     launch_k(pdl, k_axpy_p, h->gridv, kBlock, s, n, h->z, h->p, h->ctl);
     prof_end(h, sp4, s);
     int sp5 = prof_begin(h, 2, s);
-    WITH_COLS(l0.S, (launch_k(pdl, k_spmv<IDX>, h->grid64, kBlock, s, n, l0.S.sptr, cols, l0.S.v64, h->p, h->q,
+    WITH_COLS(l0.S, (launch_k(pdl, k_spmv<IDX>, h->grid64, kBlock, s, n, l0.S.sptr, cols, l0.S.v64,
+                              pats, h->p, h->q,
                               h->partials, h->ctl)));
     prof_end(h, sp5, s);
     int sp6 = prof_begin(h, 3, s);

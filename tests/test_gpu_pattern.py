@@ -1,0 +1,216 @@
+"""Level 0 stored with shared offset patterns.
+
+A sliced-ELL slice whose 32 rows all take their columns from one pattern of
+offsets (row i uses columns i + o_k, k = 0..w-1, a row's absent offsets kept
+as explicit zeros) keeps the pattern once, and the level-0 V-cycle sweeps
+and q = A p read one offset per entry column instead of one column index per
+entry. Each row still sums its entries in increasing column order, the
+inserted zeros adding exact zeros, so the values are those of the plain
+layout.
+
+Bar: on a structured Q1 mesh nearly every level-0 slice takes a pattern; a
+solve gives the same iteration count and the same x (torch.equal) as the
+plain layout (PCGAMG_UNIFORM=0) in both modes and with 16- and 32-bit
+columns, and meets the single-solve bar against the oracle; a permuted
+matrix takes no pattern; a matrix with a few long-range couplings mixes
+pattern and plain slices with the same results (and the counts of a host
+restatement of the rule); a refresh with new values equals the plain
+layout's refresh and meets the bar against the oracle's; the CSR read back
+is the input.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2210_16660_gb300 import binding as B  # noqa: E402
+from paper_2210_16660_gb300 import workloads as W  # noqa: E402
+
+RTOL = 1e-8
+X_TOL = 1e-6
+
+
+def _amg(A, mode, **env):
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        return B.AMG.from_csr(A, mode=mode)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
+
+
+def _solve(amg, b):
+    x = torch.zeros_like(b)
+    r = amg.solve(b, x, rtol=RTOL, maxit=1000)
+    assert r.status == 0, r.message
+    return r, x
+
+
+def _slices(n):
+    return (n + 31) // 32
+
+
+def _pattern_slices(A):
+    """The pattern rule restated on the host: slice s (rows 32 s ..) takes
+    the offsets of its longest row (the lowest such row) when every row's
+    offsets are among them and every row i plus every pattern offset is a row
+    index. Returns (slices, stored entries of those slices)."""
+    n, rp, ci = A.n, A.row_ptr, A.col
+    count = entries = 0
+    for s in range(_slices(n)):
+        rows = range(32 * s, min(32 * s + 32, n))
+        lens = [rp[i + 1] - rp[i] for i in rows]
+        w = max(lens)
+        src = rows[lens.index(w)]
+        pat = set((ci[rp[src]:rp[src + 1]] - src).tolist())
+        ok = True
+        for i in rows:
+            offs = ci[rp[i]:rp[i + 1]] - i
+            if not set(offs.tolist()) <= pat or min(pat) + i < 0 or max(pat) + i >= n:
+                ok = False
+                break
+        if ok:
+            count += 1
+            entries += 32 * w
+    return count, entries
+
+
+@pytest.mark.parametrize("mode", ["pcg64", "fcg32"])
+@pytest.mark.parametrize("N,col16", [(33, "1"), (24, "0")])
+def test_pattern_layout_equals_plain(mode, N, col16):
+    prob = W.make_problem(N, 1.04, seed=50 + N)
+    b = torch.from_numpy(prob.b).cuda()
+    a1 = _amg(prob.A, mode, PCGAMG_COL16=col16)
+    a2 = _amg(prob.A, mode, PCGAMG_COL16=col16, PCGAMG_UNIFORM="0")
+    pat = a1.level_pattern(0)
+    want = _pattern_slices(prob.A)
+    assert (pat["slices"], pat["entries"]) == want
+    assert pat["slices"] >= 0.95 * _slices(prob.A.n)
+    assert a2.level_pattern(0) == {"slices": 0, "entries": 0}
+    assert a1.level_pattern(1) == {"slices": 0, "entries": 0}
+    assert a1.level_layout(0) == a2.level_layout(0)
+    r1, x1 = _solve(a1, b)
+    r2, x2 = _solve(a2, b)
+    assert r1.iters == r2.iters and torch.equal(x1, x2)
+    ref = O.Hierarchy(prob.A, coarse_max=200, n_pass=2).solve(prob.b, rtol=RTOL, maxit=1000, mode=mode)
+    xs = x1.cpu().numpy()
+    assert abs(r1.iters - ref["iters"]) <= 1
+    assert np.linalg.norm(xs - ref["x"]) <= X_TOL * np.linalg.norm(ref["x"])
+    rp, ci, v = a1.level_csr(0)
+    assert np.array_equal(rp, prob.A.row_ptr) and np.array_equal(ci, prob.A.col)
+    assert np.array_equal(v, prob.A.val)
+    a1.close()
+    a2.close()
+
+
+def _permuted(A, seed):
+    import scipy.sparse as sp
+    n = A.n
+    perm = np.random.default_rng(seed).permutation(n)
+    M = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(n, n))[perm][:, perm].tocsr()
+    M.sort_indices()
+    return W.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+
+
+def test_permuted_matrix_takes_no_pattern():
+    pytest.importorskip("scipy")
+    prob = W.make_problem(14, 1.04, seed=3)
+    A = _permuted(prob.A, 7)
+    a = _amg(A, "fcg32")
+    assert a.level_pattern(0)["slices"] == 0
+    b = torch.from_numpy(W.normals(9, A.n)).cuda()
+    r, x = _solve(a, b)
+    bh = b.cpu().numpy()
+    assert np.linalg.norm(bh - W.spmv(A, x.cpu().numpy())) <= RTOL * np.linalg.norm(bh)
+    a.close()
+
+
+def test_long_range_couplings_mix_pattern_and_plain_slices():
+    """Rows 32 m and 32 m + 1 coupled to rows n/2 and n/2 + 3 further on (a
+    sum of two-node graph Laplacians added, so the matrix stays SPD): the
+    two rows of a slice carry different long offsets, so that slice and the
+    one holding both partners keep the plain layout; the host restatement of
+    the rule counts the same pattern slices."""
+    sp = pytest.importorskip("scipy.sparse")
+    A0, _, _ = W.q1_laplacian(20, 1.04)
+    n = A0.n
+    L = sp.csr_matrix((A0.val, A0.col, A0.row_ptr), shape=(n, n))
+    s0 = 32 * np.arange(5, n // 64, 9)
+    src = np.r_[s0, s0 + 1]
+    dst = np.r_[s0 + n // 2, s0 + 1 + n // 2 + 3]
+    eps = 0.05
+    rows = np.r_[src, dst, src, dst]
+    cols = np.r_[dst, src, src, dst]
+    vals = np.r_[np.full(2 * len(src), -eps), np.full(2 * len(src), eps)]
+    M = (L + sp.csr_matrix((vals, (rows, cols)), shape=(n, n))).tocsr()
+    M.sum_duplicates()
+    M.sort_indices()
+    A = W.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+    base, _ = _pattern_slices(A0)
+    want = _pattern_slices(A)
+    assert want[0] < base
+    b = torch.from_numpy(W.normals(4, n)).cuda()
+    for mode in ("pcg64", "fcg32"):
+        a1 = _amg(A, mode, PCGAMG_COL16="0")
+        a2 = _amg(A, mode, PCGAMG_COL16="0", PCGAMG_UNIFORM="0")
+        pat = a1.level_pattern(0)
+        assert (pat["slices"], pat["entries"]) == want
+        r1, x1 = _solve(a1, b)
+        r2, x2 = _solve(a2, b)
+        assert r1.iters == r2.iters and torch.equal(x1, x2)
+        a1.close()
+        a2.close()
+
+
+@pytest.mark.parametrize("mode", ["pcg64", "fcg32"])
+def test_refresh_refills_the_pattern_slices(mode):
+    A, _, _ = W.q1_laplacian(26, 1.04)
+    A2 = W.rescaled(A, seed=17)
+    b = torch.from_numpy(W.spmv(A2, W.normals(6, A.n))).cuda()
+    a1 = _amg(A, mode)
+    assert a1.level_pattern(0)["slices"] > 0
+    _solve(a1, b)
+    a1.refresh(A2)
+    fresh = _amg(A2, mode)
+    # the refreshed hierarchy keeps the first setup's aggregates, so compare
+    # with the oracle's refresh and, for the pattern layout itself, with a
+    # refreshed plain-layout handle
+    a2 = _amg(A, mode, PCGAMG_UNIFORM="0")
+    a2.refresh(A2)
+    r1, x1 = _solve(a1, b)
+    r2, x2 = _solve(a2, b)
+    assert r1.iters == r2.iters and torch.equal(x1, x2)
+    h_or = O.Hierarchy(A, coarse_max=200, n_pass=2)
+    assert h_or.refresh(A2) == 0
+    ref = h_or.solve(b.cpu().numpy(), rtol=RTOL, maxit=1000, mode=mode)
+    assert abs(r1.iters - ref["iters"]) <= 1
+    assert np.linalg.norm(x1.cpu().numpy() - ref["x"]) <= X_TOL * np.linalg.norm(ref["x"])
+    rf, xf = _solve(fresh, b)
+    bh = b.cpu().numpy()
+    assert np.linalg.norm(bh - W.spmv(A2, xf.cpu().numpy())) <= RTOL * np.linalg.norm(bh)
+    for a in (a1, a2, fresh):
+        a.close()
+
+
+def test_multi_column_and_batch_paths_with_patterns():
+    prob = W.make_problem(21, 1.04, seed=31)
+    a = _amg(prob.A, "fcg32")
+    assert a.level_pattern(0)["slices"] > 0
+    rng = np.random.default_rng(2)
+    Bm = rng.standard_normal((prob.A.n, 3))
+    X = np.zeros_like(Bm)
+    st, *_ = a.solve_multi(Bm, X, rtol=RTOL)
+    assert st == 0
+    for k in range(3):
+        res = np.linalg.norm(Bm[:, k] - W.spmv(prob.A, X[:, k]))
+        assert res <= RTOL * np.linalg.norm(Bm[:, k])
+    a.close()
