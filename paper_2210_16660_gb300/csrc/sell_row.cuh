@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -179,5 +180,62 @@ struct SellRow {
         return acc;
     }
 };
+
+// Rows of level-0 slices stored with a shared offset pattern and at most
+// kPatW entries per row: load() requests every value of the row at once
+// (kPatW registers), and dot() gathers x in chunks of kPatG entries whose
+// columns come from the pattern alone (L1-resident), so the gathers do not
+// wait for the values and a row costs about one DRAM latency, overlapped
+// with ceil(w / kPatG) gather round trips. Rows of other slices go through a
+// 4-entry SellRow. Entries are summed one by one in storage order.
+constexpr int kPatW = 32, kPatG = 8;
+// chunk depth that selects PatRow in the sweeps' Row type
+constexpr int kPatRow = 32;
+
+template <bool STREAM, typename IDX, typename T>
+struct PatRow {
+    const IDX *pat;
+    int w;
+    bool uni;
+    T v[kPatW];
+    SellRow<4, STREAM, IDX, T> R;
+
+    __device__ __forceinline__ void load(const int32_t *__restrict__ sptr, const IDX *__restrict__ col,
+                                         const T *__restrict__ val, int row,
+                                         const IDX *__restrict__ upat = nullptr) {
+        const int s = row >> 5, lane = row & 31;
+        const int32_t base = __ldg(sptr + s);
+        w = (__ldg(sptr + s + 1) - base) >> 5;
+        pat = upat + (base >> 5);
+        uni = upat && w <= kPatW && __ldg(pat) != kNoPattern<IDX>;
+        if (uni) {
+            const T *a = val + base + lane;
+#pragma unroll
+            for (int k = 0; k < kPatW; k++) v[k] = k < w ? ld_mat<STREAM>(a + 32 * k) : T(0);
+        } else {
+            R.load(sptr, col, val, row, upat);
+        }
+    }
+
+    template <typename F>
+    __device__ __forceinline__ T dot(int row, F xval) {
+        if (!uni) return R.dot(row, xval);
+        T acc = 0;
+#pragma unroll
+        for (int k0 = 0; k0 < kPatW; k0 += kPatG) {
+            if (k0 >= w) break;
+            T x[kPatG];
+#pragma unroll
+            for (int u = 0; u < kPatG; u++) x[u] = k0 + u < w ? xval(row + (int)__ldg(pat + k0 + u)) : T(0);
+#pragma unroll
+            for (int u = 0; u < kPatG; u++)
+                if (k0 + u < w) acc += v[k0 + u] * x[u];
+        }
+        return acc;
+    }
+};
+
+template <int U, bool STREAM, typename IDX, typename T>
+using RowOf = typename std::conditional<U == kPatRow, PatRow<STREAM, IDX, T>, SellRow<U, STREAM, IDX, T>>::type;
 
 }  // namespace pcgamg

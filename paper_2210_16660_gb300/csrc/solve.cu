@@ -128,7 +128,11 @@ struct Occ { static constexpr int kMinBlocks = sizeof(T) == 4 ? 6 : 4; };
 // Sweeps with 16-entry chunks hold two chunks (the current one and the one
 // in flight) in registers: two float32 blocks per SM, one float64.
 template <typename T, int U>
-struct SweepOcc { static constexpr int kMinBlocks = U <= 4 ? Occ<T>::kMinBlocks : (sizeof(T) == 4 ? 2 : 1); };
+struct SweepOcc {
+    static constexpr int kMinBlocks = U <= 4 ? Occ<T>::kMinBlocks
+                                      : U == kPatRow ? (sizeof(T) == 4 ? 3 : 1)
+                                                     : (sizeof(T) == 4 ? 2 : 1);
+};
 
 // The V-cycle sweeps, restriction and prolongation read their first row's
 // static data (matrix entries, weights, aggregate maps: written only by
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(kBlock, SweepOcc<T, U>::kMinBlocks) k_down(
     const T *__restrict__ p, T *__restrict__ t, const Ctl *__restrict__ ctl) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
-    SellRow<U, STREAM, IDX, T> R;
+    RowOf<U, STREAM, IDX, T> R;
     T pi = 0;
     if (i < n) {
         R.load(sptr, col, val, i, upat);
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(kBlock, SweepOcc<T, U>::kMinBlocks) k_post(
     const double *__restrict__ qold, double *partials, Ctl *ctl) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
-    SellRow<U, STREAM, IDX, T> R;
+    RowOf<U, STREAM, IDX, T> R;
     T di = 0;
     if (i < n) {
         R.load(sptr, col, val, i, upat);
@@ -1127,15 +1131,27 @@ int launch_coarsest(amg_hier *h, cudaStream_t s, int *kernels) {
 template <typename T>
 int grid0(const amg_hier *h) { return sizeof(T) == 4 ? h->grid32 : h->grid64; }
 
+// Float32 level-0 sweeps read whole rows at once where level 0 has shared
+// offset patterns (PatRow), else 4-entry chunks.
+inline bool pat_rows(const amg_hier *h) { return h->lev[0].S.upat != nullptr; }
+
 // Level-0 down sweep t = p (b - A xpre) (evict-first matrix stream, shared
 // offset patterns where level 0 has them).
 template <typename T>
 void launch_down0(amg_hier *h, const T *b0, cudaStream_t s) {
     using P = LP<T>;
     Level &l0 = h->lev[0];
-    WITH_COLS(l0.S, (launch_k(h->pdl, k_down<T, IDX, kUnroll, true>, grid0<T>(h), kBlock, s, l0.A.n, l0.S.sptr,
-                              cols, P::val(l0), pats, (const T *)P::xpre(l0), b0,
-                              pdown<T>(h, l0), P::t(l0), (const Ctl *)h->ctl)));
+    if constexpr (sizeof(T) == 4) {
+        if (pat_rows(h)) {
+            WITH_COLS(l0.S, (launch_k(h->pdl, k_down<T, IDX, kPatRow, true>, grid0<T>(h), kBlock, s, l0.A.n,
+                                      l0.S.sptr, cols, P::val(l0), pats, (const T *)P::xpre(l0), b0,
+                                      pdown<T>(h, l0), P::t(l0), (const Ctl *)h->ctl)));
+            return;
+        }
+    }
+    WITH_COLS(l0.S, (launch_k(h->pdl, k_down<T, IDX, kUnroll, true>, grid0<T>(h), kBlock, s, l0.A.n,
+                                  l0.S.sptr, cols, P::val(l0), pats, (const T *)P::xpre(l0), b0, pdown<T>(h, l0),
+                                  P::t(l0), (const Ctl *)h->ctl)));
 }
 
 // Level-0 post sweep z = xp + dinv (b - A xp) with r.z (and z.q_old).
@@ -1143,9 +1159,17 @@ template <typename T, bool FCG>
 void launch_post0(amg_hier *h, const T *b0, cudaStream_t s) {
     using P = LP<T>;
     Level &l0 = h->lev[0];
+    if constexpr (sizeof(T) == 4) {
+        if (pat_rows(h)) {
+            WITH_COLS(l0.S, (launch_k(h->pdl, k_post<T, double, true, FCG, IDX, kPatRow, true>, grid0<T>(h), kBlock,
+                                      s, l0.A.n, l0.S.sptr, cols, P::val(l0), pats, P::xp(l0), b0, P::dinv(l0), h->z,
+                                      h->r, h->q, h->partials, h->ctl)));
+            return;
+        }
+    }
     WITH_COLS(l0.S, (launch_k(h->pdl, k_post<T, double, true, FCG, IDX, kUnroll, true>, grid0<T>(h), kBlock, s,
-                              l0.A.n, l0.S.sptr, cols, P::val(l0), pats, P::xp(l0), b0,
-                              P::dinv(l0), h->z, h->r, h->q, h->partials, h->ctl)));
+                                  l0.A.n, l0.S.sptr, cols, P::val(l0), pats, P::xp(l0), b0, P::dinv(l0), h->z, h->r,
+                                  h->q, h->partials, h->ctl)));
 }
 
 // z = B r (one V-cycle in precision T), including rho / beta. Kernels are
@@ -1606,6 +1630,18 @@ int alloc_solve_workspace(amg_hier *h) {
         return AMG_OK;
     };
     PCG_TRY(wave((const void *)k_down<float, int32_t, kUnroll, true>, &h->grid32));
+    if (pat_rows(h)) {
+        // the whole-row sweeps: one wave of the fewer of their resident blocks
+        int gd = 0, gp = 0;
+        if (h->lev[0].S.col16) {
+            PCG_TRY(wave((const void *)k_down<float, int16_t, kPatRow, true>, &gd));
+            PCG_TRY(wave((const void *)k_post<float, double, true, true, int16_t, kPatRow, true>, &gp));
+        } else {
+            PCG_TRY(wave((const void *)k_down<float, int32_t, kPatRow, true>, &gd));
+            PCG_TRY(wave((const void *)k_post<float, double, true, true, int32_t, kPatRow, true>, &gp));
+        }
+        h->grid32 = std::min(gd, gp);
+    }
     PCG_TRY(wave((const void *)k_spmv<int32_t>, &h->grid64));
     PCG_TRY(wave((const void *)k_update<AMG_MODE_FCG32>, &h->gridv));
     h->nblk = std::max(h->grid32, std::max(h->grid64, h->gridv));
