@@ -68,17 +68,25 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tail_smem(SmemTailPlan plan, c
     const int tid = threadIdx.x, nth = blockDim.x;
     // 1. this CTA's static data (matrices, maps, coarsest rows) in one copy.
     // It is written once at setup, so the copy runs before the wait for the
-    // preceding kernel and overlaps that kernel's end.
+    // preceding kernel and overlaps that kernel's end. 16-byte asynchronous
+    // copies (global to shared, no registers): every piece of a thread is in
+    // flight at once.
     {
-        const uint4 *src = reinterpret_cast<const uint4 *>(blob + (size_t)rank * plan.static_bytes);
-        uint4 *dst = reinterpret_cast<uint4 *>(smem);
-        for (int k = tid; k < plan.static_bytes / 16; k += nth) dst[k] = __ldg(src + k);
+        const unsigned char *src = blob + (size_t)rank * plan.static_bytes;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(smem);
+        for (int k = tid; k < plan.static_bytes / 16; k += nth)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * k), "l"(src + 16 * k)
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
     pdl_enter();
     bF = after_wait(bF);
     xpreF = after_wait(xpreF);
     xF = after_wait(xF);
-    if (ctl->done) return;
+    if (ctl->done) {
+        asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may outlive the block
+        return;
+    }
     // ... and the entry level's b and xpre rows (written by the previous kernel)
     {
         const SmemTailLevel &F = plan.lev[0];
@@ -89,6 +97,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tail_smem(SmemTailPlan plan, c
             xp[i - r0] = xpreF[i];
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     cl.sync();
     // 2. down sweep and restriction, level by level
     for (int k = 0; k + 1 < plan.nt; k++) {
@@ -110,8 +119,16 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tail_smem(SmemTailPlan plan, c
         const int32_t *mp = at<int32_t>(smem, Lv.off_mp);
         const uint32_t *mem = at<uint32_t>(smem, Lv.off_mem);
         for (int I = tid; I < crows; I += nth) {
+            // members in increasing index order; the first four loaded together
+            const int q0 = mp[I], q1 = mp[I + 1];
+            T tv[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) tv[u] = q0 + u < q1 ? *remote(cl, t, mem[q0 + u]) : T(0);
             T s = 0;
-            for (int q = mp[I]; q < mp[I + 1]; q++) s += *remote(cl, t, mem[q]);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (q0 + u < q1) s += tv[u];
+            for (int q = q0 + 4; q < q1; q++) s += *remote(cl, t, mem[q]);
             if (last) {
                 at<double>(smem, plan.off_bl)[I] = (double)s;
             } else {
