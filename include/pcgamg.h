@@ -346,10 +346,12 @@ void amg_server_destroy(amg_server s);
  * are launched on this device, not what they compute). For every level
  * l >= 1 with sweeps, each V-cycle precision and each of the down phase
  * (down sweep + restriction) and the up phase (prolongation + post sweep),
- * it times eight launch shapes -- rows loading 4 or 16 entries per chunk,
+ * it times nine launch shapes -- rows loading 4 or 16 entries per chunk,
  * times a one-wave grid-stride grid or one thread per row, times two
  * launches or one fused launch (down sweep and restriction by aggregate;
- * prolongation formed per gathered entry inside the post sweep) -- `reps`
+ * prolongation formed per gathered entry inside the post sweep); and rows
+ * read by 4 lanes each, every entry of a row gathered at once and the sum
+ * chained through the lanes in storage order -- `reps`
  * runs each (reps < 1: 1) on `stream`, and moves to the fastest when it
  * beats the current shape by more than 3%. Every shape forms the same
  * values and sums a row's entries in storage order, so solves give the same
@@ -361,10 +363,11 @@ int amg_autotune(amg_handle h, int reps, int *changed, void *stream);
 
 /* Launch shapes of a level (4 ints: float down, float up, float64 down,
  * float64 up; bit 0 = 16-entry chunks, bit 1 = one thread per row, bit 2 =
- * fused launch). Level 0's sweeps have a fixed shape and report 0. */
+ * fused launch; 8 = rows read by 4 lanes each, separate launches). Level
+ * 0's sweeps have a fixed shape and report 0. */
 int amg_level_shape(amg_handle h, int level, int *shape);
 
-/* Sets the launch shapes of level 1..L (same 4-int layout, values 0..7);
+/* Sets the launch shapes of level 1..L (same 4-int layout, values 0..8);
  * for manual tuning and for tests that check every shape gives the same
  * result. Errors: AMG_ERR_ARG. */
 int amg_set_level_shape(amg_handle h, int level, const int *shape);

@@ -217,7 +217,7 @@ int amg_set_level_shape(amg_handle h, int level, const int *shape) {
         return AMG_ERR_ARG;
     }
     for (int i = 0; i < 4; i++)
-        if (shape[i] < 0 || shape[i] > 7 || (h->smoothed && (shape[i] & 4))) {
+        if (shape[i] < 0 || shape[i] > 8 || (h->smoothed && (shape[i] & 4))) {
             set_error("amg_set_level_shape: shape values are 0..7 (0..3 with smoothed aggregation: the fused "
                       "shapes transfer through the aggregate map)");
             return AMG_ERR_ARG;

@@ -182,7 +182,8 @@ struct Level {
     // bit 0 = rows load 16 entries per chunk (else 4), bit 1 = one thread per
     // row (else one wave of resident blocks, grid-stride), bit 2 = one fused
     // launch (down sweep + restriction by aggregate; prolongation formed per
-    // gathered entry inside the post sweep) instead of two. Set by setup to
+    // gathered entry inside the post sweep) instead of two; the value 8 =
+    // rows read by 4 lanes each (separate launches). Set by setup to
     // the fixed rule (16-entry chunks up to kSmallRows rows, one thread per
     // row, separate launches) and by amg_autotune to the fastest measured
     // shape. The shape never changes a result: every shape forms the same

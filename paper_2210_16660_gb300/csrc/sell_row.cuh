@@ -235,6 +235,87 @@ struct PatRow {
     }
 };
 
+// Rows read by kMlL lanes each (the multi-lane launch shape of the coarse
+// levels). In a pass, lane q of a row loads the entries [k0 + q c,
+// min(w, k0 + (q + 1) c)) with c = min(ceil(w / kMlL), kMlC), and gathers x
+// for all of them at once; the row's sum is then chained through its lanes
+// in storage order (lane q continues from lane q - 1's accumulator, passed by
+// a shuffle), so the FMAs are those of SellRow, in the same order. A row
+// costs one gather round trip per pass (rows of up to kMlL kMlC entries take
+// one pass). The lanes of a warp are 8 rows of one slice, so every lane runs
+// the same number of passes; a row past the last one (live = false) loads
+// and gathers nothing but takes part in the shuffles.
+constexpr int kMlL = 4, kMlC = 12;
+
+template <bool STREAM, typename IDX, typename T>
+struct MlRow {
+    const IDX *cp;
+    const T *ap;
+    int w, c, k0, q;
+    bool live;
+    int j[kMlC];
+    T v[kMlC];
+
+    __device__ __forceinline__ int count() const {
+        const int lo = k0 + q * c;
+        const int hi = min(w, k0 + (q + 1) * c);
+        return live && hi > lo ? hi - lo : 0;
+    }
+
+    __device__ __forceinline__ void fill(int row) {
+        const int lo = k0 + q * c, cnt = count();
+#pragma unroll
+        for (int m = 0; m < kMlC; m++) {
+            if (m < cnt) {
+                j[m] = col_of(ld_mat<STREAM>(cp + 32 * (lo + m)), row);
+                v[m] = ld_mat<STREAM>(ap + 32 * (lo + m));
+            } else {
+                j[m] = row;
+                v[m] = T(0);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void load(const int32_t *__restrict__ sptr, const IDX *__restrict__ col,
+                                         const T *__restrict__ val, int row, int lane_q, bool is_live) {
+        const int s = row >> 5, r = row & 31;
+        const int32_t base = __ldg(sptr + s);
+        w = (__ldg(sptr + s + 1) - base) >> 5;
+        cp = col + base + r;
+        ap = val + base + r;
+        c = min((w + kMlL - 1) / kMlL, kMlC);
+        k0 = 0;
+        q = lane_q;
+        live = is_live;
+        fill(row);
+    }
+
+    template <typename F>
+    __device__ __forceinline__ T dot(int row, F xval) {
+        const int g0 = (int)(threadIdx.x & 31) & ~(kMlL - 1);
+        T acc = 0;
+        for (;;) {
+            const int cnt = count();
+            T x[kMlC];
+#pragma unroll
+            for (int m = 0; m < kMlC; m++) x[m] = m < cnt ? xval(j[m]) : T(0);
+#pragma unroll
+            for (int qq = 0; qq < kMlL; qq++) {
+                if (q == qq) {
+#pragma unroll
+                    for (int m = 0; m < kMlC; m++)
+                        if (m < cnt) acc += v[m] * x[m];
+                }
+                acc = __shfl_sync(0xffffffffu, acc, g0 + qq);
+            }
+            k0 += kMlL * c;
+            if (k0 >= w) break;
+            fill(row);
+        }
+        return acc;
+    }
+};
+
 template <int U, bool STREAM, typename IDX, typename T>
 using RowOf = typename std::conditional<U == kPatRow, PatRow<STREAM, IDX, T>, SellRow<U, STREAM, IDX, T>>::type;
 

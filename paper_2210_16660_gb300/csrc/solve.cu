@@ -170,6 +170,57 @@ __global__ void __launch_bounds__(kBlock, SweepOcc<T, U>::kMinBlocks) k_down(
     }
 }
 
+// The multi-lane launch shape of the coarse levels: k_down and k_post with
+// kMlL lanes per row (MlRow), one row per lane group, the whole of a row's
+// first pass (columns and values) loaded before the wait. Same values and
+// summation order as k_down / k_post. A warp whose rows lie past the last
+// slice leaves before any shuffle; the others keep every lane to the end.
+template <typename T, typename IDX>
+__global__ void __launch_bounds__(kBlock) k_down_ml(int n, const int32_t *__restrict__ sptr,
+                                                    const IDX *__restrict__ col, const T *__restrict__ val,
+                                                    const T *__restrict__ xpre, const T *__restrict__ b,
+                                                    const T *__restrict__ p, T *__restrict__ t,
+                                                    const Ctl *__restrict__ ctl) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = gid / kMlL, q = gid % kMlL;
+    if ((row >> 5) >= (n + 31) >> 5) return;
+    const bool live = row < n;
+    MlRow<false, IDX, T> R;
+    R.load(sptr, col, val, row, q, live);
+    T pi = 0;
+    if (live && q == 0) pi = ldg(p + row);
+    pdl_enter();
+    xpre = after_wait(xpre);
+    b = after_wait(b);
+    ctl = after_wait(ctl);
+    if (ctl->done) return;
+    T acc = R.dot(row, [&](int j) { return ldg(xpre + j); });
+    if (live && q == 0) t[row] = pi * (ldg(b + row) - acc);
+}
+
+template <typename T, typename IDX>
+__global__ void __launch_bounds__(kBlock) k_post_ml(int n, const int32_t *__restrict__ sptr,
+                                                    const IDX *__restrict__ col, const T *__restrict__ val,
+                                                    const T *__restrict__ xp, const T *__restrict__ b,
+                                                    const T *__restrict__ dinv, T *__restrict__ z,
+                                                    const Ctl *__restrict__ ctl) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = gid / kMlL, q = gid % kMlL;
+    if ((row >> 5) >= (n + 31) >> 5) return;
+    const bool live = row < n;
+    MlRow<false, IDX, T> R;
+    R.load(sptr, col, val, row, q, live);
+    T di = 0;
+    if (live && q == 0) di = ldg(dinv + row);
+    pdl_enter();
+    xp = after_wait(xp);
+    b = after_wait(b);
+    ctl = after_wait(ctl);
+    if (ctl->done) return;
+    T acc = R.dot(row, [&](int j) { return ldg(xp + j); });
+    if (live && q == 0) z[row] = ldg(xp + row) + di * (ldg(b + row) - acc);
+}
+
 // xp_i = xpre_i + p_i xc[agg_i].
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_prolong(int n, const T *__restrict__ xpre, const T *__restrict__ p,
@@ -1001,6 +1052,12 @@ void launch_down(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
     using P = LP<T>;
     Level &lv = h->lev[l];
     int n = lv.A.n;
+    if (shape & 8) {
+        WITH_COLS(lv.S, (launch_k(h->pdl, k_down_ml<T, IDX>, grid_rows((int64_t)n * kMlL), kBlock, s, n, lv.S.sptr,
+                                  cols, P::val(lv), (const T *)P::xpre(lv), (const T *)P::b(lv), pdown<T>(h, lv),
+                                  P::t(lv), (const Ctl *)h->ctl)));
+        return;
+    }
     int g = shape_grid(h, n, prec_index<T>(), 0, shape);
     if (shape & 1)
         WITH_COLS(lv.S, (launch_k(h->pdl, k_down<T, IDX, kUnrollSmall, false>, g, kBlock, s, n, lv.S.sptr, cols,
@@ -1073,6 +1130,12 @@ void launch_post(amg_hier *h, int l, unsigned char shape, cudaStream_t s) {
     using P = LP<T>;
     Level &lv = h->lev[l];
     int n = lv.A.n;
+    if (shape & 8) {
+        WITH_COLS(lv.S, (launch_k(h->pdl, k_post_ml<T, IDX>, grid_rows((int64_t)n * kMlL), kBlock, s, n, lv.S.sptr,
+                                  cols, P::val(lv), (const T *)P::xp(lv), (const T *)P::b(lv), P::dinv(lv), P::x(lv),
+                                  (const Ctl *)h->ctl)));
+        return;
+    }
     int g = shape_grid(h, n, prec_index<T>(), 1, shape);
     if (shape & 1)
         WITH_COLS(lv.S, (launch_k(h->pdl, k_post<T, T, false, false, IDX, kUnrollSmall, false>, g, kBlock, s, n,
@@ -1690,7 +1753,7 @@ int alloc_solve_workspace(amg_hier *h) {
 // and moves to the fastest only if it beats the current shape by more than
 // 3% (so timing noise does not flip shapes). Work vectors are zeroed first;
 // the inputs only set the timing. Captured solve graphs are dropped.
-constexpr int kShapes = 8;
+constexpr int kShapes = 9;  // 0..7, and 8: multi-lane rows
 template <typename T>
 int tune_level(amg_hier *h, int l, cudaStream_t s, int reps, cudaEvent_t e0, cudaEvent_t e1, int *changed) {
     int pi = prec_index<T>();
