@@ -403,6 +403,7 @@ def level_table(amg, lev_prof, mode: str, peak: float) -> list:
     # the coarsest span sits on the first level of the shared-memory tail
     # (when there is one): that level's time covers the tail levels below it
     tail = next((lvl for lvl in range(L + 1) if cnt[lvl][2] > 0), L)
+    coarse_kind = amg.coarse_info().get("kind")
     out = []
     for lvl in range(L + 1):
         n = info[lvl][0]
@@ -414,13 +415,17 @@ def level_table(amg, lev_prof, mode: str, peak: float) -> list:
             restr = n * vb + 4 * (n + nc) + (nc * 8 if lvl + 1 == L else 3 * nc * vb)
             down = restr + (z * (vb + ib) + 4 * n * vb if lvl > 0 else 0)
             up = (3 * n * vb + 4 * n + nc * vb + z * (vb + ib) + 4 * n * vb) if lvl > 0 else 0
+        elif coarse_kind == "iter":
+            down = None  # FCG + block-Jacobi ILU(1): its inner iteration count varies per V-cycle
         else:
             down = 8 * n * n + 16 * n
         t = ms[lvl][0] / max(cnt[lvl][0], 1) + ms[lvl][1] / max(cnt[lvl][1], 1) + ms[lvl][2] / max(cnt[lvl][2], 1)
-        byt = down + up
+        byt = None if down is None else down + up
         row = {"level": lvl, "n": n, "stored": z, "us_per_vcycle": 1e3 * t,
-               "algorithmic_bytes": byt, "gbs": byt / (t * 1e-3) / 1e9 if t > 0 else None,
-               "frac_of_hbm": byt / (t * 1e-3) / 1e9 / peak if t > 0 else None}
+               "algorithmic_bytes": byt, "gbs": byt / (t * 1e-3) / 1e9 if t > 0 and byt else None,
+               "frac_of_hbm": byt / (t * 1e-3) / 1e9 / peak if t > 0 and byt else None}
+        if down is None:
+            row["note"] = "iterative coarsest solve (FCG + block-Jacobi ILU(1), at most the configured inner iterations)"
         if tail < L and lvl == tail:
             row["note"] = f"time of the shared-memory cluster tail, levels {tail}..{L}"
         elif lvl > tail:
