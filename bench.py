@@ -409,12 +409,17 @@ def level_table(amg, lev_prof, mode: str, peak: float) -> list:
         n = info[lvl][0]
         lay = amg.level_layout(lvl)
         z, ib = lay["stored"], lay["index_bytes"]
+        pe = amg.level_pattern(lvl)["entries"]
+        # one sweep's matrix: the values, and a column per entry of the slices
+        # without a shared offset pattern (the pattern itself per entry column
+        # and a flag per slice for the others)
+        mat = z * vb + (ib * (z - pe) + ib * (pe / 32 + (n + 31) // 32) if pe else ib * z)
         nc = info[lvl + 1][0] if lvl < L else 0
         down = up = 0.0
         if lvl < L:
             restr = n * vb + 4 * (n + nc) + (nc * 8 if lvl + 1 == L else 3 * nc * vb)
-            down = restr + (z * (vb + ib) + 4 * n * vb if lvl > 0 else 0)
-            up = (3 * n * vb + 4 * n + nc * vb + z * (vb + ib) + 4 * n * vb) if lvl > 0 else 0
+            down = restr + (mat + 4 * n * vb if lvl > 0 else 0)
+            up = (3 * n * vb + 4 * n + nc * vb + mat + 4 * n * vb) if lvl > 0 else 0
         elif coarse_kind == "iter":
             down = None  # FCG + block-Jacobi ILU(1): its inner iteration count varies per V-cycle
         else:

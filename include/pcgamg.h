@@ -393,13 +393,14 @@ int amg_level_agg(amg_handle h, int level, int pass, int32_t *agg, int64_t *n_ou
  * as int16 offsets from the row, else 4). Any pointer may be NULL. */
 int amg_level_layout(amg_handle h, int level, int *slice, int64_t *stored, int *index_bytes);
 
-/* Slices of level l stored with a shared offset pattern (level 0 only; 0
- * elsewhere, and with PCGAMG_UNIFORM=0 in the environment at setup): the
- * rows of such a slice take their columns from one pattern of offsets
- * i + o_k (each row's absent offsets kept as explicit zeros, so a row still
- * sums its entries in increasing column order), and the level-0 sweeps and
- * q = A p read that pattern once per slice instead of one column index per
- * entry. *slices such slices, *entries their stored entries (padding
+/* Slices of level l stored with a shared offset pattern (0 with
+ * PCGAMG_UNIFORM=0 in the environment at setup): the rows of such a slice
+ * take their columns from one pattern of offsets i + o_k (each row's absent
+ * offsets kept as explicit zeros, so a row still sums its entries in
+ * increasing column order), and the V-cycle sweeps and q = A p read that
+ * pattern once per slice instead of one column index per entry. On a
+ * structured mesh nearly every level-0 slice has one, and most of level
+ * 1's. *slices such slices, *entries their stored entries (padding
  * included). Any pointer may be NULL. Errors: AMG_ERR_ARG. */
 int amg_level_pattern(amg_handle h, int level, int64_t *slices, int64_t *entries);
 

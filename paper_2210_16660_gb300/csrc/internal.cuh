@@ -125,7 +125,7 @@ struct Sell {
     int16_t *col16 = nullptr;  // col - row when every |col - row| < 2^15, else null
     double *v64 = nullptr;
     float *v32 = nullptr;
-    // Shared offset patterns (level 0; null elsewhere). A slice whose rows
+    // Shared offset patterns (null when no slice of the level has one). A slice whose rows
     // all take their columns from one offset pattern (i + o_0 < i + o_1 <
     // ...) is stored in pattern order, each row's absent offsets as explicit
     // zeros, and upat[sptr[s] / 32 + k] = o_k holds the pattern once for the

@@ -928,7 +928,7 @@ int pairwise_pass(amg_hier *h, const DevCSR &cur, const double *w, int32_t **agg
     return AMG_OK;
 }
 
-int finish_level(amg_hier *h, Level &lv, bool first, bool coarsest, cudaStream_t s) {
+int finish_level(amg_hier *h, Level &lv, bool coarsest, cudaStream_t s) {
     Mem &M = h->mem;
     int n = lv.A.n;
     PCG_TRY(alloc(M, &lv.dinv, n));
@@ -985,9 +985,9 @@ int finish_level(amg_hier *h, Level &lv, bool first, bool coarsest, cudaStream_t
             PCG_LAUNCH_CK();
         }
     }
-    // shared offset patterns (level 0: the level the Krylov and level-0
-    // sweeps stream every iteration)
-    if (first && !h->no_uniform) {
+    // shared offset patterns (every level: level 0 of a structured mesh
+    // takes them almost everywhere, level 1 mostly)
+    if (!h->no_uniform) {
         PCG_TRY(alloc(M, &S.upat, (size_t)tot / kSlice));
         unsigned long long *dcount = nullptr;
         PCG_TRY(alloc(M, &dcount, 1));
@@ -1208,7 +1208,7 @@ int setup_impl(amg_hier *h, const amg_csr *A, const amg_params *prm, cudaStream_
         nx.w = curw;
     }
     int L = (int)h->lev.size() - 1;
-    for (int l = 0; l <= L; l++) PCG_TRY(finish_level(h, h->lev[l], l == 0, l == L, s));
+    for (int l = 0; l <= L; l++) PCG_TRY(finish_level(h, h->lev[l], l == L, s));
 
     // coarsest solver: dense inverse up to kDenseMax rows (AUTO), else the
     // iterative FCG + block-Jacobi ILU(1) solve of Sec. 3.1

@@ -1,14 +1,16 @@
-"""Level 0 stored with shared offset patterns.
+"""Levels stored with shared offset patterns (level 0 almost everywhere on a
+structured mesh, level 1 mostly).
 
 A sliced-ELL slice whose 32 rows all take their columns from one pattern of
 offsets (row i uses columns i + o_k, k = 0..w-1, a row's absent offsets kept
 as explicit zeros) keeps the pattern once, and the level-0 V-cycle sweeps
 and q = A p read one offset per entry column instead of one column index per
-entry. Each row still sums its entries in increasing column order, the
+entry (the coarse-level sweeps likewise). Each row still sums its entries in increasing column order, the
 inserted zeros adding exact zeros, so the values are those of the plain
 layout.
 
-Bar: on a structured Q1 mesh nearly every level-0 slice takes a pattern; a
+Bar: on a structured Q1 mesh nearly every level-0 slice takes a pattern, and
+every level's count equals a host restatement of the rule; a
 solve gives the same iteration count and the same x (torch.equal) as the
 plain layout (PCGAMG_UNIFORM=0) in both modes and with 16- and 32-bit
 columns, and meets the single-solve bar against the oracle; a permuted
@@ -96,7 +98,13 @@ def test_pattern_layout_equals_plain(mode, N, col16):
     assert (pat["slices"], pat["entries"]) == want
     assert pat["slices"] >= 0.95 * _slices(prob.A.n)
     assert a2.level_pattern(0) == {"slices": 0, "entries": 0}
-    assert a1.level_pattern(1) == {"slices": 0, "entries": 0}
+    # the coarse levels follow the same rule (level 1 of a structured mesh mostly takes one)
+    for lvl in range(1, len(a1.info())):
+        rp, ci, v = a1.level_csr(lvl)
+        C = W.CSR(len(rp) - 1, rp, ci, v)
+        got = a1.level_pattern(lvl)
+        assert (got["slices"], got["entries"]) == _pattern_slices(C), lvl
+        assert a2.level_pattern(lvl) == {"slices": 0, "entries": 0}
     assert a1.level_layout(0) == a2.level_layout(0)
     r1, x1 = _solve(a1, b)
     r2, x2 = _solve(a2, b)
