@@ -107,7 +107,7 @@ __device__ __forceinline__ T sell_row(const IDX *__restrict__ c, const T *__rest
 // dependent gather round trips whatever U is. Entries are summed one by one
 // in storage order (acc += a_k x(j_k)), as in sell_row.
 //
-// With upat (level 0), a slice stored with a shared offset pattern takes
+// With upat (the level's shared offset patterns), a slice stored with one takes
 // column i + o_k from the pattern, one offset per entry column of the slice
 // read by every lane of the warp, instead of one column index per entry: the
 // column of entry k is rb + c[cs k], with (c, cs, rb) = (the row's column
